@@ -1,0 +1,366 @@
+#!/usr/bin/env python3
+"""Benchmark: Mpixel/s of L^p-norm phase unwrapping to relative residual 1e-6 on one GB300.
+
+One step = one full call of the method (Algorithm 1 of arXiv 2203.13675: every
+outer reweighting pass with its inner PCG solve to relative residual 1e-6) on
+one synthetic 2048 x 2048 wrapped-phase map shaped like the paper's workload
+(ramp 0.02 rad/px, 12 Gaussian bumps, noise 0.5 rad, 5 % masked disk; p = 1,
+tau = 1e-2, at most 5 outer passes), inputs resident in HBM.  The working set
+(about 0.5 GB of FP64 planes) is larger than L2, so no flush is needed.
+
+Reports the chosen form (value) and the plain FP64 Jacobi form ("plain"), the
+roofline of the persistent PCG kernel (achieved algorithmic HBM bytes over its
+CUDA-event duration, against MEASURED_PEAKS.json), the end-to-end figure with
+host buffers, the oracle timed on a bounded sample on one host core, and the
+SM clocks sampled during the timed region.
+
+usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       N > 1 runs under torch.distributed.run: independent replicas (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s unwrapped to rel. residual 1e-6, plain vs chosen form; % of HBM peak"
+UNIT = "Mpixel/s"
+
+# Algorithmic HBM bytes per pixel per PCG iteration of the persistent FP64
+# solver: phase A reads s, d_old, U, V and writes d, q (48 B); phase B reads
+# phi, d, r, q, D^-1 and writes phi, r, s (64 B).  M = I has no s and no D^-1.
+ALG_BYTES = {("f64", "jacobi"): 112, ("f64", "identity"): 96}
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("ulp_fp64.cu", "ulp_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2203_13675_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel_tag):
+    """DRAM bytes per pixel per iteration from a committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    mh = re.search(r"source_hash:\s*(\w+)", txt)
+    mt = re.search(r"dram_bytes_per_px_iter:\s*([0-9.]+)", txt)
+    if not mh or not mt or mh.group(1) != kernel_source_hash():
+        return None
+    return float(mt.group(1))
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(wl_name, p, kind, gpu_iters, budget_s=20.0):
+    """The FP64 oracle on one core over a bounded sample of the same workload:
+    one outer pass capped at n1 and n2 PCG iterations.  Full-run time =
+    passes x (setup) + iterations x (per-iteration time), iterations = the
+    oracle's own count on this workload when recorded, else the GPU's."""
+    import oracle
+    from paper_2203_13675_gb300 import synth
+    w = synth.WORKLOADS[wl_name]
+    m = synth.workload_map(wl_name)
+    kinds = {"identity": oracle.M_IDENTITY, "jacobi": oracle.M_JACOBI}
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.unwrap(m.psi, m.mask, p=p, tau=w["tau"], kind=kinds[kind], tol=w["tol"], max_outer=1, max_inner=2)
+    t_small = time.perf_counter() - t0
+    n1 = 2
+    # per-iteration cost from a second sample sized to the budget
+    t0 = time.perf_counter()
+    oracle.unwrap(m.psi, m.mask, p=p, tau=w["tau"], kind=kinds[kind], tol=w["tol"], max_outer=1, max_inner=12)
+    t12 = time.perf_counter() - t0
+    per_it = max((t12 - t_small) / 10.0, 1e-9)
+    n2 = int(max(12, min(400, (budget_s - t_small - t12) / per_it)))
+    t0 = time.perf_counter()
+    oracle.unwrap(m.psi, m.mask, p=p, tau=w["tau"], kind=kinds[kind], tol=w["tol"], max_outer=1, max_inner=n2)
+    t2 = time.perf_counter() - t0
+    per_it = (t2 - t_small) / (n2 - n1)
+    setup = t_small - n1 * per_it
+    src = "GPU run"
+    iters = gpu_iters
+    gold = os.path.join(ROOT, "tests", "golden", "oracle_runs.json")
+    key = f"{wl_name}_p{p:g}_{kind}"
+    if os.path.exists(gold):
+        d = json.load(open(gold))
+        if key in d:
+            iters = d[key]["stats"]["inner"]
+            src = "oracle's own full run (tests/golden/oracle_runs.json)"
+    est = len(iters) * setup + sum(iters) * per_it
+    H, W = m.psi.shape
+    return {"value": H * W / est / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{wl_name} {H}x{W} p={p:g} {kind}: oracle unwrap, 1 outer pass capped at {n1} and "
+                       f"{n2} PCG iterations ({t_small + t12 + t2:.1f} s CPU); full run extrapolated as "
+                       f"{len(iters)} x setup {setup:.2f} s + {sum(iters)} iterations x {per_it * 1e3:.1f} ms "
+                       f"(iteration counts from the {src})"),
+            "est_full_run_s": est}
+
+
+# ------------------------------------------------------------------ our arm
+def run_form(plan, psi, mask, phi, w, precond, steps, warmup, dist):
+    import torch
+    call = dict(p=w["p"], eps=w["tau"], precond=precond, tol=w["tol"], max_outer=w["max_outer"])
+    for _ in range(warmup):
+        plan.unwrap(psi, mask, phi=phi, stats=False, **call)
+    torch.cuda.synchronize()
+    rc, st = plan.last_status()
+    if rc < 0:
+        raise RuntimeError(f"solver status {rc}")
+    plan.counters(reset=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.unwrap(psi, mask, phi=phi, stats=False, **call)
+    e1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / steps
+    cnt = plan.counters(reset=True)
+    rc, st2 = plan.last_status()
+    return ms, st2, cnt
+
+
+def run_ours(args):
+    import torch
+    from paper_2203_13675_gb300 import native, synth
+    rank, world, local = env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = td
+    torch.cuda.set_device(local)
+    native.load()
+    wl_name = args.workload
+    w = dict(synth.WORKLOADS[wl_name])
+    m = synth.workload_map(wl_name)
+    H, W = m.psi.shape
+    psi = torch.from_numpy(m.psi).cuda()
+    mask = torch.from_numpy(m.mask).cuda() if m.mask is not None else None
+    phi = torch.empty_like(psi)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+
+    # plain form: FP64 Jacobi PCG (the paper's method as written)
+    plan = native.Plan(H, W, outer_tol=0.0, profile=1)
+    with ClockSampler(uuid) as clk:
+        ms_plain, st_plain, cnt_plain = run_form(plan, psi, mask, phi, w, "jacobi", args.steps, args.warmup, dist)
+    chosen = ("f64", "jacobi")
+    ms, st, cnt = ms_plain, st_plain, cnt_plain
+
+    # roofline of the persistent PCG kernel over the timed region
+    iters = st["inner_total"] * args.steps
+    alg = ALG_BYTES[chosen] * H * W * iters
+    solver_s = cnt["solver_ms"] / 1e3
+    achieved = alg / solver_s / 1e9 if solver_s > 0 else None
+    peak, peak_kind = load_peaks()
+    tpx = profile_traffic(f"pcg64_{chosen[1]}_c2_2048")
+    traffic = None
+    if tpx is not None and cnt["timed_launches"]:
+        traffic = tpx * H * W * iters / cnt["timed_launches"]
+
+    # end to end: host (pinned) buffers in, host buffer out, inside the timed region
+    psi_h = torch.from_numpy(m.psi).pin_memory()
+    mask_h = torch.from_numpy(m.mask).pin_memory() if m.mask is not None else None
+    phi_h = torch.empty_like(psi_h).pin_memory()
+    psi_d = torch.empty_like(psi)
+    mask_d = torch.empty_like(mask) if mask is not None else None
+    call = dict(p=w["p"], eps=w["tau"], precond=chosen[1], tol=w["tol"], max_outer=w["max_outer"])
+    for _ in range(1):
+        psi_d.copy_(psi_h, non_blocking=True)
+        plan.unwrap(psi_d, mask_d if mask_d is None else mask_d.copy_(mask_h, non_blocking=True), phi=phi,
+                    stats=False, **call)
+        phi_h.copy_(phi, non_blocking=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        psi_d.copy_(psi_h, non_blocking=True)
+        if mask_d is not None:
+            mask_d.copy_(mask_h, non_blocking=True)
+        plan.unwrap(psi_d, mask_d, phi=phi, stats=False, **call)
+        phi_h.copy_(phi, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    if dist:
+        dist.barrier()
+
+    # max over ranks
+    vals = torch.tensor([ms, ms_plain, ms_e2e], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    ms, ms_plain, ms_e2e = [float(x) for x in vals.cpu()]
+    px = H * W * world
+    line = {
+        "metric": METRIC, "value": px / (ms * 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": chosen[0], "data": "synthetic",
+        "config": {"workload": f"{wl_name}_p{w['p']:g}_{chosen[1]}", "H": H, "W": W, "p": w["p"],
+                   "tau": w["tau"], "precond": chosen[1], "precision": chosen[0], "tol": w["tol"],
+                   "max_outer": w["max_outer"], "outer_tol": 0.0, "mask_frac": w["mask_frac"],
+                   "noise": w["noise"], "seed": w["seed"], "parallelism": f"replicas{world}",
+                   "l2": "working set ~0.5 GB of planes > 129 MB L2 (inputs larger than L2)",
+                   "inner_iterations": st["inner"], "outer_passes": st["outer"]},
+        "plain": {"value": px / (ms_plain * 1e3), "unit": UNIT, "ms_per_step": ms_plain, "precond": "jacobi",
+                  "dtype": "f64", "inner_iterations": st_plain["inner"]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": f"k_pcg64<{chosen[1]}> (persistent PCG)", "peak_source": f"{peak_kind} hbm_gbs",
+                     "alg_bytes_per_px_iter": ALG_BYTES[chosen],
+                     "solver_ms_per_step": cnt["solver_ms"] / args.steps},
+        "e2e": {"value": px / (ms_e2e * 1e3), "unit": UNIT, "h2d_bytes_per_step": H * W * 8 + (H * W if mask is not None else 0),
+                "d2h_bytes_per_step": H * W * 8, "ms_per_step": ms_e2e},
+        "gpu_launches": cnt["kernel_launches"],
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(wl_name, w["p"], chosen[1], st["inner"])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, local = env_rank()
+    if rank != 0:
+        return
+    from paper_2203_13675_gb300 import synth
+    wl_name = args.workload
+    w = synth.WORKLOADS[wl_name]
+    nproc = os.cpu_count()
+    vals = []
+    sample = None
+    t_all = time.perf_counter()
+    for s in range(args.warmup + args.steps):
+        r = oracle_sample(wl_name, w["p"], "jacobi", [w["max_outer"]] * 1, budget_s=8.0)
+        if s >= args.warmup:
+            vals.append(r)
+            sample = r["sample"]
+    est = statistics.median([v["est_full_run_s"] for v in vals])
+    H, W = w["H"], w["W"]
+    value = H * W / est / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{wl_name}_p{w['p']:g}_jacobi", "H": H, "W": W, "precond": "jacobi"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host_cores_available": nproc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2_2048")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

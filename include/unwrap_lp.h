@@ -1,0 +1,235 @@
+/*
+ * unwrap_lp.h -- C ABI of the GB300 (sm_103a) L^p-norm phase-unwrapping library.
+ *
+ * Method: Legarda-Saenz, Brito-Loeza, Espinosa-Romero, "On the performance of
+ * preconditioned methods to solve L^p-norm phase unwrapping" (arXiv 2203.13675),
+ * Algorithm 1: an outer reweighting (IRLS) loop that turns the wrapped-gradient
+ * residual into per-edge weights U, V (Eq. UV), around an inner preconditioned
+ * conjugate-gradient solve of the weighted 5-point system A(U,V) phi = b
+ * (Eq. Axb), with the paper's preconditioners (Sec. 2 list: identity, Jacobi,
+ * ILU(0), IC(0), SOR read as SSOR) plus a DCT Poisson preconditioner (the
+ * Fourier-basis approach of Sec. 1).
+ *
+ * Conventions shared by every entry point:
+ *  - Grids are H rows (index i, the paper's y) by W columns (index j, the
+ *    paper's x); pixel (i,j) is element i*W + j of a contiguous row-major
+ *    array.  H >= 2, W >= 2.
+ *  - Unless stated otherwise pointers are CUDA DEVICE pointers owned by the
+ *    caller; the library never frees them.  Work is enqueued on the given
+ *    stream (NULL = legacy default stream) and returns before it finishes
+ *    unless the function says it synchronises.
+ *  - Return values are ulp_status codes: 0 success, 1 a warning (phi written,
+ *    the inner solve hit l_max), negative an error (outputs undefined).
+ *    ulp_last_error() returns a message for the calling thread's last error.
+ *  - Masks are uint8 arrays (1 = pixel excluded: every edge touching it gets
+ *    weight 0 and its phi keeps the initial value); NULL means no mask.
+ *  - Every wait inside a kernel is bounded (options.spin_timeout_s); a wait
+ *    that runs out makes the call return ULP_ERR_TIMEOUT, never a hang.
+ */
+#ifndef UNWRAP_LP_H
+#define UNWRAP_LP_H
+
+#include <stdint.h>
+
+/* Symbol visibility of the entry points (the library is built with hidden
+ * default visibility, so only these names are exported). */
+#ifndef ULP_API
+#define ULP_API __attribute__((visibility("default")))
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Preconditioner M of Algorithm 1 ("estimate preconditioning matrix M from A").
+ * The first five are the paper's list (Sec. 2, items 1-5); DCT is the
+ * unweighted Neumann-Poisson pseudo-inverse applied through cosine transforms. */
+typedef enum {
+  ULP_PRECOND_IDENTITY = 0, /* M = I: PCG becomes CG */
+  ULP_PRECOND_JACOBI = 1,   /* M = diag(A) */
+  ULP_PRECOND_ILU0 = 2,     /* incomplete LU, no fill, natural row-major order */
+  ULP_PRECOND_IC0 = 3,      /* incomplete Cholesky, no fill (same M as ILU0 for symmetric A) */
+  ULP_PRECOND_SSOR = 4,     /* symmetric SOR, relaxation options.omega */
+  ULP_PRECOND_DCT = 5       /* s = L^+ r, L the unit-weight Neumann Laplacian */
+} ulp_precond;
+
+typedef enum {
+  ULP_OK = 0,
+  ULP_WARN_MAXITER = 1,    /* phi written; some inner solve stopped at l_max */
+  ULP_ERR_INVALID = -1,    /* bad argument (sizes, p, eps, non-finite psi, ...) */
+  ULP_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+  ULP_ERR_BREAKDOWN = -3,  /* d^T A d <= 0 or non-finite inside PCG */
+  ULP_ERR_TIMEOUT = -4,    /* an in-kernel wait exceeded options.spin_timeout_s */
+  ULP_ERR_NOMEM = -5,      /* device allocation failed */
+  ULP_ERR_UNSUPPORTED = -6 /* option combination not built */
+} ulp_status;
+
+typedef enum {
+  ULP_STOP_RELRES = 0, /* stop when ||r_l||_2 <= tol * ||b||_2 (recurrence residual) */
+  ULP_STOP_PAPER = 1   /* Algorithm 1's test: stop when delta_new <= tol^2 delta_0, delta = r^T M^-1 r */
+} ulp_stop_mode;
+
+typedef enum {
+  ULP_PRECISION_FP64 = 0,  /* every vector, weight and reduction in FP64 */
+  ULP_PRECISION_MIXED = 1  /* FP32 vectors/weights/stencil, FP64-accurate dot products and
+                              alpha/beta, FP64 phi and true residual every refresh period */
+} ulp_precision;
+
+typedef enum {
+  ULP_PHI0_ZERO = 0, /* phi^0 = 0 */
+  ULP_PHI0_USER = 1  /* phi holds phi^0 on entry (warm start / resume / the paper's random start) */
+} ulp_phi0_mode;
+
+typedef struct ulp_options {
+  int stop_mode;          /* ulp_stop_mode, default ULP_STOP_RELRES */
+  double outer_tol;       /* Algorithm 1 outer test: continue while ||phi^{k+1}-phi^k||/||phi^k|| > outer_tol.
+                             Default 1e-6 (the paper's tol).  ||phi^k|| = 0 counts as +infinity. */
+  long long refresh;      /* true-residual period of Algorithm 1 (r = b - A phi when l mod period = 0);
+                             <= 0: floor(sqrt(H*W)) in FP64, 20 in mixed precision */
+  double omega;           /* SSOR relaxation in (0, 2), default 1 */
+  int precision;          /* ulp_precision, default ULP_PRECISION_FP64 */
+  int phi0_mode;          /* ulp_phi0_mode, default ULP_PHI0_ZERO */
+  int tile_rows;          /* rows per warp tile; 0 = autotuned table */
+  int blocks_per_sm;      /* resident blocks per SM of the persistent solver; 0 = autotuned */
+  double spin_timeout_s;  /* bound on any in-kernel wait, default 2.0 s */
+  int profile;            /* 1: record CUDA events around every persistent solver launch (ulp_plan_counters) */
+} ulp_options;
+
+/* Per-call statistics, written on the host when the call synchronises. */
+#define ULP_MAX_OUTER_STATS 64
+typedef struct ulp_stats {
+  int status;                                 /* ulp_status of the call */
+  int outer;                                  /* outer passes run (k at exit) */
+  long long inner_total;                      /* sum of inner PCG iterations */
+  long long inner[ULP_MAX_OUTER_STATS];       /* l at exit of each inner solve */
+  double relres[ULP_MAX_OUTER_STATS];         /* ||r_l|| / ||b|| at exit of each inner solve */
+  double outer_err[ULP_MAX_OUTER_STATS];      /* Algorithm 1's error after each pass (inf if ||phi^k|| = 0) */
+} ulp_stats;
+
+/* Fills *opt with the defaults listed above. */
+ULP_API void ulp_options_default(ulp_options* opt);
+
+/* Message for the calling thread's most recent error ("" if none). Static storage. */
+ULP_API const char* ulp_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Whole method (Algorithm 1).
+ * ------------------------------------------------------------------------- */
+
+/* unwrap_lp: Algorithm 1 with default options except the arguments given.
+ *   psi   [H*W]  wrapped phase, values in (-pi, pi] (Eq. wrapped); host OR device
+ *                memory (detected with cudaPointerGetAttributes).
+ *   p            the L^p exponent, 0 <= p <= 2 (the paper states p < 2; p = 2 is the
+ *                unweighted least-squares limit).
+ *   eps          tau of Eq. (UV), > 0 (the paper uses 0.01).
+ *   precond      ulp_precond.
+ *   tol          inner relative-residual tolerance (ULP_STOP_RELRES), > 0.
+ *   max_outer    k_max of Algorithm 1 (>= 1); the outer tolerance is 0 here, so
+ *                passes continue until phi stops changing or k_max is reached.
+ *   max_inner    l_max; <= 0 means 2*H*W (the paper's choice).
+ *   phi   [H*W]  output unwrapped phase, same memory kind as psi.  phi^0 = 0.
+ * Synchronises the legacy default stream.  Host buffers are copied to and from
+ * internal device buffers inside the call.  Allocates and frees its workspace. */
+ULP_API int unwrap_lp(const double* psi, int H, int W, double p, double eps, int precond,
+              double tol, int max_outer, int max_inner, double* phi);
+
+/* Plans own all device workspace for one grid size (or one batch of sizes) and
+ * are reused across calls; creating one allocates, calls on it do not. */
+typedef struct ulp_plan_s* ulp_plan;
+
+/* ulp_plan_create: workspace for H x W maps.  opt may be NULL (defaults).
+ * Allocates device memory; the current CUDA device is the plan's device. */
+ULP_API int ulp_plan_create(int H, int W, const ulp_options* opt, ulp_plan* out);
+
+/* ulp_plan_create_batched: workspace for n maps of sizes H[t] x W[t] solved
+ * together by one persistent launch per outer pass.  1 <= n <= 256. */
+ULP_API int ulp_plan_create_batched(int n, const int* H, const int* W, const ulp_options* opt,
+                            ulp_plan* out);
+
+ULP_API void ulp_plan_destroy(ulp_plan plan);
+
+/* ulp_unwrap: Algorithm 1 on the plan's grid, enqueued on cuda_stream.
+ *   psi [H*W] device, mask [H*W] device uint8 or NULL, phi [H*W] device
+ *   (holds phi^0 on entry when opt.phi0_mode = ULP_PHI0_USER).
+ *   stats: host pointer or NULL.  Non-NULL makes the call synchronise the
+ *   stream and fill *stats; the return value is then the solve's status.
+ *   NULL returns after enqueueing (ULP_OK unless an argument is invalid);
+ *   ulp_plan_last_status() reads the outcome later. */
+ULP_API int ulp_unwrap(ulp_plan plan, const double* psi, const uint8_t* mask, double p, double eps,
+               int precond, double tol, int max_outer, int max_inner, double* phi,
+               void* cuda_stream, ulp_stats* stats);
+
+/* One map of a batch: device pointers as in ulp_unwrap, own p and tau. */
+typedef struct ulp_map {
+  const double* psi;
+  const uint8_t* mask;
+  double* phi;
+  double p;
+  double eps;
+} ulp_map;
+
+/* ulp_unwrap_batched: the n maps of a batched plan (sizes in creation order),
+ * all outer passes of all maps in max_outer persistent launches.  per_map:
+ * host array of n stats or NULL (same synchronisation rule as ulp_unwrap).
+ * Returns the worst status over the maps. */
+ULP_API int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precond, double tol,
+                       int max_outer, int max_inner, void* cuda_stream, ulp_stats* per_map);
+
+/* Synchronises the plan's last stream and returns its last call's status;
+ * fills *stats (first map of a batch) when non-NULL. */
+ULP_API int ulp_plan_last_status(ulp_plan plan, ulp_stats* stats);
+
+/* Instrumentation of a plan: kernels it enqueued, and (with options.profile)
+ * the summed device duration of its persistent solver launches, timed with
+ * CUDA events recorded on the call's stream around each launch.  Reading the
+ * durations synchronises those events.  reset != 0 clears after reading. */
+typedef struct ulp_counters {
+  long long kernel_launches;  /* every kernel the plan enqueued */
+  long long solver_launches;  /* persistent PCG launches among them */
+  double solver_ms;           /* summed duration of the timed solver launches (profile only) */
+  long long timed_launches;   /* solver launches included in solver_ms */
+} ulp_counters;
+ULP_API int ulp_plan_counters(ulp_plan plan, int reset, ulp_counters* out);
+
+/* ---------------------------------------------------------------------------
+ * Single steps of the method (device pointers, contiguous H*W arrays,
+ * enqueued on cuda_stream).  They use the same kernels as the solver.
+ * ------------------------------------------------------------------------- */
+
+/* Sec. 2.1: Delta^x_{i,j} = W(psi_{i,j+1} - psi_{i,j}) for j <= W-2 and
+ * Delta^y_{i,j} = W(psi_{i+1,j} - psi_{i,j}) for i <= H-2, with W the wrapping
+ * operator of Eq. (wrapped) onto (-pi, pi]; the last column of dx and the last
+ * row of dy are 0 (they only multiply zero boundary weights). */
+ULP_API int ulp_wrapped_diffs(const double* psi, int H, int W, double* dx, double* dy, void* cuda_stream);
+
+/* Eq. (UV) and Eq. (Axb): U_{i,j} = tau / (|phi_{i,j+1} - phi_{i,j} - dx_{i,j}|^(2-p) + tau),
+ * V likewise along i (0 on edges leaving the grid or touching a masked pixel), and the
+ * right-hand side b_{i,j} = dx_{i,j-1}U_{i,j-1} - dx_{i,j}U_{i,j} + dy_{i-1,j}V_{i-1,j} - dy_{i,j}V_{i,j}.
+ * b may be NULL. */
+ULP_API int ulp_weights(const double* phi, const double* dx, const double* dy, const uint8_t* mask,
+                int H, int W, double p, double eps, double* U, double* V, double* b,
+                void* cuda_stream);
+
+/* Eq. (Axb) left-hand side: y = A(U,V) x, with
+ * (A x)_{i,j} = (U_{i,j-1}+U_{i,j}+V_{i-1,j}+V_{i,j}) x_{i,j}
+ *              - U_{i,j} x_{i,j+1} - U_{i,j-1} x_{i,j-1} - V_{i,j} x_{i+1,j} - V_{i-1,j} x_{i-1,j}. */
+ULP_API int ulp_matvec(const double* U, const double* V, const double* x, int H, int W, double* y,
+               void* cuda_stream);
+
+/* One application s = M^{-1} r of the preconditioner built from A(U,V)
+ * (Algorithm 1, "estimate preconditioning matrix M from A").  omega is used by
+ * SSOR only.  mask is used by the DCT preconditioner only (s = 0 on masked pixels). */
+ULP_API int ulp_precond_apply(int precond, const double* U, const double* V, const uint8_t* mask,
+                      int H, int W, double omega, const double* r, double* s, void* cuda_stream);
+
+/* The inner PCG of Algorithm 1 on A(U,V) phi = b, warm-started from phi
+ * (overwritten with the result).  stats (host, nullable) receives inner[0],
+ * relres[0] and the status; non-NULL synchronises. */
+ULP_API int ulp_pcg(const double* U, const double* V, const double* b, int H, int W, int precond,
+            double tol, int max_inner, const ulp_options* opt, double* phi, void* cuda_stream,
+            ulp_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UNWRAP_LP_H */

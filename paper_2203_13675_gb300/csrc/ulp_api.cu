@@ -1,0 +1,557 @@
+// ulp_api.cu -- C ABI of the GB300 L^p phase-unwrapping library: plans
+// (workspace ownership), argument checks, and the host orchestration of
+// Algorithm 1 (outer reweighting passes around the persistent PCG engine).
+// All control decisions of the iteration stay on the device, so a call
+// enqueues a fixed sequence of kernels and never waits for the GPU unless
+// statistics are requested.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "ulp_host.h"
+
+using namespace ulp;
+
+struct ulp_plan_s {
+  Plan p;
+};
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define ULP_CU(x)                                                                   \
+  do {                                                                              \
+    cudaError_t e_ = (x);                                                           \
+    if (e_ != cudaSuccess) return fail(ULP_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" void ulp_options_default(ulp_options* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->stop_mode = ULP_STOP_RELRES;
+  o->outer_tol = 1e-6;
+  o->refresh = 0;
+  o->omega = 1.0;
+  o->precision = ULP_PRECISION_FP64;
+  o->phi0_mode = ULP_PHI0_ZERO;
+  o->tile_rows = 0;
+  o->blocks_per_sm = 0;
+  o->spin_timeout_s = 2.0;
+}
+
+extern "C" const char* ulp_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ plans
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static void destroy_plan(Plan& pl) {
+  for (cudaEvent_t e : pl.ev_pool) cudaEventDestroy(e);
+  pl.ev_pool.clear();
+  if (pl.arena) cudaFree(pl.arena);
+  pl.arena = nullptr;
+}
+
+// Next (start, stop) event pair for timing one solver launch, or nulls when
+// profiling is off.
+static void next_events(Plan& pl, cudaEvent_t* e0, cudaEvent_t* e1) {
+  *e0 = *e1 = nullptr;
+  if (!pl.opt.profile) return;
+  while (pl.ev_pool.size() < pl.ev_used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    pl.ev_pool.push_back(e);
+  }
+  *e0 = pl.ev_pool[pl.ev_used];
+  *e1 = pl.ev_pool[pl.ev_used + 1];
+  pl.ev_used += 2;
+}
+
+static int default_tile_rows(int H, int W) {
+  // rows per warp tile: enough tiles to fill the resident warps, long enough
+  // windows to amortise the two halo rows.
+  (void)W;
+  if (H >= 2048) return 32;
+  if (H >= 512) return 16;
+  return 8;
+}
+
+static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_options* opt) {
+  if (n < 1 || n > kMaxMaps) return fail(ULP_ERR_INVALID, "map count %d outside [1, %d]", n, kMaxMaps);
+  for (int m = 0; m < n; ++m) {
+    if (H[m] < 2 || W[m] < 2) return fail(ULP_ERR_INVALID, "map %d: H=%d W=%d (need >= 2)", m, H[m], W[m]);
+    if ((long long)H[m] * W[m] > (1LL << 31)) return fail(ULP_ERR_INVALID, "map %d too large", m);
+  }
+  if (opt) pl.opt = *opt; else ulp_options_default(&pl.opt);
+  if (!(pl.opt.spin_timeout_s > 0.0)) pl.opt.spin_timeout_s = 2.0;
+  if (pl.opt.precision != ULP_PRECISION_FP64 && pl.opt.precision != ULP_PRECISION_MIXED)
+    return fail(ULP_ERR_INVALID, "unknown precision %d", pl.opt.precision);
+  ULP_CU(cudaGetDevice(&pl.device));
+  ULP_CU(cudaDeviceGetAttribute(&pl.nsm, cudaDevAttrMultiProcessorCount, pl.device));
+  int coop = 0;
+  ULP_CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, pl.device));
+  if (!coop) return fail(ULP_ERR_UNSUPPORTED, "device lacks cooperative launch");
+  pl.nmaps = n;
+  int maxH = 0;
+  for (int m = 0; m < n; ++m) maxH = H[m] > maxH ? H[m] : maxH;
+  pl.R = pl.opt.tile_rows > 0 ? pl.opt.tile_rows : default_tile_rows(maxH, 0);
+
+  // geometry and arena layout
+  pl.hmaps.assign(n, MapDesc{});
+  size_t bytes = 0;
+  int tiles = 0;
+  std::vector<size_t> plane_off(n);
+  for (int m = 0; m < n; ++m) {
+    MapDesc& M = pl.hmaps[m];
+    M.H = H[m];
+    M.W = W[m];
+    M.pitch = (W[m] + kStrip - 1) / kStrip * kStrip;
+    M.nsx = M.pitch / kStrip;
+    M.nsy = (H[m] + pl.R - 1) / pl.R;
+    M.tile_base = tiles;
+    M.ntiles = M.nsx * M.nsy;
+    tiles += M.ntiles;
+    long long rf = pl.opt.refresh > 0 ? pl.opt.refresh
+                                      : (long long)std::floor(std::sqrt((double)H[m] * (double)W[m]));
+    if (pl.opt.refresh <= 0 && pl.opt.precision == ULP_PRECISION_MIXED) rf = 20;
+    if (rf < 1) rf = 1;
+    if (rf > (1LL << 30)) rf = 1LL << 30;
+    M.refresh = (int)rf;
+    plane_off[m] = bytes;
+    const size_t e = (size_t)M.H * M.pitch;
+    bytes += 16 * align256(e * sizeof(double));   // FP64 planes
+    bytes += 13 * align256(e * sizeof(float));    // FP32 planes
+    bytes += align256(e);                         // mask
+    bytes += align256((size_t)M.ntiles * sizeof(int));
+  }
+  pl.ntiles = tiles;
+  pl.bx_elem = pl.nsm * 4;
+  const size_t off_maps = bytes;
+  bytes += align256(sizeof(MapDesc) * n);
+  const size_t off_state = bytes;
+  bytes += align256(sizeof(MapState) * n);
+  const size_t off_stats = bytes;
+  bytes += align256(sizeof(MapStats) * n);
+  const size_t off_part = bytes;
+  bytes += 3 * align256(sizeof(double) * tiles);
+  const size_t off_outer = bytes;
+  bytes += align256(sizeof(double) * 2 * (size_t)n * pl.bx_elem);
+  const size_t off_bar = bytes;
+  bytes += align256(sizeof(Barrier)) + align256(sizeof(int));
+  const size_t off_pt = bytes;
+  bytes += 2 * align256(sizeof(double) * n);
+
+  cudaError_t e = cudaMalloc(&pl.arena, bytes);
+  if (e != cudaSuccess) {
+    pl.arena = nullptr;
+    cudaGetLastError();
+    return fail(ULP_ERR_NOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+  }
+  pl.arena_bytes = bytes;
+  ULP_CU(cudaMemset(pl.arena, 0, bytes));
+  char* base = static_cast<char*>(pl.arena);
+  for (int m = 0; m < n; ++m) {
+    MapDesc& M = pl.hmaps[m];
+    const size_t e64 = align256((size_t)M.H * M.pitch * sizeof(double));
+    const size_t e32 = align256((size_t)M.H * M.pitch * sizeof(float));
+    char* p = base + plane_off[m];
+    double** f64[] = {&M.f.dx, &M.f.dy, &M.f.U, &M.f.V, &M.f.D, &M.f.Dinv, &M.f.b, &M.f.phi,
+                      &M.f.phi_prev, &M.f.r, &M.f.s, &M.f.q, &M.f.d0, &M.f.d1, &M.f.piv, &M.f.y};
+    for (double** q : f64) { *q = reinterpret_cast<double*>(p); p += e64; }
+    float** f32[] = {&M.h.U, &M.h.V, &M.h.Dinv, &M.h.x, &M.h.r, &M.h.s, &M.h.q,
+                     &M.h.d0, &M.h.d1, &M.h.cw, &M.h.cn, &M.h.pinv, &M.h.y};
+    for (float** q : f32) { *q = reinterpret_cast<float*>(p); p += e32; }
+    M.f.mask = reinterpret_cast<uint8_t*>(p);
+    p += align256((size_t)M.H * M.pitch);
+    M.flags = reinterpret_cast<int*>(p);
+  }
+  pl.dmaps = reinterpret_cast<MapDesc*>(base + off_maps);
+  pl.dstate = reinterpret_cast<MapState*>(base + off_state);
+  pl.dstats = reinterpret_cast<MapStats*>(base + off_stats);
+  pl.P0 = reinterpret_cast<double*>(base + off_part);
+  pl.P1 = reinterpret_cast<double*>(base + off_part + align256(sizeof(double) * tiles));
+  pl.P2 = reinterpret_cast<double*>(base + off_part + 2 * align256(sizeof(double) * tiles));
+  pl.outer_part = reinterpret_cast<double*>(base + off_outer);
+  pl.bar = reinterpret_cast<Barrier*>(base + off_bar);
+  pl.n_active = reinterpret_cast<int*>(base + off_bar + align256(sizeof(Barrier)));
+  pl.d_p = reinterpret_cast<double*>(base + off_pt);
+  pl.d_tau = reinterpret_cast<double*>(base + off_pt + align256(sizeof(double) * n));
+  ULP_CU(cudaMemcpy(pl.dmaps, pl.hmaps.data(), sizeof(MapDesc) * n, cudaMemcpyHostToDevice));
+  ULP_CU(cudaDeviceSynchronize());  // workspace zeroed before any stream may use it
+
+  int occ = pcg64_max_blocks_per_sm(kIdentity);
+  const int occ2 = pcg64_max_blocks_per_sm(kJacobi);
+  occ = occ2 < occ ? occ2 : occ;
+  if (occ < 1) return fail(ULP_ERR_CUDA, "persistent solver does not fit on an SM");
+  pl.bps = pl.opt.blocks_per_sm > 0 && pl.opt.blocks_per_sm < occ ? pl.opt.blocks_per_sm : occ;
+  return ULP_OK;
+}
+
+extern "C" int ulp_plan_create_batched(int n, const int* H, const int* W, const ulp_options* opt,
+                                       ulp_plan* out) {
+  if (!out || !H || !W) return fail(ULP_ERR_INVALID, "null argument");
+  *out = nullptr;
+  ulp_plan_s* p = new ulp_plan_s();
+  int rc = plan_init(p->p, n, H, W, opt);
+  if (rc != ULP_OK) {
+    destroy_plan(p->p);
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return ULP_OK;
+}
+
+extern "C" int ulp_plan_create(int H, int W, const ulp_options* opt, ulp_plan* out) {
+  return ulp_plan_create_batched(1, &H, &W, opt, out);
+}
+
+extern "C" void ulp_plan_destroy(ulp_plan plan) {
+  if (!plan) return;
+  destroy_plan(plan->p);
+  delete plan;
+}
+
+// ------------------------------------------------------------------ solve
+struct PT {
+  double p[64];
+  double tau[64];
+};
+__global__ void k_set_pt(PT pt, double* p, double* tau, int first, int n) {
+  const int t = threadIdx.x;
+  if (t < n) {
+    p[first + t] = pt.p[t];
+    tau[first + t] = pt.tau[t];
+  }
+}
+
+static int check_solver_args(int precond, double tol, int max_outer) {
+  if (precond < ULP_PRECOND_IDENTITY || precond > ULP_PRECOND_DCT)
+    return fail(ULP_ERR_INVALID, "unknown preconditioner %d", precond);
+  if (precond != ULP_PRECOND_IDENTITY && precond != ULP_PRECOND_JACOBI)
+    return fail(ULP_ERR_UNSUPPORTED, "preconditioner %d not available in this build", precond);
+  if (!(tol > 0.0)) return fail(ULP_ERR_INVALID, "tol must be > 0");
+  if (max_outer < 1) return fail(ULP_ERR_INVALID, "max_outer must be >= 1");
+  return ULP_OK;
+}
+
+static void fill_stats(const MapStats& d, ulp_stats* s) {
+  std::memset(s, 0, sizeof(*s));
+  s->status = d.status;
+  s->outer = d.outer;
+  s->inner_total = d.inner_total;
+  for (int k = 0; k < ULP_MAX_OUTER_STATS; ++k) {
+    s->inner[k] = d.inner[k];
+    s->relres[k] = d.relres[k];
+    s->outer_err[k] = d.outer_err[k];
+  }
+}
+
+static PcgArgs pcg_args(const Plan& pl, double tol, int max_inner) {
+  PcgArgs a{};
+  a.maps = pl.dmaps;
+  a.st = pl.dstate;
+  a.nmaps = pl.nmaps;
+  a.ntiles = pl.ntiles;
+  a.R = pl.R;
+  a.P0 = pl.P0;
+  a.P1 = pl.P1;
+  a.P2 = pl.P2;
+  a.bar = pl.bar;
+  a.n_active = pl.n_active;
+  a.stop_mode = pl.opt.stop_mode;
+  a.tol2 = tol * tol;
+  a.lmax = max_inner;
+  a.timeout_ns = (unsigned long long)(pl.opt.spin_timeout_s * 1e9);
+  a.omega = pl.opt.omega;
+  return a;
+}
+
+static int collect(Plan& pl, cudaStream_t st, ulp_stats* per_map) {
+  std::vector<MapStats> hs(pl.nmaps);
+  ULP_CU(cudaMemcpyAsync(hs.data(), pl.dstats, sizeof(MapStats) * pl.nmaps, cudaMemcpyDeviceToHost, st));
+  ULP_CU(cudaStreamSynchronize(st));
+  int worst = ULP_OK;
+  for (int m = 0; m < pl.nmaps; ++m) {
+    if (per_map) fill_stats(hs[m], per_map + m);
+    const int s = hs[m].status;
+    if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+    else if (s == ULP_WARN_MAXITER && worst == ULP_OK) worst = s;
+  }
+  pl.last_status = worst;
+  if (worst < 0) {
+    const char* why = worst == ULP_ERR_TIMEOUT   ? "an in-kernel wait ran out"
+                      : worst == ULP_ERR_BREAKDOWN ? "PCG breakdown (d^T A d <= 0 or not finite)"
+                      : worst == ULP_ERR_INVALID   ? "non-finite wrapped phase"
+                                                   : "solver error";
+    fail(worst, "%s", why);
+  }
+  return worst;
+}
+
+extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precond, double tol,
+                                  int max_outer, int max_inner, void* cuda_stream, ulp_stats* per_map) {
+  if (!plan || !maps) return fail(ULP_ERR_INVALID, "null argument");
+  Plan& pl = plan->p;
+  int rc = check_solver_args(precond, tol, max_outer);
+  if (rc != ULP_OK) return rc;
+  for (int m = 0; m < pl.nmaps; ++m) {
+    if (!maps[m].psi || !maps[m].phi) return fail(ULP_ERR_INVALID, "map %d: null psi or phi", m);
+    if (!(maps[m].p >= 0.0 && maps[m].p <= 2.0)) return fail(ULP_ERR_INVALID, "map %d: p outside [0, 2]", m);
+    if (!(maps[m].eps > 0.0) || !std::isfinite(maps[m].eps)) return fail(ULP_ERR_INVALID, "map %d: eps must be > 0", m);
+  }
+  ULP_CU(cudaSetDevice(pl.device));
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  pl.last_stream = st;
+  for (int first = 0; first < pl.nmaps; first += 64) {
+    PT pt{};
+    const int cnt = pl.nmaps - first < 64 ? pl.nmaps - first : 64;
+    for (int t = 0; t < cnt; ++t) {
+      pt.p[t] = maps[first + t].p;
+      pt.tau[t] = maps[first + t].eps;
+    }
+    k_set_pt<<<1, 64, 0, st>>>(pt, pl.d_p, pl.d_tau, first, cnt);
+  }
+  ULP_CU(cudaGetLastError());
+  ULP_CU(launch_begin(pl, st));
+  const bool user_phi0 = pl.opt.phi0_mode == ULP_PHI0_USER;
+  for (int m = 0; m < pl.nmaps; ++m)
+    ULP_CU(launch_pack(pl, m, maps[m].psi, maps[m].mask, user_phi0 ? maps[m].phi : nullptr, st));
+  ULP_CU(launch_check(pl, st));
+  const PcgArgs a = pcg_args(pl, tol, max_inner);
+  for (int k = 0; k < max_outer; ++k) {
+    ULP_CU(launch_system(pl, pl.d_p, pl.d_tau, st));
+    cudaEvent_t e0, e1;
+    next_events(pl, &e0, &e1);
+    ULP_CU(launch_pcg64(pl, precond, a, st, e0, e1));
+    ULP_CU(launch_outer_error(pl, pl.opt.outer_tol, max_outer, st));
+  }
+  for (int m = 0; m < pl.nmaps; ++m) ULP_CU(launch_unpack(pl, m, maps[m].phi, st));
+  if (per_map) return collect(pl, st, per_map);
+  pl.last_status = ULP_OK;
+  return ULP_OK;
+}
+
+extern "C" int ulp_unwrap(ulp_plan plan, const double* psi, const uint8_t* mask, double p, double eps,
+                          int precond, double tol, int max_outer, int max_inner, double* phi,
+                          void* cuda_stream, ulp_stats* stats) {
+  if (!plan) return fail(ULP_ERR_INVALID, "null plan");
+  if (plan->p.nmaps != 1) return fail(ULP_ERR_INVALID, "batched plan: use ulp_unwrap_batched");
+  ulp_map mp{psi, mask, phi, p, eps};
+  return ulp_unwrap_batched(plan, &mp, precond, tol, max_outer, max_inner, cuda_stream, stats);
+}
+
+extern "C" int ulp_plan_counters(ulp_plan plan, int reset, ulp_counters* out) {
+  if (!plan || !out) return fail(ULP_ERR_INVALID, "null argument");
+  Plan& pl = plan->p;
+  ULP_CU(cudaSetDevice(pl.device));
+  out->kernel_launches = pl.kernel_launches;
+  out->solver_launches = pl.solver_launches;
+  out->solver_ms = 0.0;
+  out->timed_launches = (long long)(pl.ev_used / 2);
+  for (size_t k = 0; k + 1 < pl.ev_used; k += 2) {
+    ULP_CU(cudaEventSynchronize(pl.ev_pool[k + 1]));
+    float ms = 0.f;
+    ULP_CU(cudaEventElapsedTime(&ms, pl.ev_pool[k], pl.ev_pool[k + 1]));
+    out->solver_ms += ms;
+  }
+  if (reset) {
+    pl.kernel_launches = 0;
+    pl.solver_launches = 0;
+    pl.ev_used = 0;
+  }
+  return ULP_OK;
+}
+
+extern "C" int ulp_plan_last_status(ulp_plan plan, ulp_stats* stats) {
+  if (!plan) return fail(ULP_ERR_INVALID, "null plan");
+  Plan& pl = plan->p;
+  ULP_CU(cudaSetDevice(pl.device));
+  return collect(pl, pl.last_stream, stats);
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+extern "C" int unwrap_lp(const double* psi, int H, int W, double p, double eps, int precond, double tol,
+                         int max_outer, int max_inner, double* phi) {
+  if (!psi || !phi) return fail(ULP_ERR_INVALID, "null psi or phi");
+  if (H < 2 || W < 2) return fail(ULP_ERR_INVALID, "H=%d W=%d (need >= 2)", H, W);
+  ulp_options o;
+  ulp_options_default(&o);
+  o.outer_tol = 0.0;
+  ulp_plan plan = nullptr;
+  int rc = ulp_plan_create(H, W, &o, &plan);
+  if (rc != ULP_OK) return rc;
+  const bool dev_in = is_device_ptr(psi), dev_out = is_device_ptr(phi);
+  const size_t bytes = (size_t)H * W * sizeof(double);
+  double *dpsi = const_cast<double*>(psi), *dphi = phi;
+  if (!dev_in || !dev_out) {
+    cudaError_t e = cudaSuccess;
+    if (!dev_in) e = cudaMalloc(&dpsi, bytes);
+    if (e == cudaSuccess && !dev_out) e = cudaMalloc(&dphi, bytes);
+    if (e == cudaSuccess && !dev_in) e = cudaMemcpy(dpsi, psi, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      if (!dev_in && dpsi != psi) cudaFree(dpsi);
+      if (!dev_out && dphi != phi) cudaFree(dphi);
+      ulp_plan_destroy(plan);
+      return fail(ULP_ERR_CUDA, "staging: %s", cudaGetErrorString(e));
+    }
+  }
+  ulp_stats stats;
+  rc = ulp_unwrap(plan, dpsi, nullptr, p, eps, precond, tol, max_outer, max_inner, dphi, nullptr, &stats);
+  if (rc >= 0 && !dev_out) {
+    cudaError_t e = cudaMemcpy(phi, dphi, bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = fail(ULP_ERR_CUDA, "copy out: %s", cudaGetErrorString(e));
+  }
+  if (!dev_in) cudaFree(dpsi);
+  if (!dev_out) cudaFree(dphi);
+  ulp_plan_destroy(plan);
+  return rc;
+}
+
+// ------------------------------------------------------------------ single steps
+// Each builds a one-map workspace, runs the solver's own kernels, copies the
+// result back to the caller's contiguous array and releases the workspace.
+struct TempPlan {
+  ulp_plan plan = nullptr;
+  cudaStream_t st = nullptr;
+  ~TempPlan() {
+    if (plan) {
+      cudaStreamSynchronize(st);
+      ulp_plan_destroy(plan);
+    }
+  }
+};
+
+static int temp_plan(TempPlan& tp, int H, int W, const ulp_options* opt, void* stream) {
+  tp.st = static_cast<cudaStream_t>(stream);
+  return ulp_plan_create(H, W, opt, &tp.plan);
+}
+
+extern "C" int ulp_wrapped_diffs(const double* psi, int H, int W, double* dx, double* dy, void* stream) {
+  if (!psi || !dx || !dy) return fail(ULP_ERR_INVALID, "null argument");
+  TempPlan tp;
+  int rc = temp_plan(tp, H, W, nullptr, stream);
+  if (rc != ULP_OK) return rc;
+  Plan& pl = tp.plan->p;
+  ULP_CU(launch_begin(pl, tp.st));
+  ULP_CU(launch_pack(pl, 0, psi, nullptr, nullptr, tp.st));
+  ULP_CU(launch_from_plane(pl, pl.hmaps[0].f.dx, dx, tp.st));
+  ULP_CU(launch_from_plane(pl, pl.hmaps[0].f.dy, dy, tp.st));
+  ULP_CU(cudaStreamSynchronize(tp.st));
+  return ULP_OK;
+}
+
+extern "C" int ulp_weights(const double* phi, const double* dx, const double* dy, const uint8_t* mask,
+                           int H, int W, double p, double eps, double* U, double* V, double* b,
+                           void* stream) {
+  if (!phi || !dx || !dy || !U || !V) return fail(ULP_ERR_INVALID, "null argument");
+  if (!(p >= 0.0 && p <= 2.0) || !(eps > 0.0)) return fail(ULP_ERR_INVALID, "p or eps out of range");
+  TempPlan tp;
+  int rc = temp_plan(tp, H, W, nullptr, stream);
+  if (rc != ULP_OK) return rc;
+  Plan& pl = tp.plan->p;
+  const MapDesc& M = pl.hmaps[0];
+  PT pt{};
+  pt.p[0] = p;
+  pt.tau[0] = eps;
+  k_set_pt<<<1, 64, 0, tp.st>>>(pt, pl.d_p, pl.d_tau, 0, 1);
+  ULP_CU(launch_begin(pl, tp.st));
+  ULP_CU(launch_to_plane(pl, phi, M.f.phi, tp.st));
+  ULP_CU(launch_to_plane(pl, dx, M.f.dx, tp.st));
+  ULP_CU(launch_to_plane(pl, dy, M.f.dy, tp.st));
+  ULP_CU(launch_mask_to_plane(pl, mask, tp.st));
+  ULP_CU(launch_system(pl, pl.d_p, pl.d_tau, tp.st));
+  ULP_CU(launch_from_plane(pl, M.f.U, U, tp.st));
+  ULP_CU(launch_from_plane(pl, M.f.V, V, tp.st));
+  if (b) ULP_CU(launch_from_plane(pl, M.f.b, b, tp.st));
+  ULP_CU(cudaStreamSynchronize(tp.st));
+  return ULP_OK;
+}
+
+// Loads caller weights U, V into a temporary plan and forms D, D^-1 (b = 0).
+static int load_weights(Plan& pl, const double* U, const double* V, cudaStream_t st) {
+  const MapDesc& M = pl.hmaps[0];
+  ULP_CU(launch_begin(pl, st));
+  ULP_CU(launch_to_plane(pl, U, M.f.U, st));
+  ULP_CU(launch_to_plane(pl, V, M.f.V, st));
+  ULP_CU(launch_diag(pl, st));
+  return ULP_OK;
+}
+
+extern "C" int ulp_matvec(const double* U, const double* V, const double* x, int H, int W, double* y,
+                          void* stream) {
+  if (!U || !V || !x || !y) return fail(ULP_ERR_INVALID, "null argument");
+  TempPlan tp;
+  int rc = temp_plan(tp, H, W, nullptr, stream);
+  if (rc != ULP_OK) return rc;
+  Plan& pl = tp.plan->p;
+  const MapDesc& M = pl.hmaps[0];
+  rc = load_weights(pl, U, V, tp.st);
+  if (rc != ULP_OK) return rc;
+  ULP_CU(launch_to_plane(pl, x, M.f.r, tp.st));
+  ULP_CU(launch_matvec(pl, M.f.r, M.f.q, tp.st));
+  ULP_CU(launch_from_plane(pl, M.f.q, y, tp.st));
+  ULP_CU(cudaStreamSynchronize(tp.st));
+  return ULP_OK;
+}
+
+extern "C" int ulp_precond_apply(int precond, const double* U, const double* V, const uint8_t* mask,
+                                 int H, int W, double omega, const double* r, double* s, void* stream) {
+  if (!U || !V || !r || !s) return fail(ULP_ERR_INVALID, "null argument");
+  int rc = check_solver_args(precond, 1.0, 1);
+  if (rc != ULP_OK) return rc;
+  (void)mask;
+  (void)omega;
+  TempPlan tp;
+  rc = temp_plan(tp, H, W, nullptr, stream);
+  if (rc != ULP_OK) return rc;
+  Plan& pl = tp.plan->p;
+  const MapDesc& M = pl.hmaps[0];
+  rc = load_weights(pl, U, V, tp.st);
+  if (rc != ULP_OK) return rc;
+  ULP_CU(launch_to_plane(pl, r, M.f.r, tp.st));
+  ULP_CU(launch_jacobi_apply(pl, precond, M.f.r, M.f.s, tp.st));
+  ULP_CU(launch_from_plane(pl, M.f.s, s, tp.st));
+  ULP_CU(cudaStreamSynchronize(tp.st));
+  return ULP_OK;
+}
+
+extern "C" int ulp_pcg(const double* U, const double* V, const double* b, int H, int W, int precond,
+                       double tol, int max_inner, const ulp_options* opt, double* phi, void* stream,
+                       ulp_stats* stats) {
+  if (!U || !V || !b || !phi) return fail(ULP_ERR_INVALID, "null argument");
+  int rc = check_solver_args(precond, tol, 1);
+  if (rc != ULP_OK) return rc;
+  TempPlan tp;
+  rc = temp_plan(tp, H, W, opt, stream);
+  if (rc != ULP_OK) return rc;
+  Plan& pl = tp.plan->p;
+  const MapDesc& M = pl.hmaps[0];
+  rc = load_weights(pl, U, V, tp.st);
+  if (rc != ULP_OK) return rc;
+  ULP_CU(launch_to_plane(pl, b, M.f.b, tp.st));
+  ULP_CU(launch_to_plane(pl, phi, M.f.phi, tp.st));
+  ULP_CU(launch_pcg64(pl, precond, pcg_args(pl, tol, max_inner), tp.st, nullptr, nullptr));
+  ULP_CU(launch_outer_error(pl, 0.0, 1, tp.st));
+  ULP_CU(launch_from_plane(pl, M.f.phi, phi, tp.st));
+  if (stats) return collect(pl, tp.st, stats);
+  ULP_CU(cudaStreamSynchronize(tp.st));
+  return ULP_OK;
+}

@@ -1,0 +1,727 @@
+// ulp_fp64.cu -- FP64 kernels of Algorithm 1 (arXiv 2203.13675):
+//   wrapped differences (Sec. 2.1), weights (Eq. UV), system (Eq. Axb),
+//   the persistent PCG engine (Algorithm 1 inner loop) for M = I and
+//   M = diag(A), the outer error (Algorithm 1), and single-step kernels.
+#include "ulp_internal.cuh"
+#include "ulp_host.h"
+
+#include <math.h>
+
+namespace ulp {
+
+// ------------------------------------------------------------------ pack
+// Sec. 2.1: Delta^x = W(psi_{i,j+1} - psi_{i,j}) (j <= W-2), Delta^y likewise
+// along i; ghost entries 0.  Also copies the mask and phi^0 into the padded
+// planes and checks that psi is finite.
+__global__ void k_pack(MapDesc M, MapState* S, const double* __restrict__ psi,
+                       const uint8_t* __restrict__ mask, const double* __restrict__ phi0) {
+  const size_t n = (size_t)M.H * M.pitch;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / M.pitch), j = (int)(t % M.pitch);
+    double dx = 0.0, dy = 0.0, ph = 0.0;
+    uint8_t mk = 0;
+    if (j < M.W) {
+      const size_t k = (size_t)i * M.W + j;
+      const double c = psi[k];
+      if (!isfinite(c)) atomicExch(&S->err_flag, 1);
+      if (j + 1 < M.W) dx = wrap_pv(__dsub_rn(psi[k + 1], c));
+      if (i + 1 < M.H) dy = wrap_pv(__dsub_rn(psi[k + M.W], c));
+      if (mask) mk = mask[k] ? 1 : 0;
+      if (phi0) ph = phi0[k];
+    }
+    M.f.dx[t] = dx;
+    M.f.dy[t] = dy;
+    M.f.mask[t] = mk;
+    M.f.phi[t] = ph;
+  }
+}
+
+__global__ void k_unpack(MapDesc M, double* __restrict__ phi) {
+  const size_t n = (size_t)M.H * M.W;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(k / M.W), j = (int)(k % M.W);
+    phi[k] = M.f.phi[(size_t)i * M.pitch + j];
+  }
+}
+
+// ------------------------------------------------------------------ weights
+// Eq. (UV): w(e) = tau / (|e|^(2-p) + tau), with the exponent specialised for
+// p in {0, 1, 2}.  Zero on edges leaving the grid or touching a masked pixel.
+__device__ __forceinline__ double irls_weight(double e, double p, double tau, int pcase) {
+  const double a = fabs(e);
+  double t;
+  switch (pcase) {
+    case 2: t = 1.0; break;                 // p = 2: |e|^0 = 1
+    case 1: t = a; break;                   // p = 1
+    case 0: t = __dmul_rn(a, a); break;     // p = 0
+    default: t = pow(a, 2.0 - p); break;
+  }
+  return __ddiv_rn(tau, __dadd_rn(t, tau));
+}
+
+__device__ __forceinline__ int p_case(double p) {
+  return (p == 2.0) ? 2 : (p == 1.0) ? 1 : (p == 0.0) ? 0 : -1;
+}
+
+// One outer pass, first half: U, V from phi^k, and phi_prev = phi^k.
+__global__ void k_weights(const MapDesc* __restrict__ maps, MapState* S, const double* __restrict__ pv,
+                          const double* __restrict__ tauv) {
+  const int m = blockIdx.y;
+  const MapDesc& M = maps[m];
+  if (!S[m].outer_active) return;
+  const double p = pv[m], tau = tauv[m];
+  const int pc = p_case(p);
+  const size_t n = (size_t)M.H * M.pitch;
+  const size_t P = M.pitch;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / P), j = (int)(t % P);
+    const double ph = M.f.phi[t];
+    const bool mk = M.f.mask[t] != 0;
+    double u = 0.0, v = 0.0;
+    if (j + 1 < M.W && !mk && !M.f.mask[t + 1]) {
+      const double e = __dsub_rn(__dsub_rn(M.f.phi[t + 1], ph), M.f.dx[t]);
+      u = irls_weight(e, p, tau, pc);
+    }
+    if (j < M.W && i + 1 < M.H && !mk && !M.f.mask[t + P]) {
+      const double e = __dsub_rn(__dsub_rn(M.f.phi[t + P], ph), M.f.dy[t]);
+      v = irls_weight(e, p, tau, pc);
+    }
+    M.f.U[t] = u;
+    M.f.V[t] = v;
+    M.f.phi_prev[t] = ph;
+  }
+}
+
+// One outer pass, second half: diagonal D, its guarded inverse, and b (Eq. Axb),
+// summed in the order the equation writes them.
+__global__ void k_system(const MapDesc* __restrict__ maps, MapState* S) {
+  const int m = blockIdx.y;
+  const MapDesc& M = maps[m];
+  if (!S[m].outer_active) return;
+  const size_t n = (size_t)M.H * M.pitch;
+  const size_t P = M.pitch;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / P), j = (int)(t % P);
+    const double uw = (j > 0) ? M.f.U[t - 1] : 0.0;
+    const double ue = M.f.U[t];
+    const double vn = (i > 0) ? M.f.V[t - P] : 0.0;
+    const double vs = M.f.V[t];
+    const double d = __dadd_rn(__dadd_rn(__dadd_rn(uw, ue), vn), vs);
+    double bk = 0.0;
+    if (j > 0) bk = __dadd_rn(bk, __dmul_rn(M.f.dx[t - 1], uw));
+    bk = __dsub_rn(bk, __dmul_rn(M.f.dx[t], ue));
+    if (i > 0) bk = __dadd_rn(bk, __dmul_rn(M.f.dy[t - P], vn));
+    bk = __dsub_rn(bk, __dmul_rn(M.f.dy[t], vs));
+    M.f.D[t] = d;
+    M.f.Dinv[t] = (d > 0.0) ? __drcp_rn(d) : 0.0;
+    M.f.b[t] = bk;
+  }
+}
+
+// ------------------------------------------------------------------ stencil walker
+// Sliding-window 5-point stencil over one warp tile (64 columns x rows i0..i1-1):
+// each lane owns columns j, j+1; north/south neighbours come from the window,
+// east/west from the neighbouring lanes, the two tile-edge columns from a halo
+// load by lanes 0 and 31.  X supplies the vector being multiplied:
+// X::row(i, j) -> values at (i, j), (i, j+1); X::at(i, c) -> value at (i, c).
+template <class X, class Epi>
+__device__ __forceinline__ void stencil_tile(const MapDesc& M, int i0, int i1, int j0, int lane,
+                                             const double* U, const double* V, const double* D,
+                                             const X& x, Epi& epi) {
+  const int j = j0 + 2 * lane;
+  const bool hw = (lane == 0) && (j0 > 0);
+  const bool he = (lane == 31) && (j0 + kStrip < M.pitch);
+  const int hc = (lane == 0) ? j0 - 1 : j0 + kStrip;
+  const size_t P = (size_t)M.pitch;
+  double2 xn = make_double2(0.0, 0.0), vn = make_double2(0.0, 0.0);
+  if (i0 > 0) {
+    xn = x.row(i0 - 1, j);
+    vn = ld2(V, (size_t)(i0 - 1) * P + j);
+  }
+  double2 xc = x.row(i0, j);
+  for (int i = i0; i < i1; ++i) {
+    const size_t off = (size_t)i * P + j;
+    double2 xs = make_double2(0.0, 0.0);
+    if (i + 1 < M.H) xs = x.row(i + 1, j);
+    const double2 u = ld2(U, off), v = ld2(V, off), dd = ld2(D, off);
+    double h = 0.0, uwh = 0.0;
+    if (hw || he) h = x.at(i, hc);
+    if (hw) uwh = ld1(U, (size_t)i * P + hc);
+    double west = __shfl_up_sync(kFull, xc.y, 1);
+    double east = __shfl_down_sync(kFull, xc.x, 1);
+    double uw = __shfl_up_sync(kFull, u.y, 1);
+    if (lane == 0) { west = h; uw = uwh; }
+    if (lane == 31) east = h;
+    double2 ax;
+    ax.x = dd.x * xc.x;
+    ax.x = fma(-u.x, xc.y, ax.x);
+    ax.x = fma(-uw, west, ax.x);
+    ax.x = fma(-v.x, xs.x, ax.x);
+    ax.x = fma(-vn.x, xn.x, ax.x);
+    ax.y = dd.y * xc.y;
+    ax.y = fma(-u.y, east, ax.y);
+    ax.y = fma(-u.x, xc.x, ax.y);
+    ax.y = fma(-v.y, xs.y, ax.y);
+    ax.y = fma(-vn.y, xn.y, ax.y);
+    epi(off, xc, ax);
+    xn = xc;
+    xc = xs;
+    vn = v;
+  }
+}
+
+struct XPlane {  // plain vector
+  const double* x;
+  size_t P;
+  __device__ __forceinline__ double2 row(int i, int j) const { return ld2(x, (size_t)i * P + j); }
+  __device__ __forceinline__ double at(int i, int c) const { return ld1(x, (size_t)i * P + c); }
+};
+
+struct XDir {  // d = s + beta d_old, or d = s on the first iteration (Algorithm 1)
+  const double* s;
+  const double* dold;
+  double beta;
+  bool first;
+  size_t P;
+  __device__ __forceinline__ double2 row(int i, int j) const {
+    const size_t off = (size_t)i * P + j;
+    const double2 sv = ld2(s, off);
+    if (first) return sv;
+    const double2 dv = ld2(dold, off);
+    return make_double2(fma(beta, dv.x, sv.x), fma(beta, dv.y, sv.y));
+  }
+  __device__ __forceinline__ double at(int i, int c) const {
+    const size_t off = (size_t)i * P + c;
+    const double sv = ld1(s, off);
+    return first ? sv : fma(beta, ld1(dold, off), sv);
+  }
+};
+
+struct TileGeo {
+  int i0, i1, j0;
+};
+__device__ __forceinline__ TileGeo tile_geo(const MapDesc& M, int t, int R) {
+  const int lt = t - M.tile_base;
+  const int sy = lt / M.nsx, sx = lt - sy * M.nsx;
+  TileGeo g;
+  g.i0 = sy * R;
+  g.i1 = min(g.i0 + R, M.H);
+  g.j0 = sx * kStrip;
+  return g;
+}
+
+// ------------------------------------------------------------------ PCG engine
+enum Phase { kPhResInit = 0, kPhA = 1, kPhB = 2, kPhRes = 3 };
+
+// Runs in the warp whose tile arrival completed phase `ph` for map m: reduces
+// the map's tile partials in a fixed order and advances its scalars
+// (alpha = delta_new / d^T q; delta_old, delta_new, beta; stop tests).
+__device__ void finish_map(const PcgArgs& a, const MapDesc& M, MapState* Sp, int ph, int lane) {
+  volatile MapState* S = Sp;
+  const int base = M.tile_base, n = M.ntiles;
+  const double v0 = warp_sum_partials(a.P0 + base, n, lane);
+  double v1 = 0.0, v2 = 0.0;
+  if (ph != kPhA) v1 = warp_sum_partials(a.P1 + base, n, lane);
+  if (ph == kPhResInit) v2 = warp_sum_partials(a.P2 + base, n, lane);
+  if (lane == 0) {
+    bool done = false;
+    if (ph == kPhA) {
+      S->dq = v0;
+      if (!(v0 > 0.0) || !isfinite(v0)) {  // breakdown: stop after this iteration
+        S->status = -3;
+        S->alpha = 0.0;
+        S->stop_after = 1;
+      } else {
+        S->alpha = S->delta / v0;
+      }
+    } else {
+      if (ph == kPhResInit) {
+        S->delta = v0;
+        S->delta0 = v0;
+        S->rr = v1;
+        S->bb = v2;
+        S->iter = 0;
+      } else {
+        const double dold = S->delta;
+        S->delta = v0;
+        S->rr = v1;
+        S->beta = v0 / dold;
+        S->iter += 1;
+      }
+      const double tol2 = a.tol2;
+      const bool conv = (a.stop_mode == 1) ? !(S->delta > tol2 * S->delta0) : !(S->rr > tol2 * S->bb);
+      S->relres = (S->bb > 0.0) ? sqrt(S->rr / S->bb) : 0.0;
+      if (S->stop_after) {
+        done = true;
+      } else if (S->bb == 0.0 || conv) {
+        done = true;
+        S->status = 0;
+      } else if (S->iter >= (a.lmax > 0 ? a.lmax : 2LL * M.H * M.W)) {
+        done = true;
+        S->status = 1;
+      }
+    }
+    S->arrive = 0u;
+    if (done) {
+      S->done = 1;
+      __threadfence();
+      atomicSub(a.n_active, 1);
+    }
+    __threadfence();
+  }
+  __syncwarp();
+}
+
+// Publishes this warp's tile partials and runs the map's finisher if this was
+// the last tile of the map in this phase.
+__device__ __forceinline__ void tile_arrive(const PcgArgs& a, const MapDesc& M, MapState* S, int t,
+                                            int ph, double v0, double v1, double v2, int lane) {
+  v0 = warp_sum(v0);
+  if (ph != kPhA) v1 = warp_sum(v1);
+  if (ph == kPhResInit) v2 = warp_sum(v2);
+  unsigned old = 0;
+  if (lane == 0) {
+    __stcg(a.P0 + t, v0);
+    if (ph != kPhA) __stcg(a.P1 + t, v1);
+    if (ph == kPhResInit) __stcg(a.P2 + t, v2);
+    __threadfence();
+    old = atomicAdd(&S->arrive, 1u);
+  }
+  old = __shfl_sync(kFull, old, 0);
+  if (old == (unsigned)M.ntiles - 1u) {
+    __threadfence();
+    finish_map(a, M, S, ph, lane);
+  }
+}
+
+// r = b - A phi, s = M^{-1} r, partials r^T s, r^T r (and b^T b at the start).
+template <int KIND>
+__device__ __forceinline__ void res_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t,
+                                         bool init, int lane) {
+  const TileGeo g = tile_geo(M, t, a.R);
+  const size_t P = M.pitch;
+  XPlane x{M.f.phi, P};
+  double rs = 0.0, rr = 0.0, bb = 0.0;
+  auto epi = [&](size_t off, double2 xc, double2 ax) {
+    const double2 bv = ld2(M.f.b, off);
+    double2 r = make_double2(bv.x - ax.x, bv.y - ax.y);
+    st2(M.f.r, off, r);
+    if (KIND == kJacobi) {
+      const double2 di = ld2(M.f.Dinv, off);
+      const double2 s = make_double2(di.x * r.x, di.y * r.y);
+      st2(M.f.s, off, s);
+      rs = fma(r.x, s.x, rs);
+      rs = fma(r.y, s.y, rs);
+    }
+    rr = fma(r.x, r.x, rr);
+    rr = fma(r.y, r.y, rr);
+    if (init) {
+      bb = fma(bv.x, bv.x, bb);
+      bb = fma(bv.y, bv.y, bb);
+    }
+  };
+  stencil_tile(M, g.i0, g.i1, g.j0, lane, M.f.U, M.f.V, M.f.D, x, epi);
+  if (KIND == kIdentity) rs = rr;
+  tile_arrive(a, M, S, t, init ? kPhResInit : kPhRes, rs, rr, bb, lane);
+}
+
+// d = s + beta d_old, q = A d, partial d^T q (Algorithm 1: q <- A d, d^T q).
+template <int KIND>
+__device__ __forceinline__ void a_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t, int lane) {
+  const TileGeo g = tile_geo(M, t, a.R);
+  const size_t P = M.pitch;
+  const long long it = *(volatile long long*)&S->iter;
+  const double* sv = (KIND == kIdentity) ? M.f.r : M.f.s;
+  const double* dold = (it & 1) ? M.f.d1 : M.f.d0;
+  double* dnew = (it & 1) ? M.f.d0 : M.f.d1;
+  XDir x{sv, dold, *(volatile double*)&S->beta, it == 0, P};
+  double dq = 0.0;
+  auto epi = [&](size_t off, double2 xc, double2 ax) {
+    st2(dnew, off, xc);
+    st2(M.f.q, off, ax);
+    dq = fma(xc.x, ax.x, dq);
+    dq = fma(xc.y, ax.y, dq);
+  };
+  stencil_tile(M, g.i0, g.i1, g.j0, lane, M.f.U, M.f.V, M.f.D, x, epi);
+  tile_arrive(a, M, S, t, kPhA, dq, 0.0, 0.0, lane);
+}
+
+// phi += alpha d; r -= alpha q; s = M^{-1} r; partials r^T s, r^T r.
+// On a refresh iteration only phi is updated (the residual is recomputed).
+template <int KIND>
+__device__ __forceinline__ void b_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t,
+                                       bool refresh, int lane) {
+  const TileGeo g = tile_geo(M, t, a.R);
+  const size_t P = M.pitch;
+  const long long it = *(volatile long long*)&S->iter;
+  const double* d = (it & 1) ? M.f.d0 : M.f.d1;
+  const double alpha = *(volatile double*)&S->alpha;
+  const int j = g.j0 + 2 * lane;
+  double rs = 0.0, rr = 0.0;
+  for (int i = g.i0; i < g.i1; ++i) {
+    const size_t off = (size_t)i * P + j;
+    const double2 dv = ld2(d, off);
+    double2 ph = ld2(M.f.phi, off);
+    ph.x = fma(alpha, dv.x, ph.x);
+    ph.y = fma(alpha, dv.y, ph.y);
+    st2(M.f.phi, off, ph);
+    if (!refresh) {
+      const double2 qv = ld2(M.f.q, off);
+      double2 r = ld2(M.f.r, off);
+      r.x = fma(-alpha, qv.x, r.x);
+      r.y = fma(-alpha, qv.y, r.y);
+      st2(M.f.r, off, r);
+      if (KIND == kJacobi) {
+        const double2 di = ld2(M.f.Dinv, off);
+        const double2 s = make_double2(di.x * r.x, di.y * r.y);
+        st2(M.f.s, off, s);
+        rs = fma(r.x, s.x, rs);
+        rs = fma(r.y, s.y, rs);
+      }
+      rr = fma(r.x, r.x, rr);
+      rr = fma(r.y, r.y, rr);
+    }
+  }
+  if (!refresh) {
+    if (KIND == kIdentity) rs = rr;
+    tile_arrive(a, M, S, t, kPhB, rs, rr, 0.0, lane);
+  }
+}
+
+// The inner PCG of Algorithm 1 for every map of the call, as one persistent
+// cooperative kernel: phases separated by grid barriers, per-map scalars
+// advanced by the last warp of each phase.  Maps that converge drop out.
+template <int KIND>
+__global__ void __launch_bounds__(kThreads, 2) k_pcg64(PcgArgs a) {
+  __shared__ int s_base[kMaxMaps + 1];
+  __shared__ int s_any;
+  for (int m = threadIdx.x; m <= a.nmaps; m += blockDim.x)
+    s_base[m] = (m < a.nmaps) ? a.maps[m].tile_base : a.ntiles;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int NW = gridDim.x * kWarps;
+
+  for (int t = gw; t < a.ntiles; t += NW) {
+    const int m = find_map(s_base, a.nmaps, t);
+    MapState* S = a.st + m;
+    if (*(volatile int*)&S->done) continue;
+    res_tile<KIND>(a, a.maps[m], S, t, true, lane);
+  }
+  if (!grid_sync(a.bar, a.timeout_ns)) return;
+
+  for (int g = 0;; ++g) {
+    if (*(volatile int*)a.n_active == 0) break;
+    for (int t = gw; t < a.ntiles; t += NW) {
+      const int m = find_map(s_base, a.nmaps, t);
+      MapState* S = a.st + m;
+      if (*(volatile int*)&S->done) continue;
+      a_tile<KIND>(a, a.maps[m], S, t, lane);
+    }
+    if (!grid_sync(a.bar, a.timeout_ns)) return;
+    // refresh iterations (l mod period = 0) are a static function of g
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    for (int m = threadIdx.x; m < a.nmaps; m += blockDim.x)
+      if (g % a.maps[m].refresh == 0) s_any = 1;
+    __syncthreads();
+    const bool any_refresh = s_any != 0;
+    for (int t = gw; t < a.ntiles; t += NW) {
+      const int m = find_map(s_base, a.nmaps, t);
+      MapState* S = a.st + m;
+      if (*(volatile int*)&S->done) continue;
+      const MapDesc& M = a.maps[m];
+      b_tile<KIND>(a, M, S, t, (g % M.refresh) == 0, lane);
+    }
+    if (!grid_sync(a.bar, a.timeout_ns)) return;
+    if (any_refresh) {
+      for (int t = gw; t < a.ntiles; t += NW) {
+        const int m = find_map(s_base, a.nmaps, t);
+        MapState* S = a.st + m;
+        const MapDesc& M = a.maps[m];
+        if (*(volatile int*)&S->done || (g % M.refresh) != 0) continue;
+        res_tile<KIND>(a, M, S, t, false, lane);
+      }
+      if (!grid_sync(a.bar, a.timeout_ns)) return;
+    }
+  }
+}
+
+// Resets the per-map solver state before a PCG launch.
+__global__ void k_pcg_reset(MapState* S, int nmaps, int* n_active, Barrier* bar) {
+  __shared__ int s_cnt;
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  for (int m = threadIdx.x; m < nmaps; m += blockDim.x) {
+    MapState* s = S + m;
+    const int act = s->outer_active;
+    s->delta = s->delta0 = s->rr = s->bb = s->dq = s->alpha = s->beta = s->relres = 0.0;
+    s->iter = 0;
+    s->status = 0;
+    s->done = act ? 0 : 1;
+    s->stop_after = 0;
+    s->arrive = 0u;
+    if (act) atomicAdd(&s_cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *n_active = s_cnt;
+    bar->count = 0u;
+    bar->err = 0;
+    __threadfence();
+  }
+}
+
+// ------------------------------------------------------------------ outer error
+// Algorithm 1: error = ||phi^{k+1} - phi^k|| / ||phi^k|| (infinite when
+// ||phi^k|| = 0); records the pass in the map's statistics and decides
+// whether the next pass runs.
+__global__ void k_outer_error(const MapDesc* __restrict__ maps, MapState* S, MapStats* stats,
+                              double* part, int nbx, double outer_tol, int max_outer, int* bar_err) {
+  const int m = blockIdx.y;
+  const MapDesc& M = maps[m];
+  MapState* s = S + m;
+  if (!s->outer_active) return;
+  const size_t n = (size_t)M.H * M.pitch;
+  double num = 0.0, den = 0.0;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const double e = M.f.phi[t] - M.f.phi_prev[t];
+    num = fma(e, e, num);
+    den = fma(M.f.phi_prev[t], M.f.phi_prev[t], den);
+  }
+  __shared__ double sn[kWarps], sd[kWarps];
+  num = warp_sum(num);
+  den = warp_sum(den);
+  if ((threadIdx.x & 31) == 0) {
+    sn[threadIdx.x >> 5] = num;
+    sd[threadIdx.x >> 5] = den;
+  }
+  __syncthreads();
+  __shared__ unsigned s_old;
+  double* pn = part + (size_t)m * nbx * 2;   // nbx numerators, then nbx denominators
+  double* pd = pn + nbx;
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sn[w]; b += sd[w]; }
+    pn[blockIdx.x] = a;
+    pd[blockIdx.x] = b;
+    __threadfence();
+    s_old = atomicAdd(&s->arrive_outer, 1u);
+  }
+  __syncthreads();
+  if (s_old != (unsigned)gridDim.x - 1u || threadIdx.x >= 32) return;
+  __threadfence();
+  const double a = warp_sum_partials(pn, gridDim.x, threadIdx.x);
+  const double b = warp_sum_partials(pd, gridDim.x, threadIdx.x);
+  if (threadIdx.x != 0) return;
+  const double err = (b > 0.0) ? sqrt(a) / sqrt(b) : INFINITY;
+  MapStats* st = stats + m;
+  const int k = s->outer_k;
+  if (k < 64) {
+    st->inner[k] = s->iter;
+    st->relres[k] = s->relres;
+    st->outer_err[k] = err;
+  }
+  st->inner_total += s->iter;
+  int status = s->status;
+  if (*(volatile int*)bar_err) status = -4;
+  if (status < 0) st->status = status;
+  else if (status == 1 && st->status == 0) st->status = 1;
+  st->outer = k + 1;
+  s->outer_err = err;
+  s->outer_k = k + 1;
+  s->arrive_outer = 0u;
+  s->outer_active = (status >= 0 && err > outer_tol && k + 1 < max_outer) ? 1 : 0;
+  __threadfence();
+}
+
+// Starts a call: statistics cleared, every map active unless its input failed the checks.
+__global__ void k_begin(MapState* S, MapStats* stats, int nmaps) {
+  for (int m = threadIdx.x; m < nmaps; m += blockDim.x) {
+    MapState* s = S + m;
+    MapStats* st = stats + m;
+    st->status = 0;
+    st->outer = 0;
+    st->inner_total = 0;
+    for (int k = 0; k < 64; ++k) { st->inner[k] = 0; st->relres[k] = 0.0; st->outer_err[k] = 0.0; }
+    s->outer_k = 0;
+    s->arrive_outer = 0u;
+    s->err_flag = 0;
+    s->outer_active = 1;
+  }
+}
+
+__global__ void k_check_input(MapState* S, MapStats* stats, int nmaps) {
+  for (int m = threadIdx.x; m < nmaps; m += blockDim.x) {
+    if (S[m].err_flag) {
+      S[m].outer_active = 0;
+      stats[m].status = -1;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ single steps
+// y = A x on one map, with the solver's stencil walker.
+__global__ void __launch_bounds__(kThreads) k_matvec(MapDesc M, const double* __restrict__ xin, double* y, int R) {
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int NW = gridDim.x * kWarps;
+  for (int t = gw; t < M.ntiles; t += NW) {
+    const TileGeo g = tile_geo(M, t + M.tile_base, R);
+    XPlane x{xin, (size_t)M.pitch};
+    auto epi = [&](size_t off, double2, double2 ax) { st2(y, off, ax); };
+    stencil_tile(M, g.i0, g.i1, g.j0, lane, M.f.U, M.f.V, M.f.D, x, epi);
+  }
+}
+
+__global__ void k_jacobi_apply(MapDesc M, const double* __restrict__ r, double* s, int kind) {
+  const size_t n = (size_t)M.H * M.pitch;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    s[t] = (kind == kJacobi) ? M.f.Dinv[t] * r[t] : r[t];
+}
+
+// Copies a user-layout H x W array into a padded plane (zero padding) and back.
+__global__ void k_to_plane(MapDesc M, const double* __restrict__ src, double* dst) {
+  const size_t n = (size_t)M.H * M.pitch;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / M.pitch), j = (int)(t % M.pitch);
+    dst[t] = (j < M.W) ? src[(size_t)i * M.W + j] : 0.0;
+  }
+}
+__global__ void k_from_plane(MapDesc M, const double* __restrict__ src, double* dst) {
+  const size_t n = (size_t)M.H * M.W;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(k / M.W), j = (int)(k % M.W);
+    dst[k] = src[(size_t)i * M.pitch + j];
+  }
+}
+__global__ void k_mask_to_plane(MapDesc M, const uint8_t* __restrict__ src) {
+  const size_t n = (size_t)M.H * M.pitch;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / M.pitch), j = (int)(t % M.pitch);
+    M.f.mask[t] = (j < M.W && src) ? (src[(size_t)i * M.W + j] ? 1 : 0) : 0;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+static int grid_for(size_t n, int nsm) {
+  size_t b = (n + kThreads - 1) / kThreads;
+  size_t cap = (size_t)nsm * 8;
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+cudaError_t launch_pack(const Plan& pl, int m, const double* psi, const uint8_t* mask, const double* phi0,
+                        cudaStream_t st) {
+  const MapDesc& M = pl.hmaps[m];
+  pl.kernel_launches += 1;
+  k_pack<<<grid_for((size_t)M.H * M.pitch, pl.nsm), kThreads, 0, st>>>(M, pl.dstate + m, psi, mask, phi0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const Plan& pl, int m, double* phi, cudaStream_t st) {
+  const MapDesc& M = pl.hmaps[m];
+  pl.kernel_launches += 1;
+  k_unpack<<<grid_for((size_t)M.H * M.W, pl.nsm), kThreads, 0, st>>>(M, phi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_begin(const Plan& pl, cudaStream_t st) {
+  pl.kernel_launches += 1;
+  k_begin<<<1, kThreads, 0, st>>>(pl.dstate, pl.dstats, pl.nmaps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check(const Plan& pl, cudaStream_t st) {
+  pl.kernel_launches += 1;
+  k_check_input<<<1, kThreads, 0, st>>>(pl.dstate, pl.dstats, pl.nmaps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const Plan& pl, cudaStream_t st) {
+  dim3 grid(pl.bx_elem, pl.nmaps);
+  pl.kernel_launches += 1;
+  k_system<<<grid, kThreads, 0, st>>>(pl.dmaps, pl.dstate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_system(const Plan& pl, const double* d_p, const double* d_tau, cudaStream_t st) {
+  dim3 grid(pl.bx_elem, pl.nmaps);
+  pl.kernel_launches += 2;
+  k_weights<<<grid, kThreads, 0, st>>>(pl.dmaps, pl.dstate, d_p, d_tau);
+  k_system<<<grid, kThreads, 0, st>>>(pl.dmaps, pl.dstate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_outer_error(const Plan& pl, double outer_tol, int max_outer, cudaStream_t st) {
+  dim3 grid(pl.bx_elem, pl.nmaps);
+  pl.kernel_launches += 1;
+  k_outer_error<<<grid, kThreads, 0, st>>>(pl.dmaps, pl.dstate, pl.dstats, pl.outer_part, pl.bx_elem,
+                                           outer_tol, max_outer, &pl.bar->err);
+  return cudaGetLastError();
+}
+
+template <int KIND>
+static cudaError_t launch_pcg64_kind(const Plan& pl, const PcgArgs& a, int blocks, cudaStream_t st) {
+  void* args[] = {(void*)&a};
+  return cudaLaunchCooperativeKernel((void*)k_pcg64<KIND>, blocks, kThreads, args, 0, st);
+}
+
+int pcg64_max_blocks_per_sm(int kind) {
+  int nb = 0;
+  if (kind == kIdentity) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg64<kIdentity>, kThreads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg64<kJacobi>, kThreads, 0);
+  return nb;
+}
+
+cudaError_t launch_pcg64(const Plan& pl, int kind, const PcgArgs& a, cudaStream_t st, cudaEvent_t e0,
+                         cudaEvent_t e1) {
+  pl.kernel_launches += 2;
+  pl.solver_launches += 1;
+  k_pcg_reset<<<1, kThreads, 0, st>>>(pl.dstate, pl.nmaps, pl.n_active, pl.bar);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (e0) cudaEventRecord(e0, st);
+  const int blocks = pl.nsm * pl.bps;
+  e = (kind == kIdentity) ? launch_pcg64_kind<kIdentity>(pl, a, blocks, st)
+                          : launch_pcg64_kind<kJacobi>(pl, a, blocks, st);
+  if (e == cudaSuccess && e1) e = cudaEventRecord(e1, st);
+  return e;
+}
+
+cudaError_t launch_matvec(const Plan& pl, const double* x, double* y, cudaStream_t st) {
+  const MapDesc& M = pl.hmaps[0];
+  const int blocks = (M.ntiles + kWarps - 1) / kWarps;
+  pl.kernel_launches += 1;
+  k_matvec<<<blocks, kThreads, 0, st>>>(M, x, y, pl.R);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi_apply(const Plan& pl, int kind, const double* r, double* s, cudaStream_t st) {
+  const MapDesc& M = pl.hmaps[0];
+  pl.kernel_launches += 1;
+  k_jacobi_apply<<<grid_for((size_t)M.H * M.pitch, pl.nsm), kThreads, 0, st>>>(M, r, s, kind);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_plane(const Plan& pl, const double* src, double* dst, cudaStream_t st) {
+  const MapDesc& M = pl.hmaps[0];
+  pl.kernel_launches += 1;
+  k_to_plane<<<grid_for((size_t)M.H * M.pitch, pl.nsm), kThreads, 0, st>>>(M, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_plane(const Plan& pl, const double* src, double* dst, cudaStream_t st) {
+  const MapDesc& M = pl.hmaps[0];
+  pl.kernel_launches += 1;
+  k_from_plane<<<grid_for((size_t)M.H * M.W, pl.nsm), kThreads, 0, st>>>(M, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask_to_plane(const Plan& pl, const uint8_t* mask, cudaStream_t st) {
+  const MapDesc& M = pl.hmaps[0];
+  pl.kernel_launches += 1;
+  k_mask_to_plane<<<grid_for((size_t)M.H * M.pitch, pl.nsm), kThreads, 0, st>>>(M, mask);
+  return cudaGetLastError();
+}
+
+}  // namespace ulp

@@ -1,0 +1,58 @@
+// ulp_host.h -- host-side plan of the GB300 L^p phase-unwrapping library and
+// the launchers each kernel file exports to the C ABI layer (internal).
+#pragma once
+#include <vector>
+
+#include "../../include/unwrap_lp.h"
+#include "ulp_internal.cuh"
+
+namespace ulp {
+
+struct Plan {
+  int device = 0;
+  int nsm = 0;
+  int nmaps = 0;
+  int ntiles = 0;
+  int R = 32;                // rows per warp tile
+  int bps = 1;               // resident blocks per SM of the persistent solvers
+  int bx_elem = 1;           // blocks per map of the elementwise kernels
+  ulp_options opt{};
+  std::vector<MapDesc> hmaps;
+  MapDesc* dmaps = nullptr;
+  MapState* dstate = nullptr;
+  MapStats* dstats = nullptr;
+  double *P0 = nullptr, *P1 = nullptr, *P2 = nullptr;
+  double* outer_part = nullptr;
+  Barrier* bar = nullptr;
+  int* n_active = nullptr;
+  double *d_p = nullptr, *d_tau = nullptr;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  cudaStream_t last_stream = nullptr;
+  int last_status = 0;
+  // instrumentation
+  mutable long long kernel_launches = 0;
+  mutable long long solver_launches = 0;
+  std::vector<cudaEvent_t> ev_pool;      // pairs (start, stop) recorded around solver launches
+  size_t ev_used = 0;
+};
+
+// ulp_fp64.cu
+cudaError_t launch_pack(const Plan& pl, int m, const double* psi, const uint8_t* mask, const double* phi0,
+                        cudaStream_t st);
+cudaError_t launch_unpack(const Plan& pl, int m, double* phi, cudaStream_t st);
+cudaError_t launch_begin(const Plan& pl, cudaStream_t st);
+cudaError_t launch_check(const Plan& pl, cudaStream_t st);
+cudaError_t launch_diag(const Plan& pl, cudaStream_t st);
+cudaError_t launch_system(const Plan& pl, const double* d_p, const double* d_tau, cudaStream_t st);
+cudaError_t launch_outer_error(const Plan& pl, double outer_tol, int max_outer, cudaStream_t st);
+cudaError_t launch_pcg64(const Plan& pl, int kind, const PcgArgs& a, cudaStream_t st, cudaEvent_t e0 = nullptr,
+                         cudaEvent_t e1 = nullptr);
+int pcg64_max_blocks_per_sm(int kind);
+cudaError_t launch_matvec(const Plan& pl, const double* x, double* y, cudaStream_t st);
+cudaError_t launch_jacobi_apply(const Plan& pl, int kind, const double* r, double* s, cudaStream_t st);
+cudaError_t launch_to_plane(const Plan& pl, const double* src, double* dst, cudaStream_t st);
+cudaError_t launch_from_plane(const Plan& pl, const double* src, double* dst, cudaStream_t st);
+cudaError_t launch_mask_to_plane(const Plan& pl, const uint8_t* mask, cudaStream_t st);
+
+}  // namespace ulp

@@ -1,0 +1,201 @@
+// ulp_internal.cuh -- internal types and device helpers of the GB300 L^p
+// phase-unwrapping library (not part of the C ABI).
+//
+// Data layout in HBM: every internal plane of a map is an H x pitch row-major
+// array, pitch = W rounded up to a multiple of 64 elements, so each row starts
+// on a 512-byte boundary and a warp moving one double2 per lane covers one
+// 64-column strip.  Columns W..pitch-1 are zero padding with zero weights, so
+// every kernel may treat them as part of the grid.
+//
+// Work unit: a warp tile = 64 columns x R rows of one map.  Tiles of all maps
+// of a call are numbered consecutively (map by map, row band by row band);
+// per-tile partial sums make every reduction independent of which warp or
+// block processed which tile.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace ulp {
+
+constexpr int kStrip = 64;            // columns per warp tile (32 lanes x double2 / float2)
+constexpr int kThreads = 256;         // threads per block of the persistent solver
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxMaps = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+enum Kind { kIdentity = 0, kJacobi = 1, kIlu = 2, kIc = 3, kSsor = 4, kDct = 5 };
+
+// FP64 planes of one map (all H x pitch).
+struct Planes64 {
+  double *dx, *dy;          // wrapped differences (Sec. 2.1)
+  double *U, *V;            // Eq. (UV) weights
+  double *D, *Dinv;         // diagonal of A and its guarded inverse
+  double *b;                // Eq. (Axb) right-hand side
+  double *phi, *phi_prev;   // current iterate, previous outer iterate
+  double *r, *s, *q;        // PCG residual, preconditioned residual, A d
+  double *d0, *d1;          // search direction (ping-pong)
+  double *piv;              // ILU(0)/IC(0) pivots, or D/omega for SSOR
+  double *y;                // triangular-sweep intermediate
+  uint8_t* mask;            // 1 = excluded pixel
+};
+
+// FP32 planes of one map for the mixed-precision solver.
+struct Planes32 {
+  float *U, *V, *Dinv;      // weights (FP32) and Jacobi inverse
+  float *x, *r, *s, *q, *d0, *d1;
+  float *cw, *cn, *pinv, *y; // sweep coefficients (mixed ILU/SSOR)
+};
+
+struct MapDesc {
+  int H, W, pitch;
+  int nsx, nsy;             // strips (pitch/64) and row bands
+  int tile_base, ntiles;    // first tile index, number of tiles
+  int refresh;              // true-residual period
+  Planes64 f;
+  Planes32 h;
+  int* flags;               // wavefront tile flags (nsx * nsy ints)
+};
+
+// Mutable per-map solver state (device).
+struct MapState {
+  double delta, delta0, rr, bb, dq, alpha, beta, relres;
+  long long iter;
+  int status, done, stop_after, outer_active;
+  int outer_k, err_flag;
+  unsigned arrive, arrive_outer;
+  double outer_err;
+  int sweep_epoch, pad;
+};
+
+// Device-side record of one call (per map), copied to the host at the end.
+struct MapStats {
+  int status, outer;
+  long long inner_total;
+  long long inner[64];
+  double relres[64];
+  double outer_err[64];
+};
+
+struct Barrier {
+  unsigned count;
+  unsigned gen;
+  int err;
+  int pad;
+};
+
+// Arguments of the persistent PCG kernels.
+struct PcgArgs {
+  const MapDesc* maps;
+  MapState* st;
+  int nmaps, ntiles, R;
+  double *P0, *P1, *P2;     // per-tile partial sums
+  Barrier* bar;
+  int* n_active;
+  int stop_mode;
+  double tol2;
+  long long lmax;
+  unsigned long long timeout_ns;
+  double omega;
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_acquire_i(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_i(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative (co-resident) grid with a bounded wait.
+// Returns false if any block gave up; every caller then leaves the kernel.
+__device__ __forceinline__ bool grid_sync(Barrier* b, unsigned long long timeout_ns) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned g = ld_acquire(&b->gen);
+    __threadfence();
+    unsigned arrived = atomicAdd(&b->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      st_release(&b->gen, g + 1u);
+    } else {
+      unsigned long long t0 = globaltimer();
+      while (ld_acquire(&b->gen) == g) {
+        if (*(volatile int*)&b->err) break;
+        if (globaltimer() - t0 > timeout_ns) {
+          atomicExch(&b->err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)&b->err == 0;
+}
+
+__device__ __forceinline__ double2 ld2(const double* base, size_t off) {
+  return __ldcg(reinterpret_cast<const double2*>(base + off));
+}
+__device__ __forceinline__ void st2(double* base, size_t off, double2 v) {
+  __stcg(reinterpret_cast<double2*>(base + off), v);
+}
+__device__ __forceinline__ double ld1(const double* base, size_t off) { return __ldcg(base + off); }
+
+// Deterministic warp sum: fixed shfl_down tree, result broadcast from lane 0.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  return __shfl_sync(kFull, v, 0);
+}
+
+// Fixed-order sum of n partials (stride-32 lanes, 4 accumulators, fixed tree).
+__device__ __forceinline__ double warp_sum_partials(const double* P, int n, int lane) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int k = lane;
+  for (; k + 96 < n; k += 128) {
+    a0 += __ldcg(P + k);
+    a1 += __ldcg(P + k + 32);
+    a2 += __ldcg(P + k + 64);
+    a3 += __ldcg(P + k + 96);
+  }
+  if (k < n) a0 += __ldcg(P + k);
+  if (k + 32 < n) a1 += __ldcg(P + k + 32);
+  if (k + 64 < n) a2 += __ldcg(P + k + 64);
+  return warp_sum((a0 + a1) + (a2 + a3));
+}
+
+__device__ __forceinline__ int find_map(const int* base, int nmaps, int t) {
+  int lo = 0, hi = nmaps - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (base[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Principal value onto (-pi, pi] (Eq. wrapped): x - 2 pi ceil((x - pi) / (2 pi)).
+__device__ __forceinline__ double wrap_pv(double x) {
+  const double pi = 3.14159265358979323846;
+  const double two_pi = 2.0 * pi;
+  double k = ceil(__ddiv_rn(__dsub_rn(x, pi), two_pi));
+  return __dsub_rn(x, __dmul_rn(two_pi, k));
+}
+
+}  // namespace ulp

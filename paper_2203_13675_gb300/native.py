@@ -1,0 +1,271 @@
+"""Thin ctypes binding of libunwrap_lp.so (include/unwrap_lp.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Arrays are torch tensors (CUDA for device pointers, CPU for the
+host-pointer form of ``unwrap_lp``); torch supplies memory and streams.
+There is no CPU fallback: if the library is missing the import fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+PRECOND = {"identity": 0, "jacobi": 1, "ilu0": 2, "ic0": 3, "ssor": 4, "dct": 5}
+ULP_OK, ULP_WARN_MAXITER = 0, 1
+ULP_ERR_INVALID, ULP_ERR_CUDA, ULP_ERR_BREAKDOWN, ULP_ERR_TIMEOUT, ULP_ERR_NOMEM, ULP_ERR_UNSUPPORTED = \
+    -1, -2, -3, -4, -5, -6
+ULP_STOP_RELRES, ULP_STOP_PAPER = 0, 1
+ULP_PRECISION_FP64, ULP_PRECISION_MIXED = 0, 1
+ULP_PHI0_ZERO, ULP_PHI0_USER = 0, 1
+
+EXPORTED = ["ulp_options_default", "ulp_last_error", "unwrap_lp", "ulp_plan_create",
+            "ulp_plan_create_batched", "ulp_plan_destroy", "ulp_unwrap", "ulp_unwrap_batched",
+            "ulp_plan_last_status", "ulp_wrapped_diffs", "ulp_weights", "ulp_matvec",
+            "ulp_precond_apply", "ulp_pcg", "ulp_plan_counters"]
+
+
+class UlpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"unwrap_lp status {status}: {msg}")
+        self.status = status
+
+
+class ulp_options(ctypes.Structure):
+    _fields_ = [("stop_mode", ctypes.c_int), ("outer_tol", ctypes.c_double),
+                ("refresh", ctypes.c_longlong), ("omega", ctypes.c_double),
+                ("precision", ctypes.c_int), ("phi0_mode", ctypes.c_int),
+                ("tile_rows", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("spin_timeout_s", ctypes.c_double), ("profile", ctypes.c_int)]
+
+
+class ulp_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer", ctypes.c_int), ("inner_total", ctypes.c_longlong),
+                ("inner", ctypes.c_longlong * 64), ("relres", ctypes.c_double * 64),
+                ("outer_err", ctypes.c_double * 64)]
+
+    def as_dict(self):
+        k = min(self.outer, 64)
+        return {"status": self.status, "outer": self.outer, "inner_total": self.inner_total,
+                "inner": list(self.inner[:k]), "relres": list(self.relres[:k]),
+                "outer_err": list(self.outer_err[:k])}
+
+
+class ulp_counters(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_longlong), ("solver_launches", ctypes.c_longlong),
+                ("solver_ms", ctypes.c_double), ("timed_launches", ctypes.c_longlong)]
+
+
+class ulp_map(ctypes.Structure):
+    _fields_ = [("psi", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("phi", ctypes.c_void_p),
+                ("p", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Loads the library (built in-tree by paper_2203_13675_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build the CUDA library first "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(path)
+    V, I, D, P = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    L.ulp_options_default.argtypes = [ctypes.POINTER(ulp_options)]
+    L.ulp_options_default.restype = None
+    L.ulp_last_error.restype = ctypes.c_char_p
+    L.unwrap_lp.argtypes = [P, I, I, D, D, I, D, I, I, P]
+    L.ulp_plan_create.argtypes = [I, I, ctypes.POINTER(ulp_options), ctypes.POINTER(V)]
+    L.ulp_plan_create_batched.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(I),
+                                          ctypes.POINTER(ulp_options), ctypes.POINTER(V)]
+    L.ulp_plan_destroy.argtypes = [V]
+    L.ulp_plan_destroy.restype = None
+    L.ulp_unwrap.argtypes = [V, P, P, D, D, I, D, I, I, P, V, ctypes.POINTER(ulp_stats)]
+    L.ulp_unwrap_batched.argtypes = [V, ctypes.POINTER(ulp_map), I, D, I, I, V, ctypes.POINTER(ulp_stats)]
+    L.ulp_plan_last_status.argtypes = [V, ctypes.POINTER(ulp_stats)]
+    L.ulp_plan_counters.argtypes = [V, I, ctypes.POINTER(ulp_counters)]
+    L.ulp_wrapped_diffs.argtypes = [P, I, I, P, P, V]
+    L.ulp_weights.argtypes = [P, P, P, P, I, I, D, D, P, P, P, V]
+    L.ulp_matvec.argtypes = [P, P, P, I, I, P, V]
+    L.ulp_precond_apply.argtypes = [I, P, P, P, I, I, D, P, P, V]
+    L.ulp_pcg.argtypes = [P, P, P, I, I, I, D, I, ctypes.POINTER(ulp_options), P, V,
+                          ctypes.POINTER(ulp_stats)]
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return load().ulp_last_error().decode()
+
+
+def _check(rc):
+    if rc < 0:
+        raise UlpError(rc, last_error())
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev(t, dtype=torch.float64):
+    assert t.is_cuda and t.dtype == dtype and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return t
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _precond(p):
+    return PRECOND[p] if isinstance(p, str) else int(p)
+
+
+def ulp_options_default(**overrides) -> ulp_options:
+    o = ulp_options()
+    load().ulp_options_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def unwrap_lp(psi, p=1.0, eps=1e-2, precond="jacobi", tol=1e-6, max_outer=5, max_inner=0, phi=None):
+    """unwrap_lp(): whole method, host (CPU tensor) or device (CUDA tensor) buffers."""
+    H, W = psi.shape
+    assert psi.dtype == torch.float64 and psi.is_contiguous()
+    if phi is None:
+        phi = torch.empty_like(psi)
+    rc = load().unwrap_lp(_ptr(psi), H, W, float(p), float(eps), _precond(precond), float(tol),
+                          int(max_outer), int(max_inner), _ptr(phi))
+    _check(rc)
+    return phi, rc
+
+
+class Plan:
+    """Owns a ulp_plan (device workspace for one size or one batch of sizes)."""
+
+    def __init__(self, H, W=None, options: ulp_options | None = None, sizes=None, **opt):
+        L = load()
+        self._h = ctypes.c_void_p()
+        o = options or ulp_options_default(**opt)
+        if sizes is not None:
+            n = len(sizes)
+            Ha = (ctypes.c_int * n)(*[s[0] for s in sizes])
+            Wa = (ctypes.c_int * n)(*[s[1] for s in sizes])
+            _check(L.ulp_plan_create_batched(n, Ha, Wa, ctypes.byref(o), ctypes.byref(self._h)))
+            self.sizes = list(sizes)
+        else:
+            _check(L.ulp_plan_create(int(H), int(W), ctypes.byref(o), ctypes.byref(self._h)))
+            self.sizes = [(H, W)]
+        self.options = o
+
+    def close(self):
+        if self._h:
+            load().ulp_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def unwrap(self, psi, mask=None, p=1.0, eps=1e-2, precond="jacobi", tol=1e-6, max_outer=5,
+               max_inner=0, phi=None, stream=None, stats=True):
+        """ulp_unwrap(): returns (phi, stats dict or None)."""
+        _dev(psi)
+        if mask is not None:
+            _dev(mask, torch.uint8)
+        if phi is None:
+            phi = torch.empty_like(psi)
+        st = ulp_stats() if stats else None
+        rc = load().ulp_unwrap(self._h, _ptr(psi), _ptr(mask), float(p), float(eps), _precond(precond),
+                               float(tol), int(max_outer), int(max_inner), _ptr(phi), _stream(stream),
+                               ctypes.byref(st) if st is not None else None)
+        _check(rc)
+        return phi, (st.as_dict() if st is not None else None)
+
+    def unwrap_batched(self, maps, precond="jacobi", tol=1e-6, max_outer=5, max_inner=0, stream=None,
+                       stats=True):
+        """ulp_unwrap_batched(): maps = list of dicts with psi, mask, phi, p, eps (CUDA tensors)."""
+        n = len(maps)
+        arr = (ulp_map * n)()
+        for t, m in enumerate(maps):
+            arr[t].psi = m["psi"].data_ptr()
+            arr[t].mask = m["mask"].data_ptr() if m.get("mask") is not None else None
+            arr[t].phi = m["phi"].data_ptr()
+            arr[t].p = float(m["p"])
+            arr[t].eps = float(m.get("eps", 1e-2))
+        st = (ulp_stats * n)() if stats else None
+        rc = load().ulp_unwrap_batched(self._h, arr, _precond(precond), float(tol), int(max_outer),
+                                       int(max_inner), _stream(stream), st)
+        _check(rc)
+        return rc, ([s.as_dict() for s in st] if st is not None else None)
+
+    def counters(self, reset=False):
+        """ulp_plan_counters(): kernel launches, solver launches and (profile=1) solver ms."""
+        c = ulp_counters()
+        _check(load().ulp_plan_counters(self._h, int(bool(reset)), ctypes.byref(c)))
+        return {"kernel_launches": c.kernel_launches, "solver_launches": c.solver_launches,
+                "solver_ms": c.solver_ms, "timed_launches": c.timed_launches}
+
+    def last_status(self):
+        st = ulp_stats()
+        rc = load().ulp_plan_last_status(self._h, ctypes.byref(st))
+        return rc, st.as_dict()
+
+
+def ulp_wrapped_diffs(psi, stream=None):
+    H, W = psi.shape
+    _dev(psi)
+    dx = torch.empty_like(psi)
+    dy = torch.empty_like(psi)
+    _check(load().ulp_wrapped_diffs(_ptr(psi), H, W, _ptr(dx), _ptr(dy), _stream(stream)))
+    return dx, dy
+
+
+def ulp_weights(phi, dx, dy, mask=None, p=1.0, eps=1e-2, stream=None):
+    H, W = phi.shape
+    U = torch.empty_like(phi)
+    V = torch.empty_like(phi)
+    b = torch.empty_like(phi)
+    _check(load().ulp_weights(_ptr(_dev(phi)), _ptr(_dev(dx)), _ptr(_dev(dy)),
+                              _ptr(mask), H, W, float(p), float(eps), _ptr(U), _ptr(V), _ptr(b),
+                              _stream(stream)))
+    return U, V, b
+
+
+def ulp_matvec(U, V, x, stream=None):
+    H, W = x.shape
+    y = torch.empty_like(x)
+    _check(load().ulp_matvec(_ptr(_dev(U)), _ptr(_dev(V)), _ptr(_dev(x)), H, W, _ptr(y), _stream(stream)))
+    return y
+
+
+def ulp_precond_apply(precond, U, V, r, mask=None, omega=1.0, stream=None):
+    H, W = r.shape
+    s = torch.empty_like(r)
+    _check(load().ulp_precond_apply(_precond(precond), _ptr(_dev(U)), _ptr(_dev(V)), _ptr(mask), H, W,
+                                    float(omega), _ptr(_dev(r)), _ptr(s), _stream(stream)))
+    return s
+
+
+def ulp_pcg(U, V, b, phi, precond="jacobi", tol=1e-6, max_inner=0, stream=None, **opt):
+    H, W = b.shape
+    o = ulp_options_default(**opt)
+    st = ulp_stats()
+    rc = load().ulp_pcg(_ptr(_dev(U)), _ptr(_dev(V)), _ptr(_dev(b)), H, W, _precond(precond), float(tol),
+                        int(max_inner), ctypes.byref(o), _ptr(_dev(phi)), _stream(stream), ctypes.byref(st))
+    _check(rc)
+    return phi, st.as_dict()

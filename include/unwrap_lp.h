@@ -229,6 +229,37 @@ ULP_API int ulp_pcg(const double* U, const double* V, const double* b, int H, in
             double tol, int max_inner, const ulp_options* opt, double* phi, void* cuda_stream,
             ulp_stats* stats);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free inner solve.  The paper has no counterpart: this entry point
+ * exists for callers of this library that cannot allocate device memory --
+ * a caller whose device memory is already held by another allocator (a
+ * framework's caching pool, where cudaMalloc would fail or force the pool to
+ * release memory), or a caller on a latency-bound loop that cannot pay for
+ * cudaMalloc/cudaFree (cudaFree waits for the whole device) or risk an
+ * out-of-memory failure mid-run.  ulp_pcg allocates and frees a workspace on
+ * every call; this variant allocates nothing.
+ * ------------------------------------------------------------------------- */
+
+/* ulp_pcg_noalloc: the same solve and results as ulp_pcg with default options
+ * and precond ULP_PRECOND_IDENTITY or ULP_PRECOND_JACOBI (others return
+ * ULP_ERR_UNSUPPORTED); U, V, b, phi are caller-owned device arrays as there.
+ *   Workspace: one static device array of 8 MiB inside the library, which
+ *   every GPU that loads the library holds until the process exits.  Grids are
+ *   limited to H * round_up(W, 64) <= 65536 elements (e.g. 256 x 256);
+ *   larger grids return ULP_ERR_INVALID with a message in ulp_last_error().
+ *   No cudaMalloc, cudaFree or other allocating routine is called.
+ *   Set-up: the first call on each device (with that device current) looks up
+ *   the array's device address; make that first call before any stream
+ *   capture.
+ *   Sharing: all calls on a device use the same array and leave their
+ *   contents in it; each call clears what it needs before use.  Calls whose
+ *   work overlaps on the GPU (different streams or host threads) race on the
+ *   array: the caller must serialise them.
+ *   stats (host, nullable) as in ulp_pcg; non-NULL synchronises the stream. */
+ULP_API int ulp_pcg_noalloc(const double* U, const double* V, const double* b, int H, int W,
+                            int precond, double tol, int max_inner, double* phi, void* cuda_stream,
+                            ulp_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

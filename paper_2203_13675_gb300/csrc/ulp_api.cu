@@ -30,6 +30,9 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+// Records msg as the calling thread's last error (for files other than this one).
+int ulp::set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 #define ULP_CU(x)                                                                   \
   do {                                                                              \
     cudaError_t e_ = (x);                                                           \

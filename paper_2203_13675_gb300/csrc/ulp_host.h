@@ -37,6 +37,9 @@ struct Plan {
   size_t ev_used = 0;
 };
 
+// ulp_api.cu: records msg as the calling thread's last error and returns code.
+int set_error(int code, const char* msg);
+
 // ulp_fp64.cu
 cudaError_t launch_pack(const Plan& pl, int m, const double* psi, const uint8_t* mask, const double* phi0,
                         cudaStream_t st);

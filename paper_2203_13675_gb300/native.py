@@ -25,7 +25,7 @@ ULP_PHI0_ZERO, ULP_PHI0_USER = 0, 1
 EXPORTED = ["ulp_options_default", "ulp_last_error", "unwrap_lp", "ulp_plan_create",
             "ulp_plan_create_batched", "ulp_plan_destroy", "ulp_unwrap", "ulp_unwrap_batched",
             "ulp_plan_last_status", "ulp_wrapped_diffs", "ulp_weights", "ulp_matvec",
-            "ulp_precond_apply", "ulp_pcg", "ulp_plan_counters"]
+            "ulp_precond_apply", "ulp_pcg", "ulp_plan_counters", "ulp_pcg_noalloc"]
 
 
 class UlpError(RuntimeError):
@@ -97,6 +97,7 @@ def load(path: str | None = None):
     L.ulp_precond_apply.argtypes = [I, P, P, P, I, I, D, P, P, V]
     L.ulp_pcg.argtypes = [P, P, P, I, I, I, D, I, ctypes.POINTER(ulp_options), P, V,
                           ctypes.POINTER(ulp_stats)]
+    L.ulp_pcg_noalloc.argtypes = [P, P, P, I, I, I, D, I, P, V, ctypes.POINTER(ulp_stats)]
     _lib = L
     return L
 
@@ -267,5 +268,15 @@ def ulp_pcg(U, V, b, phi, precond="jacobi", tol=1e-6, max_inner=0, stream=None, 
     st = ulp_stats()
     rc = load().ulp_pcg(_ptr(_dev(U)), _ptr(_dev(V)), _ptr(_dev(b)), H, W, _precond(precond), float(tol),
                         int(max_inner), ctypes.byref(o), _ptr(_dev(phi)), _stream(stream), ctypes.byref(st))
+    _check(rc)
+    return phi, st.as_dict()
+
+
+def ulp_pcg_noalloc(U, V, b, phi, precond="jacobi", tol=1e-6, max_inner=0, stream=None):
+    """ulp_pcg_noalloc(): ulp_pcg without any device allocation (static workspace)."""
+    H, W = b.shape
+    st = ulp_stats()
+    rc = load().ulp_pcg_noalloc(_ptr(_dev(U)), _ptr(_dev(V)), _ptr(_dev(b)), H, W, _precond(precond),
+                                float(tol), int(max_inner), _ptr(_dev(phi)), _stream(stream), ctypes.byref(st))
     _check(rc)
     return phi, st.as_dict()

@@ -79,13 +79,14 @@ static void next_events(Plan& pl, cudaEvent_t* e0, cudaEvent_t* e1) {
   pl.ev_used += 2;
 }
 
-static int default_tile_rows(int H, int W) {
-  // rows per warp tile: enough tiles to fill the resident warps, long enough
-  // windows to amortise the two halo rows.
-  (void)W;
-  if (H >= 2048) return 32;
-  if (H >= 512) return 16;
-  return 8;
+// Rows per warp tile: about one tile per resident warp of the persistent
+// solver (static round-robin assignment, so equal counts balance the work),
+// between 4 and 64 rows so the two halo rows stay amortised.
+int ulp::default_tile_rows(int n, const int* H, const int* W, int resident_warps) {
+  double cells = 0.0;  // rows x 64-column strips over all maps
+  for (int m = 0; m < n; ++m) cells += (double)H[m] * ((W[m] + kStrip - 1) / kStrip);
+  int R = (int)std::ceil(cells / (resident_warps > 0 ? resident_warps : 1));
+  return R < 4 ? 4 : (R > 64 ? 64 : R);
 }
 
 static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_options* opt) {
@@ -96,6 +97,7 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
   }
   if (opt) pl.opt = *opt; else ulp_options_default(&pl.opt);
   if (!(pl.opt.spin_timeout_s > 0.0)) pl.opt.spin_timeout_s = 2.0;
+  if (!(pl.opt.omega > 0.0 && pl.opt.omega < 2.0)) return fail(ULP_ERR_INVALID, "omega must be in (0, 2)");
   if (pl.opt.precision != ULP_PRECISION_FP64 && pl.opt.precision != ULP_PRECISION_MIXED)
     return fail(ULP_ERR_INVALID, "unknown precision %d", pl.opt.precision);
   ULP_CU(cudaGetDevice(&pl.device));
@@ -104,14 +106,19 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
   ULP_CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, pl.device));
   if (!coop) return fail(ULP_ERR_UNSUPPORTED, "device lacks cooperative launch");
   pl.nmaps = n;
-  int maxH = 0;
-  for (int m = 0; m < n; ++m) maxH = H[m] > maxH ? H[m] : maxH;
-  pl.R = pl.opt.tile_rows > 0 ? pl.opt.tile_rows : default_tile_rows(maxH, 0);
+  int occ = 1 << 30;
+  for (int kind : {kIdentity, kJacobi, kIlu, kSsor}) {
+    const int o = pcg64_max_blocks_per_sm(kind);
+    occ = o < occ ? o : occ;
+  }
+  if (occ < 1) return fail(ULP_ERR_CUDA, "persistent solver does not fit on an SM");
+  pl.bps = pl.opt.blocks_per_sm > 0 && pl.opt.blocks_per_sm < occ ? pl.opt.blocks_per_sm : occ;
+  pl.R = pl.opt.tile_rows > 0 ? pl.opt.tile_rows : default_tile_rows(n, H, W, pl.nsm * pl.bps * kWarps);
 
   // geometry and arena layout
   pl.hmaps.assign(n, MapDesc{});
   size_t bytes = 0;
-  int tiles = 0;
+  int tiles = 0, bands = 0;
   std::vector<size_t> plane_off(n);
   for (int m = 0; m < n; ++m) {
     MapDesc& M = pl.hmaps[m];
@@ -123,6 +130,9 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
     M.tile_base = tiles;
     M.ntiles = M.nsx * M.nsy;
     tiles += M.ntiles;
+    M.nbands = (H[m] + 31) / 32;
+    M.band_base = bands;
+    bands += M.nbands;
     long long rf = pl.opt.refresh > 0 ? pl.opt.refresh
                                       : (long long)std::floor(std::sqrt((double)H[m] * (double)W[m]));
     if (pl.opt.refresh <= 0 && pl.opt.precision == ULP_PRECISION_MIXED) rf = 20;
@@ -131,12 +141,12 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
     M.refresh = (int)rf;
     plane_off[m] = bytes;
     const size_t e = (size_t)M.H * M.pitch;
-    bytes += 16 * align256(e * sizeof(double));   // FP64 planes
+    bytes += 20 * align256(e * sizeof(double));   // FP64 planes
     bytes += 13 * align256(e * sizeof(float));    // FP32 planes
     bytes += align256(e);                         // mask
-    bytes += align256((size_t)M.ntiles * sizeof(int));
   }
   pl.ntiles = tiles;
+  pl.nbands = bands;
   pl.bx_elem = pl.nsm * 4;
   const size_t off_maps = bytes;
   bytes += align256(sizeof(MapDesc) * n);
@@ -152,6 +162,8 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
   bytes += align256(sizeof(Barrier)) + align256(sizeof(int));
   const size_t off_pt = bytes;
   bytes += 2 * align256(sizeof(double) * n);
+  const size_t off_prog = bytes;
+  bytes += align256(sizeof(unsigned long long) * bands);
 
   cudaError_t e = cudaMalloc(&pl.arena, bytes);
   if (e != cudaSuccess) {
@@ -168,15 +180,16 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
     const size_t e32 = align256((size_t)M.H * M.pitch * sizeof(float));
     char* p = base + plane_off[m];
     double** f64[] = {&M.f.dx, &M.f.dy, &M.f.U, &M.f.V, &M.f.D, &M.f.Dinv, &M.f.b, &M.f.phi,
-                      &M.f.phi_prev, &M.f.r, &M.f.s, &M.f.q, &M.f.d0, &M.f.d1, &M.f.piv, &M.f.y};
+                      &M.f.phi_prev, &M.f.r, &M.f.s, &M.f.q, &M.f.d0, &M.f.d1, &M.f.piv, &M.f.y,
+                      &M.f.cw, &M.f.cn, &M.f.ce, &M.f.cs};
     for (double** q : f64) { *q = reinterpret_cast<double*>(p); p += e64; }
     float** f32[] = {&M.h.U, &M.h.V, &M.h.Dinv, &M.h.x, &M.h.r, &M.h.s, &M.h.q,
                      &M.h.d0, &M.h.d1, &M.h.cw, &M.h.cn, &M.h.pinv, &M.h.y};
     for (float** q : f32) { *q = reinterpret_cast<float*>(p); p += e32; }
     M.f.mask = reinterpret_cast<uint8_t*>(p);
-    p += align256((size_t)M.H * M.pitch);
-    M.flags = reinterpret_cast<int*>(p);
+    M.prog = reinterpret_cast<unsigned long long*>(base + off_prog) + M.band_base;
   }
+  pl.prog = reinterpret_cast<unsigned long long*>(base + off_prog);
   pl.dmaps = reinterpret_cast<MapDesc*>(base + off_maps);
   pl.dstate = reinterpret_cast<MapState*>(base + off_state);
   pl.dstats = reinterpret_cast<MapStats*>(base + off_stats);
@@ -190,12 +203,6 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
   pl.d_tau = reinterpret_cast<double*>(base + off_pt + align256(sizeof(double) * n));
   ULP_CU(cudaMemcpy(pl.dmaps, pl.hmaps.data(), sizeof(MapDesc) * n, cudaMemcpyHostToDevice));
   ULP_CU(cudaDeviceSynchronize());  // workspace zeroed before any stream may use it
-
-  int occ = pcg64_max_blocks_per_sm(kIdentity);
-  const int occ2 = pcg64_max_blocks_per_sm(kJacobi);
-  occ = occ2 < occ ? occ2 : occ;
-  if (occ < 1) return fail(ULP_ERR_CUDA, "persistent solver does not fit on an SM");
-  pl.bps = pl.opt.blocks_per_sm > 0 && pl.opt.blocks_per_sm < occ ? pl.opt.blocks_per_sm : occ;
   return ULP_OK;
 }
 
@@ -240,7 +247,7 @@ __global__ void k_set_pt(PT pt, double* p, double* tau, int first, int n) {
 static int check_solver_args(int precond, double tol, int max_outer) {
   if (precond < ULP_PRECOND_IDENTITY || precond > ULP_PRECOND_DCT)
     return fail(ULP_ERR_INVALID, "unknown preconditioner %d", precond);
-  if (precond != ULP_PRECOND_IDENTITY && precond != ULP_PRECOND_JACOBI)
+  if (precond == ULP_PRECOND_DCT)
     return fail(ULP_ERR_UNSUPPORTED, "preconditioner %d not available in this build", precond);
   if (!(tol > 0.0)) return fail(ULP_ERR_INVALID, "tol must be > 0");
   if (max_outer < 1) return fail(ULP_ERR_INVALID, "max_outer must be >= 1");
@@ -265,6 +272,7 @@ static PcgArgs pcg_args(const Plan& pl, double tol, int max_inner) {
   a.st = pl.dstate;
   a.nmaps = pl.nmaps;
   a.ntiles = pl.ntiles;
+  a.nbands = pl.nbands;
   a.R = pl.R;
   a.P0 = pl.P0;
   a.P1 = pl.P1;
@@ -521,16 +529,26 @@ extern "C" int ulp_precond_apply(int precond, const double* U, const double* V, 
   int rc = check_solver_args(precond, 1.0, 1);
   if (rc != ULP_OK) return rc;
   (void)mask;
-  (void)omega;
+  ulp_options o;
+  ulp_options_default(&o);
+  o.omega = omega;
   TempPlan tp;
-  rc = temp_plan(tp, H, W, nullptr, stream);
+  rc = temp_plan(tp, H, W, &o, stream);
   if (rc != ULP_OK) return rc;
   Plan& pl = tp.plan->p;
   const MapDesc& M = pl.hmaps[0];
   rc = load_weights(pl, U, V, tp.st);
   if (rc != ULP_OK) return rc;
-  ULP_CU(launch_to_plane(pl, r, M.f.r, tp.st));
-  ULP_CU(launch_jacobi_apply(pl, precond, M.f.r, M.f.s, tp.st));
+  if (precond == ULP_PRECOND_IDENTITY || precond == ULP_PRECOND_JACOBI) {
+    ULP_CU(launch_to_plane(pl, r, M.f.r, tp.st));
+    ULP_CU(launch_jacobi_apply(pl, precond, M.f.r, M.f.s, tp.st));
+  } else {
+    // the sweep solver's set-up and first s = M^-1 r, with b = r and phi = 0
+    ULP_CU(launch_to_plane(pl, r, M.f.b, tp.st));
+    PcgArgs a = pcg_args(pl, 1.0, 1);
+    a.apply_only = 1;
+    ULP_CU(launch_pcg64(pl, precond, a, tp.st, nullptr, nullptr));
+  }
   ULP_CU(launch_from_plane(pl, M.f.s, s, tp.st));
   ULP_CU(cudaStreamSynchronize(tp.st));
   return ULP_OK;

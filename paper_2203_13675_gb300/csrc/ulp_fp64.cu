@@ -4,6 +4,7 @@
 //   M = diag(A), the outer error (Algorithm 1), and single-step kernels.
 #include "ulp_internal.cuh"
 #include "ulp_host.h"
+#include "ulp_sweep.cuh"
 
 #include <math.h>
 
@@ -122,31 +123,49 @@ __global__ void k_system(const MapDesc* __restrict__ maps, MapState* S) {
 // Sliding-window 5-point stencil over one warp tile (64 columns x rows i0..i1-1):
 // each lane owns columns j, j+1; north/south neighbours come from the window,
 // east/west from the neighbouring lanes, the two tile-edge columns from a halo
-// load by lanes 0 and 31.  X supplies the vector being multiplied:
-// X::row(i, j) -> values at (i, j), (i, j+1); X::at(i, c) -> value at (i, c).
+// load by lanes 0 and 31.  X supplies the vector being multiplied in two
+// stages so that loads run one row ahead of the arithmetic:
+//   X::Raw X::load(i, j)   -- the planes behind x at (i, j), (i, j+1)
+//   double2 X::make(raw)   -- x itself
+//   double X::at(i, c)     -- x at one column (halo lanes)
 template <class X, class Epi>
 __device__ __forceinline__ void stencil_tile(const MapDesc& M, int i0, int i1, int j0, int lane,
                                              const double* U, const double* V, const double* D,
                                              const X& x, Epi& epi) {
+  using Raw = typename X::Raw;
   const int j = j0 + 2 * lane;
   const bool hw = (lane == 0) && (j0 > 0);
   const bool he = (lane == 31) && (j0 + kStrip < M.pitch);
+  const bool halo = hw || he;
   const int hc = (lane == 0) ? j0 - 1 : j0 + kStrip;
   const size_t P = (size_t)M.pitch;
-  double2 xn = make_double2(0.0, 0.0), vn = make_double2(0.0, 0.0);
+  const double2 z2 = make_double2(0.0, 0.0);
+  double2 xn = z2, vn = z2;
   if (i0 > 0) {
-    xn = x.row(i0 - 1, j);
+    xn = x.make(x.load(i0 - 1, j));
     vn = ld2(V, (size_t)(i0 - 1) * P + j);
   }
-  double2 xc = x.row(i0, j);
+  double2 xc = x.make(x.load(i0, j));
+  Raw rs = (i0 + 1 < M.H) ? x.load(i0 + 1, j) : X::zero();   // row i+1, raw
+  size_t off = (size_t)i0 * P + j;
+  double2 u = ld2(U, off), v = ld2(V, off), dd = ld2(D, off);
+  double h = halo ? x.at(i0, hc) : 0.0;
+  double uwh = hw ? ld1(U, (size_t)i0 * P + hc) : 0.0;
   for (int i = i0; i < i1; ++i) {
-    const size_t off = (size_t)i * P + j;
-    double2 xs = make_double2(0.0, 0.0);
-    if (i + 1 < M.H) xs = x.row(i + 1, j);
-    const double2 u = ld2(U, off), v = ld2(V, off), dd = ld2(D, off);
-    double h = 0.0, uwh = 0.0;
-    if (hw || he) h = x.at(i, hc);
-    if (hw) uwh = ld1(U, (size_t)i * P + hc);
+    // loads for the next row, issued before this row's arithmetic
+    const bool more = i + 1 < i1;
+    const size_t off2 = off + P;
+    Raw rs2 = (more && i + 2 < M.H) ? x.load(i + 2, j) : X::zero();
+    double2 u2 = z2, v2 = z2, dd2 = z2;
+    double h2 = 0.0, uwh2 = 0.0;
+    if (more) {
+      u2 = ld2(U, off2);
+      v2 = ld2(V, off2);
+      dd2 = ld2(D, off2);
+      if (halo) h2 = x.at(i + 1, hc);
+      if (hw) uwh2 = ld1(U, (size_t)(i + 1) * P + hc);
+    }
+    const double2 xs = (i + 1 < M.H) ? x.make(rs) : z2;
     double west = __shfl_up_sync(kFull, xc.y, 1);
     double east = __shfl_down_sync(kFull, xc.x, 1);
     double uw = __shfl_up_sync(kFull, u.y, 1);
@@ -167,13 +186,23 @@ __device__ __forceinline__ void stencil_tile(const MapDesc& M, int i0, int i1, i
     xn = xc;
     xc = xs;
     vn = v;
+    rs = rs2;
+    u = u2;
+    v = v2;
+    dd = dd2;
+    h = h2;
+    uwh = uwh2;
+    off = off2;
   }
 }
 
 struct XPlane {  // plain vector
   const double* x;
   size_t P;
-  __device__ __forceinline__ double2 row(int i, int j) const { return ld2(x, (size_t)i * P + j); }
+  using Raw = double2;
+  __device__ __forceinline__ static Raw zero() { return make_double2(0.0, 0.0); }
+  __device__ __forceinline__ Raw load(int i, int j) const { return ld2(x, (size_t)i * P + j); }
+  __device__ __forceinline__ double2 make(const Raw& r) const { return r; }
   __device__ __forceinline__ double at(int i, int c) const { return ld1(x, (size_t)i * P + c); }
 };
 
@@ -183,12 +212,20 @@ struct XDir {  // d = s + beta d_old, or d = s on the first iteration (Algorithm
   double beta;
   bool first;
   size_t P;
-  __device__ __forceinline__ double2 row(int i, int j) const {
+  struct Raw {
+    double2 s, d;
+  };
+  __device__ __forceinline__ static Raw zero() { return Raw{make_double2(0.0, 0.0), make_double2(0.0, 0.0)}; }
+  __device__ __forceinline__ Raw load(int i, int j) const {
     const size_t off = (size_t)i * P + j;
-    const double2 sv = ld2(s, off);
-    if (first) return sv;
-    const double2 dv = ld2(dold, off);
-    return make_double2(fma(beta, dv.x, sv.x), fma(beta, dv.y, sv.y));
+    Raw r;
+    r.s = ld2(s, off);
+    r.d = first ? make_double2(0.0, 0.0) : ld2(dold, off);
+    return r;
+  }
+  __device__ __forceinline__ double2 make(const Raw& r) const {
+    if (first) return r.s;
+    return make_double2(fma(beta, r.d.x, r.s.x), fma(beta, r.d.y, r.s.y));
   }
   __device__ __forceinline__ double at(int i, int c) const {
     const size_t off = (size_t)i * P + c;
@@ -357,30 +394,51 @@ __device__ __forceinline__ void b_tile(const PcgArgs& a, const MapDesc& M, MapSt
   const double* d = (it & 1) ? M.f.d0 : M.f.d1;
   const double alpha = *(volatile double*)&S->alpha;
   const int j = g.j0 + 2 * lane;
+  const double2 z2 = make_double2(0.0, 0.0);
   double rs = 0.0, rr = 0.0;
+  size_t off = (size_t)g.i0 * P + j;
+  double2 dv = ld2(d, off), ph = ld2(M.f.phi, off);
+  double2 qv = z2, rv = z2, di = z2;
+  if (!refresh) {
+    qv = ld2(M.f.q, off);
+    rv = ld2(M.f.r, off);
+    if (KIND == kJacobi) di = ld2(M.f.Dinv, off);
+  }
   for (int i = g.i0; i < g.i1; ++i) {
-    const size_t off = (size_t)i * P + j;
-    const double2 dv = ld2(d, off);
-    double2 ph = ld2(M.f.phi, off);
+    const size_t off2 = off + P;
+    const bool more = i + 1 < g.i1;
+    double2 dv2 = z2, ph2 = z2, qv2 = z2, rv2 = z2, di2 = z2;
+    if (more) {
+      dv2 = ld2(d, off2);
+      ph2 = ld2(M.f.phi, off2);
+      if (!refresh) {
+        qv2 = ld2(M.f.q, off2);
+        rv2 = ld2(M.f.r, off2);
+        if (KIND == kJacobi) di2 = ld2(M.f.Dinv, off2);
+      }
+    }
     ph.x = fma(alpha, dv.x, ph.x);
     ph.y = fma(alpha, dv.y, ph.y);
     st2(M.f.phi, off, ph);
     if (!refresh) {
-      const double2 qv = ld2(M.f.q, off);
-      double2 r = ld2(M.f.r, off);
-      r.x = fma(-alpha, qv.x, r.x);
-      r.y = fma(-alpha, qv.y, r.y);
-      st2(M.f.r, off, r);
+      rv.x = fma(-alpha, qv.x, rv.x);
+      rv.y = fma(-alpha, qv.y, rv.y);
+      st2(M.f.r, off, rv);
       if (KIND == kJacobi) {
-        const double2 di = ld2(M.f.Dinv, off);
-        const double2 s = make_double2(di.x * r.x, di.y * r.y);
-        st2(M.f.s, off, s);
-        rs = fma(r.x, s.x, rs);
-        rs = fma(r.y, s.y, rs);
+        const double2 sv = make_double2(di.x * rv.x, di.y * rv.y);
+        st2(M.f.s, off, sv);
+        rs = fma(rv.x, sv.x, rs);
+        rs = fma(rv.y, sv.y, rs);
       }
-      rr = fma(r.x, r.x, rr);
-      rr = fma(r.y, r.y, rr);
+      rr = fma(rv.x, rv.x, rr);
+      rr = fma(rv.y, rv.y, rr);
     }
+    dv = dv2;
+    ph = ph2;
+    qv = qv2;
+    rv = rv2;
+    di = di2;
+    off = off2;
   }
   if (!refresh) {
     if (KIND == kIdentity) rs = rr;
@@ -447,10 +505,217 @@ __global__ void __launch_bounds__(kThreads, 2) k_pcg64(PcgArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ ILU(0) / IC(0) / SSOR engine
+// Factor applied to r before the forward sweep: 1 for ILU/IC, (2 - omega)/omega
+// for SSOR (the omega/(2 - omega) of M moved onto the right-hand side).
+template <int KIND>
+__device__ __forceinline__ double sweep_rscale(const PcgArgs& a) {
+  return (KIND == kSsor) ? (2.0 - a.omega) / a.omega : 1.0;
+}
+
+// r = b - A phi and the forward sweep's right-hand side r pinv c (stored in s).
+template <int KIND>
+__device__ __forceinline__ void res_tile_sweep(const PcgArgs& a, const MapDesc& M, int t, int lane) {
+  const TileGeo g = tile_geo(M, t, a.R);
+  XPlane x{M.f.phi, (size_t)M.pitch};
+  const double c = sweep_rscale<KIND>(a);
+  auto epi = [&](size_t off, double2, double2 ax) {
+    const double2 bv = ld2(M.f.b, off);
+    const double2 r = make_double2(bv.x - ax.x, bv.y - ax.y);
+    st2(M.f.r, off, r);
+    const double2 pv = ld2(M.f.piv, off);
+    st2(M.f.s, off, make_double2(r.x * pv.x * c, r.y * pv.y * c));
+  };
+  stencil_tile(M, g.i0, g.i1, g.j0, lane, M.f.U, M.f.V, M.f.D, x, epi);
+}
+
+// phi += alpha d; r -= alpha q (not on refresh iterations); s = r pinv c.
+template <int KIND>
+__device__ __forceinline__ void b_tile_sweep(const PcgArgs& a, const MapDesc& M, MapState* S, int t,
+                                             bool refresh, int lane) {
+  const TileGeo g = tile_geo(M, t, a.R);
+  const size_t P = M.pitch;
+  const long long it = *(volatile long long*)&S->iter;
+  const double* d = (it & 1) ? M.f.d0 : M.f.d1;
+  const double alpha = *(volatile double*)&S->alpha;
+  const double c = sweep_rscale<KIND>(a);
+  const int j = g.j0 + 2 * lane;
+  for (int i = g.i0; i < g.i1; ++i) {
+    const size_t off = (size_t)i * P + j;
+    const double2 dv = ld2(d, off);
+    double2 ph = ld2(M.f.phi, off);
+    double2 qv, rv, pv;
+    if (!refresh) {
+      qv = ld2(M.f.q, off);
+      rv = ld2(M.f.r, off);
+      pv = ld2(M.f.piv, off);
+    }
+    ph.x = fma(alpha, dv.x, ph.x);
+    ph.y = fma(alpha, dv.y, ph.y);
+    st2(M.f.phi, off, ph);
+    if (!refresh) {
+      rv.x = fma(-alpha, qv.x, rv.x);
+      rv.y = fma(-alpha, qv.y, rv.y);
+      st2(M.f.r, off, rv);
+      st2(M.f.s, off, make_double2(rv.x * pv.x * c, rv.y * pv.y * c));
+    }
+  }
+}
+
+// Partials r^T s, r^T r (and b^T b on the first pass) after the backward sweep.
+__device__ __forceinline__ void dots_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t, bool init,
+                                          int lane) {
+  const TileGeo g = tile_geo(M, t, a.R);
+  const size_t P = M.pitch;
+  const int j = g.j0 + 2 * lane;
+  double rs = 0.0, rr = 0.0, bb = 0.0;
+  for (int i = g.i0; i < g.i1; ++i) {
+    const size_t off = (size_t)i * P + j;
+    const double2 rv = ld2(M.f.r, off), sv = ld2(M.f.s, off);
+    rs = fma(rv.x, sv.x, rs);
+    rs = fma(rv.y, sv.y, rs);
+    rr = fma(rv.x, rv.x, rr);
+    rr = fma(rv.y, rv.y, rr);
+    if (init) {
+      const double2 bv = ld2(M.f.b, off);
+      bb = fma(bv.x, bv.x, bb);
+      bb = fma(bv.y, bv.y, bb);
+    }
+  }
+  tile_arrive(a, M, S, t, init ? kPhResInit : kPhB, rs, rr, bb, lane);
+}
+
+// Sweep coefficients from U, V and 1/P (SSOR: 1/P = omega/D, D = 0 read as 1).
+template <int KIND>
+__device__ __forceinline__ void coef_tile(const PcgArgs& a, const MapDesc& M, int t, int lane) {
+  const TileGeo g = tile_geo(M, t, a.R);
+  const size_t P = M.pitch;
+  const int j = g.j0 + 2 * lane;
+  for (int i = g.i0; i < g.i1; ++i) {
+    const size_t off = (size_t)i * P + j;
+    double2 pv;
+    if (KIND == kSsor) {
+      const double2 dd = ld2(M.f.D, off);
+      pv.x = a.omega / (dd.x > 0.0 ? dd.x : 1.0);
+      pv.y = a.omega / (dd.y > 0.0 ? dd.y : 1.0);
+      st2(M.f.piv, off, pv);
+    } else {
+      pv = ld2(M.f.piv, off);
+    }
+    const double2 u = ld2(M.f.U, off), v = ld2(M.f.V, off);
+    const double uw = (j > 0) ? ld1(M.f.U, off - 1) : 0.0;
+    const double2 vn = (i > 0) ? ld2(M.f.V, off - P) : make_double2(0.0, 0.0);
+    st2(M.f.cw, off, make_double2(uw * pv.x, u.x * pv.y));
+    st2(M.f.cn, off, make_double2(vn.x * pv.x, vn.y * pv.y));
+    st2(M.f.ce, off, make_double2(u.x * pv.x, u.y * pv.y));
+    st2(M.f.cs, off, make_double2(v.x * pv.x, v.y * pv.y));
+  }
+}
+
+// Runs one sweep over every band of every map still iterating: consecutive
+// slots sit on different SMs; forward sweeps take bands in increasing order,
+// backward sweeps in decreasing order, so every wait is on a band that an
+// earlier-ordered slot step has already been given (no cycle).
+template <int MODE>
+__device__ bool sweep_phase(const PcgArgs& a, const int* s_bbase, unsigned long long epoch,
+                            bool (*want)(const MapState*)) {
+  const int lane = threadIdx.x & 31;
+  const int slot = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const int NS = gridDim.x * kWarps;
+  for (int k = slot; k < a.nbands; k += NS) {
+    const int gb = (MODE == kSweepBwd) ? a.nbands - 1 - k : k;
+    const int m = find_map(s_bbase, a.nmaps, gb);
+    MapState* S = a.st + m;
+    if (!want(S)) continue;
+    const MapDesc& M = a.maps[m];
+    SweepIO io;
+    if (MODE == kSweepPiv) io = SweepIO{M.f.D, M.f.U, M.f.V, M.f.piv};
+    else if (MODE == kSweepFwd) io = SweepIO{M.f.s, M.f.cw, M.f.cn, M.f.y};
+    else io = SweepIO{M.f.y, M.f.ce, M.f.cs, M.f.s};
+    if (!band_sweep<MODE>(M, gb - M.band_base, lane, M.prog, epoch, io, a.timeout_ns, &a.bar->err))
+      return false;  // the error flag is set: the next grid barrier ends every block
+  }
+  return true;
+}
+
+__device__ bool map_active(const MapState* S) { return *(volatile const int*)&S->done == 0; }
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads, 2) k_pcg64_sweep(PcgArgs a) {
+  __shared__ int s_base[kMaxMaps + 1];
+  __shared__ int s_bbase[kMaxMaps + 1];
+  __shared__ int s_any;
+  for (int m = threadIdx.x; m <= a.nmaps; m += blockDim.x) {
+    s_base[m] = (m < a.nmaps) ? a.maps[m].tile_base : a.ntiles;
+    s_bbase[m] = (m < a.nmaps) ? a.maps[m].band_base : a.nbands;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int NW = gridDim.x * kWarps;
+  unsigned long long epoch = 0;
+  auto for_tiles = [&](auto&& body) {
+    for (int t = gw; t < a.ntiles; t += NW) {
+      const int m = find_map(s_base, a.nmaps, t);
+      MapState* S = a.st + m;
+      if (*(volatile int*)&S->done) continue;
+      body(a.maps[m], S, t);
+    }
+  };
+
+  // preconditioner set-up (Algorithm 1: estimate M from A)
+  if (KIND == kIlu) {
+    sweep_phase<kSweepPiv>(a, s_bbase, ++epoch, map_active);
+    if (!grid_sync(a.bar, a.timeout_ns)) return;
+  }
+  for_tiles([&](const MapDesc& M, MapState*, int t) { coef_tile<KIND>(a, M, t, lane); });
+  if (!grid_sync(a.bar, a.timeout_ns)) return;
+  // r = b - A phi, d = M^-1 r, delta_new = r^T d
+  for_tiles([&](const MapDesc& M, MapState*, int t) { res_tile_sweep<KIND>(a, M, t, lane); });
+  if (!grid_sync(a.bar, a.timeout_ns)) return;
+  sweep_phase<kSweepFwd>(a, s_bbase, ++epoch, map_active);
+  if (!grid_sync(a.bar, a.timeout_ns)) return;
+  sweep_phase<kSweepBwd>(a, s_bbase, ++epoch, map_active);
+  if (!grid_sync(a.bar, a.timeout_ns)) return;
+  for_tiles([&](const MapDesc& M, MapState* S, int t) { dots_tile(a, M, S, t, true, lane); });
+  if (!grid_sync(a.bar, a.timeout_ns)) return;
+  if (a.apply_only) return;
+
+  for (int g = 0;; ++g) {
+    if (*(volatile int*)a.n_active == 0) break;
+    for_tiles([&](const MapDesc& M, MapState* S, int t) { a_tile<kIlu>(a, M, S, t, lane); });
+    if (!grid_sync(a.bar, a.timeout_ns)) return;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    for (int m = threadIdx.x; m < a.nmaps; m += blockDim.x)
+      if (g % a.maps[m].refresh == 0) s_any = 1;
+    __syncthreads();
+    const bool any_refresh = s_any != 0;
+    for_tiles([&](const MapDesc& M, MapState* S, int t) {
+      b_tile_sweep<KIND>(a, M, S, t, (g % M.refresh) == 0, lane);
+    });
+    if (!grid_sync(a.bar, a.timeout_ns)) return;
+    if (any_refresh) {
+      for_tiles([&](const MapDesc& M, MapState*, int t) {
+        if ((g % M.refresh) == 0) res_tile_sweep<KIND>(a, M, t, lane);
+      });
+      if (!grid_sync(a.bar, a.timeout_ns)) return;
+    }
+    sweep_phase<kSweepFwd>(a, s_bbase, ++epoch, map_active);
+    if (!grid_sync(a.bar, a.timeout_ns)) return;
+    sweep_phase<kSweepBwd>(a, s_bbase, ++epoch, map_active);
+    if (!grid_sync(a.bar, a.timeout_ns)) return;
+    for_tiles([&](const MapDesc& M, MapState* S, int t) { dots_tile(a, M, S, t, false, lane); });
+    if (!grid_sync(a.bar, a.timeout_ns)) return;
+  }
+}
+
 // Resets the per-map solver state before a PCG launch.
-__global__ void k_pcg_reset(MapState* S, int nmaps, int* n_active, Barrier* bar) {
+__global__ void k_pcg_reset(MapState* S, int nmaps, int* n_active, Barrier* bar, unsigned long long* prog,
+                            int nbands) {
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
+  for (int k = threadIdx.x; k < nbands; k += blockDim.x) prog[k] = 0ull;
   __syncthreads();
   for (int m = threadIdx.x; m < nmaps; m += blockDim.x) {
     MapState* s = S + m;
@@ -668,8 +933,14 @@ static cudaError_t launch_pcg64_kind(const Plan& pl, const PcgArgs& a, int block
 
 int pcg64_max_blocks_per_sm(int kind) {
   int nb = 0;
-  if (kind == kIdentity) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg64<kIdentity>, kThreads, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg64<kJacobi>, kThreads, 0);
+  switch (kind) {
+    case kIdentity: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg64<kIdentity>, kThreads, 0); break;
+    case kJacobi: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg64<kJacobi>, kThreads, 0); break;
+    case kIlu:
+    case kIc: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg64_sweep<kIlu>, kThreads, 0); break;
+    case kSsor: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg64_sweep<kSsor>, kThreads, 0); break;
+    default: nb = 0;
+  }
   return nb;
 }
 
@@ -677,13 +948,27 @@ cudaError_t launch_pcg64(const Plan& pl, int kind, const PcgArgs& a, cudaStream_
                          cudaEvent_t e1) {
   pl.kernel_launches += 2;
   pl.solver_launches += 1;
-  k_pcg_reset<<<1, kThreads, 0, st>>>(pl.dstate, pl.nmaps, pl.n_active, pl.bar);
+  k_pcg_reset<<<1, kThreads, 0, st>>>(pl.dstate, pl.nmaps, pl.n_active, pl.bar, pl.prog, pl.nbands);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (e0) cudaEventRecord(e0, st);
   const int blocks = pl.nsm * pl.bps;
-  e = (kind == kIdentity) ? launch_pcg64_kind<kIdentity>(pl, a, blocks, st)
-                          : launch_pcg64_kind<kJacobi>(pl, a, blocks, st);
+  switch (kind) {
+    case kIdentity: e = launch_pcg64_kind<kIdentity>(pl, a, blocks, st); break;
+    case kJacobi: e = launch_pcg64_kind<kJacobi>(pl, a, blocks, st); break;
+    case kIlu:
+    case kIc: {
+      void* args[] = {(void*)&a};
+      e = cudaLaunchCooperativeKernel((void*)k_pcg64_sweep<kIlu>, blocks, kThreads, args, 0, st);
+      break;
+    }
+    case kSsor: {
+      void* args[] = {(void*)&a};
+      e = cudaLaunchCooperativeKernel((void*)k_pcg64_sweep<kSsor>, blocks, kThreads, args, 0, st);
+      break;
+    }
+    default: e = cudaErrorInvalidValue;
+  }
   if (e == cudaSuccess && e1) e = cudaEventRecord(e1, st);
   return e;
 }

@@ -25,6 +25,8 @@ struct Plan {
   double* outer_part = nullptr;
   Barrier* bar = nullptr;
   int* n_active = nullptr;
+  unsigned long long* prog = nullptr;  // sweep progress flags of all bands
+  int nbands = 0;
   double *d_p = nullptr, *d_tau = nullptr;
   void* arena = nullptr;
   size_t arena_bytes = 0;
@@ -39,6 +41,8 @@ struct Plan {
 
 // ulp_api.cu: records msg as the calling thread's last error and returns code.
 int set_error(int code, const char* msg);
+// ulp_api.cu: rows per warp tile for n maps and the solver's resident warps.
+int default_tile_rows(int n, const int* H, const int* W, int resident_warps);
 
 // ulp_fp64.cu
 cudaError_t launch_pack(const Plan& pl, int m, const double* psi, const uint8_t* mask, const double* phi0,

@@ -35,8 +35,9 @@ struct Planes64 {
   double *phi, *phi_prev;   // current iterate, previous outer iterate
   double *r, *s, *q;        // PCG residual, preconditioned residual, A d
   double *d0, *d1;          // search direction (ping-pong)
-  double *piv;              // ILU(0)/IC(0) pivots, or D/omega for SSOR
-  double *y;                // triangular-sweep intermediate
+  double *piv;              // 1/P: inverse ILU(0)/IC(0) pivots, or omega/D for SSOR
+  double *y;                // forward-sweep result z
+  double *cw, *cn, *ce, *cs; // sweep coefficients U_{i,j-1}/P, V_{i-1,j}/P, U_{i,j}/P, V_{i,j}/P
   uint8_t* mask;            // 1 = excluded pixel
 };
 
@@ -52,9 +53,10 @@ struct MapDesc {
   int nsx, nsy;             // strips (pitch/64) and row bands
   int tile_base, ntiles;    // first tile index, number of tiles
   int refresh;              // true-residual period
+  int nbands, band_base;    // 32-row bands of the triangular sweeps
   Planes64 f;
   Planes32 h;
-  int* flags;               // wavefront tile flags (nsx * nsy ints)
+  unsigned long long* prog; // per-band sweep progress flags (epoch << 32 | columns)
 };
 
 // Mutable per-map solver state (device).
@@ -88,7 +90,7 @@ struct Barrier {
 struct PcgArgs {
   const MapDesc* maps;
   MapState* st;
-  int nmaps, ntiles, R;
+  int nmaps, ntiles, R, nbands;
   double *P0, *P1, *P2;     // per-tile partial sums
   Barrier* bar;
   int* n_active;
@@ -97,6 +99,7 @@ struct PcgArgs {
   long long lmax;
   unsigned long long timeout_ns;
   double omega;
+  int apply_only;           // sweep solvers: stop after the first s = M^-1 r (single-step entry point)
 };
 
 // ------------------------------------------------------------------ helpers

@@ -87,8 +87,11 @@ extern "C" int ulp_pcg_noalloc(const double* U, const double* V, const double* b
     if (cudaDeviceGetAttribute(&D.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
       return nfail(ULP_ERR_CUDA, "ulp_pcg_noalloc: device attributes unavailable");
-    int o1 = pcg64_max_blocks_per_sm(kIdentity), o2 = pcg64_max_blocks_per_sm(kJacobi);
-    D.bps = o1 < o2 ? o1 : o2;
+    D.bps = 1 << 30;  // the same resident blocks per SM as a plan (minimum over the solvers)
+    for (int kind : {kIdentity, kJacobi, kIlu, kSsor}) {
+      const int o = pcg64_max_blocks_per_sm(kind);
+      D.bps = o < D.bps ? o : D.bps;
+    }
     if (D.bps < 1) return nfail(ULP_ERR_CUDA, "ulp_pcg_noalloc: solver does not fit on an SM");
     D.base = p;
     D.plan.hmaps.resize(1);  // the only host allocation, once per device
@@ -101,7 +104,7 @@ extern "C" int ulp_pcg_noalloc(const double* U, const double* V, const double* b
   pl.nsm = D.nsm;
   pl.bps = D.bps;
   pl.nmaps = 1;
-  pl.R = 8;
+  pl.R = default_tile_rows(1, &H, &W, D.nsm * D.bps * kWarps);  // same tiles as ulp_pcg
   pl.bx_elem = D.nsm * 4;
   ulp_options_default(&pl.opt);
   MapDesc& M = pl.hmaps[0];

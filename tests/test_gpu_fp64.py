@@ -249,3 +249,29 @@ def test_full_size_c2_2048_properties():
     assert np.array_equal(gU.cpu().numpy(), U) and np.array_equal(gb.cpu().numpy(), A.b)
     y = native.ulp_matvec(gU, gV, phi).cpu().numpy()
     np.testing.assert_allclose(y, A.matvec(g), rtol=0, atol=1e-13 * np.abs(g).max())
+
+
+@pytest.mark.slow
+def test_full_size_c2_2048_matches_oracle_run():
+    # the oracle's own full run of this workload (tests/golden/oracle_runs.json, written by
+    # tests/golden/make_oracle_runs.py): per-pass iteration counts and phase at sampled pixels
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_runs.json")))
+    g = gold["c2_2048_p1_jacobi"]
+    m = synth.workload_map(g["workload"])
+    H, W = m.psi.shape
+    plan = native.Plan(H, W, outer_tol=g["outer_tol"])
+    phi, st = plan.unwrap(_cuda(m.psi), _cuda(m.mask, torch.uint8), p=g["p"], eps=g["tau"],
+                          precond=g["precond"], tol=g["tol"], max_outer=g["max_outer"])
+    assert st["outer"] == g["stats"]["outer"]
+    for a, b in zip(st["inner"], g["stats"]["inner"]):
+        assert abs(a - b) <= ITER_TOL, (st["inner"], g["stats"]["inner"])
+    got = phi.cpu().numpy()
+    keep = m.mask == 0
+    mean = got[keep].mean()
+    ii, jj = np.array(g["sample_i"]), np.array(g["sample_j"])
+    e = (got[ii, jj] - mean) - np.array(g["sample_phi_mean_removed"])
+    assert np.sqrt(np.mean(e ** 2)) < RMS_TOL
+    rms_phi = float(np.sqrt(np.mean((got[keep] - mean) ** 2)))
+    assert abs(rms_phi - g["rms_phi_mean_removed"]) < RMS_TOL

@@ -93,6 +93,9 @@ typedef struct ulp_options {
   int blocks_per_sm;      /* resident blocks per SM of the persistent solver; 0 = autotuned */
   double spin_timeout_s;  /* bound on any in-kernel wait, default 2.0 s */
   int profile;            /* 1: record CUDA events around every persistent solver launch (ulp_plan_counters) */
+  int graph;              /* 1: ulp_unwrap / ulp_unwrap_batched capture their kernel sequence into a CUDA
+                             graph on the first call and replay it while the arguments stay the same
+                             (ignored when profile = 1) */
 } ulp_options;
 
 /* Per-call statistics, written on the host when the call synchronises. */

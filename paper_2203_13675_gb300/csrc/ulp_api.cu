@@ -58,6 +58,10 @@ extern "C" const char* ulp_last_error(void) { return g_err.c_str(); }
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static void destroy_plan(Plan& pl) {
+  if (pl.graph_exec) cudaGraphExecDestroy(pl.graph_exec);
+  if (pl.cap_stream) cudaStreamDestroy(pl.cap_stream);
+  pl.graph_exec = nullptr;
+  pl.cap_stream = nullptr;
   for (cudaEvent_t e : pl.ev_pool) cudaEventDestroy(e);
   pl.ev_pool.clear();
   if (pl.arena) cudaFree(pl.arena);
@@ -82,6 +86,21 @@ static void next_events(Plan& pl, cudaEvent_t* e0, cudaEvent_t* e1) {
 // Rows per warp tile: about one tile per resident warp of the persistent
 // solver (static round-robin assignment, so equal counts balance the work),
 // between 4 and 64 rows so the two halo rows stay amortised.
+int ulp::solver_blocks_per_sm() {
+  int occ = 1 << 30;
+  for (int kind : {kIdentity, kJacobi}) {
+    const int o = pcg64_max_blocks_per_sm(kind), o2 = pcg32_max_blocks_per_sm(kind);
+    occ = o < occ ? o : occ;
+    occ = o2 < occ ? o2 : occ;
+  }
+  return occ;
+}
+
+int ulp::sweep_blocks_per_sm() {
+  const int a = pcg64_max_blocks_per_sm(kIlu), b = pcg64_max_blocks_per_sm(kSsor);
+  return a < b ? a : b;
+}
+
 int ulp::default_tile_rows(int n, const int* H, const int* W, int resident_warps) {
   double cells = 0.0;  // rows x 64-column strips over all maps
   for (int m = 0; m < n; ++m) cells += (double)H[m] * ((W[m] + kStrip - 1) / kStrip);
@@ -106,13 +125,10 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
   ULP_CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, pl.device));
   if (!coop) return fail(ULP_ERR_UNSUPPORTED, "device lacks cooperative launch");
   pl.nmaps = n;
-  int occ = 1 << 30;
-  for (int kind : {kIdentity, kJacobi, kIlu, kSsor}) {
-    const int o = pcg64_max_blocks_per_sm(kind);
-    occ = o < occ ? o : occ;
-  }
-  if (occ < 1) return fail(ULP_ERR_CUDA, "persistent solver does not fit on an SM");
+  const int occ = solver_blocks_per_sm();
+  if (occ < 1 || sweep_blocks_per_sm() < 1) return fail(ULP_ERR_CUDA, "persistent solver does not fit on an SM");
   pl.bps = pl.opt.blocks_per_sm > 0 && pl.opt.blocks_per_sm < occ ? pl.opt.blocks_per_sm : occ;
+  pl.bps_sweep = sweep_blocks_per_sm() < pl.bps ? sweep_blocks_per_sm() : pl.bps;
   pl.R = pl.opt.tile_rows > 0 ? pl.opt.tile_rows : default_tile_rows(n, H, W, pl.nsm * pl.bps * kWarps);
 
   // geometry and arena layout
@@ -144,6 +160,7 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
     bytes += 20 * align256(e * sizeof(double));   // FP64 planes
     bytes += 13 * align256(e * sizeof(float));    // FP32 planes
     bytes += align256(e);                         // mask
+    bytes += 2 * align256((size_t)M.nbands * M.pitch * sizeof(double));  // sweep exchange rows
   }
   pl.ntiles = tiles;
   pl.nbands = bands;
@@ -162,8 +179,6 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
   bytes += align256(sizeof(Barrier)) + align256(sizeof(int));
   const size_t off_pt = bytes;
   bytes += 2 * align256(sizeof(double) * n);
-  const size_t off_prog = bytes;
-  bytes += align256(sizeof(unsigned long long) * bands);
 
   cudaError_t e = cudaMalloc(&pl.arena, bytes);
   if (e != cudaSuccess) {
@@ -187,9 +202,11 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
                      &M.h.d0, &M.h.d1, &M.h.cw, &M.h.cn, &M.h.pinv, &M.h.y};
     for (float** q : f32) { *q = reinterpret_cast<float*>(p); p += e32; }
     M.f.mask = reinterpret_cast<uint8_t*>(p);
-    M.prog = reinterpret_cast<unsigned long long*>(base + off_prog) + M.band_base;
+    p += align256((size_t)M.H * M.pitch);
+    M.xf = reinterpret_cast<double*>(p);
+    p += align256((size_t)M.nbands * M.pitch * sizeof(double));
+    M.xb = reinterpret_cast<double*>(p);
   }
-  pl.prog = reinterpret_cast<unsigned long long*>(base + off_prog);
   pl.dmaps = reinterpret_cast<MapDesc*>(base + off_maps);
   pl.dstate = reinterpret_cast<MapState*>(base + off_state);
   pl.dstats = reinterpret_cast<MapStats*>(base + off_stats);
@@ -309,20 +326,9 @@ static int collect(Plan& pl, cudaStream_t st, ulp_stats* per_map) {
   return worst;
 }
 
-extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precond, double tol,
-                                  int max_outer, int max_inner, void* cuda_stream, ulp_stats* per_map) {
-  if (!plan || !maps) return fail(ULP_ERR_INVALID, "null argument");
-  Plan& pl = plan->p;
-  int rc = check_solver_args(precond, tol, max_outer);
-  if (rc != ULP_OK) return rc;
-  for (int m = 0; m < pl.nmaps; ++m) {
-    if (!maps[m].psi || !maps[m].phi) return fail(ULP_ERR_INVALID, "map %d: null psi or phi", m);
-    if (!(maps[m].p >= 0.0 && maps[m].p <= 2.0)) return fail(ULP_ERR_INVALID, "map %d: p outside [0, 2]", m);
-    if (!(maps[m].eps > 0.0) || !std::isfinite(maps[m].eps)) return fail(ULP_ERR_INVALID, "map %d: eps must be > 0", m);
-  }
-  ULP_CU(cudaSetDevice(pl.device));
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  pl.last_stream = st;
+// Enqueues one call of Algorithm 1 for every map of the plan on stream st.
+static int enqueue_call(Plan& pl, const ulp_map* maps, int precond, double tol, int max_outer, int max_inner,
+                        cudaStream_t st, bool mixed) {
   for (int first = 0; first < pl.nmaps; first += 64) {
     PT pt{};
     const int cnt = pl.nmaps - first < 64 ? pl.nmaps - first : 64;
@@ -330,6 +336,7 @@ extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precon
       pt.p[t] = maps[first + t].p;
       pt.tau[t] = maps[first + t].eps;
     }
+    pl.kernel_launches += 1;
     k_set_pt<<<1, 64, 0, st>>>(pt, pl.d_p, pl.d_tau, first, cnt);
   }
   ULP_CU(cudaGetLastError());
@@ -343,10 +350,77 @@ extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precon
     ULP_CU(launch_system(pl, pl.d_p, pl.d_tau, st));
     cudaEvent_t e0, e1;
     next_events(pl, &e0, &e1);
-    ULP_CU(launch_pcg64(pl, precond, a, st, e0, e1));
+    if (mixed) ULP_CU(launch_pcg32(pl, precond, a, st, e0, e1));
+    else ULP_CU(launch_pcg64(pl, precond, a, st, e0, e1));
     ULP_CU(launch_outer_error(pl, pl.opt.outer_tol, max_outer, st));
   }
   for (int m = 0; m < pl.nmaps; ++m) ULP_CU(launch_unpack(pl, m, maps[m].phi, st));
+  return ULP_OK;
+}
+
+// Replays the plan's captured call when the arguments are the ones it was
+// captured with, capturing it (on the plan's own stream) otherwise.
+static int graph_call(Plan& pl, const ulp_map* maps, int precond, double tol, int max_outer, int max_inner,
+                      cudaStream_t st, bool mixed) {
+  std::vector<unsigned char> key(sizeof(ulp_map) * pl.nmaps + sizeof(int) * 3 + sizeof(double));
+  unsigned char* k = key.data();
+  std::memcpy(k, maps, sizeof(ulp_map) * pl.nmaps);
+  k += sizeof(ulp_map) * pl.nmaps;
+  const int ints[3] = {precond, max_outer, max_inner};
+  std::memcpy(k, ints, sizeof(ints));
+  std::memcpy(k + sizeof(ints), &tol, sizeof(double));
+  if (!pl.graph_exec || key != pl.graph_key) {
+    if (pl.graph_exec) {
+      cudaGraphExecDestroy(pl.graph_exec);
+      pl.graph_exec = nullptr;
+    }
+    if (!pl.cap_stream) ULP_CU(cudaStreamCreateWithFlags(&pl.cap_stream, cudaStreamNonBlocking));
+    const long long before = pl.kernel_launches;
+    ULP_CU(cudaStreamBeginCapture(pl.cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_call(pl, maps, precond, tol, max_outer, max_inner, pl.cap_stream, mixed);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(pl.cap_stream, &g);
+    if (rc != ULP_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(ULP_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&pl.graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      pl.graph_exec = nullptr;
+      return fail(ULP_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    pl.graph_key = key;
+    pl.graph_kernels = pl.kernel_launches - before;
+    pl.kernel_launches = before;
+  }
+  ULP_CU(cudaGraphLaunch(pl.graph_exec, st));
+  pl.kernel_launches += pl.graph_kernels;
+  pl.solver_launches += max_outer;
+  return ULP_OK;
+}
+
+extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precond, double tol,
+                                  int max_outer, int max_inner, void* cuda_stream, ulp_stats* per_map) {
+  if (!plan || !maps) return fail(ULP_ERR_INVALID, "null argument");
+  Plan& pl = plan->p;
+  int rc = check_solver_args(precond, tol, max_outer);
+  if (rc != ULP_OK) return rc;
+  const bool mixed = pl.opt.precision == ULP_PRECISION_MIXED;
+  if (mixed && precond != ULP_PRECOND_IDENTITY && precond != ULP_PRECOND_JACOBI)
+    return fail(ULP_ERR_UNSUPPORTED, "mixed precision supports the identity and Jacobi preconditioners");
+  for (int m = 0; m < pl.nmaps; ++m) {
+    if (!maps[m].psi || !maps[m].phi) return fail(ULP_ERR_INVALID, "map %d: null psi or phi", m);
+    if (!(maps[m].p >= 0.0 && maps[m].p <= 2.0)) return fail(ULP_ERR_INVALID, "map %d: p outside [0, 2]", m);
+    if (!(maps[m].eps > 0.0) || !std::isfinite(maps[m].eps)) return fail(ULP_ERR_INVALID, "map %d: eps must be > 0", m);
+  }
+  ULP_CU(cudaSetDevice(pl.device));
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  pl.last_stream = st;
+  if (pl.opt.graph && !pl.opt.profile) rc = graph_call(pl, maps, precond, tol, max_outer, max_inner, st, mixed);
+  else rc = enqueue_call(pl, maps, precond, tol, max_outer, max_inner, st, mixed);
+  if (rc != ULP_OK) return rc;
   if (per_map) return collect(pl, st, per_map);
   pl.last_status = ULP_OK;
   return ULP_OK;

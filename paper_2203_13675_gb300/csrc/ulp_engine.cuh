@@ -1,0 +1,222 @@
+// ulp_engine.cuh -- pieces of the persistent PCG engine shared by the FP64 and
+// mixed-precision solvers: the FP64 sliding-window stencil walker, tile
+// geometry, and the per-map finisher that advances Algorithm 1's scalars
+// (alpha, beta, delta, stop tests) from fixed-order sums of per-tile partials.
+#pragma once
+#include "ulp_internal.cuh"
+
+namespace ulp {
+
+// ------------------------------------------------------------------ stencil walker
+// Sliding-window 5-point stencil over one warp tile (64 columns x rows i0..i1-1):
+// each lane owns columns j, j+1; north/south neighbours come from the window,
+// east/west from the neighbouring lanes, the two tile-edge columns from a halo
+// load by lanes 0 and 31.  X supplies the vector being multiplied in two
+// stages so that loads run one row ahead of the arithmetic:
+//   X::Raw X::load(i, j)   -- the planes behind x at (i, j), (i, j+1)
+//   double2 X::make(raw)   -- x itself
+//   double X::at(i, c)     -- x at one column (halo lanes)
+template <class X, class Epi>
+__device__ __forceinline__ void stencil_tile(const MapDesc& M, int i0, int i1, int j0, int lane,
+                                             const double* U, const double* V, const double* D,
+                                             const X& x, Epi& epi) {
+  using Raw = typename X::Raw;
+  const int j = j0 + 2 * lane;
+  const bool hw = (lane == 0) && (j0 > 0);
+  const bool he = (lane == 31) && (j0 + kStrip < M.pitch);
+  const bool halo = hw || he;
+  const int hc = (lane == 0) ? j0 - 1 : j0 + kStrip;
+  const size_t P = (size_t)M.pitch;
+  const double2 z2 = make_double2(0.0, 0.0);
+  double2 xn = z2, vn = z2;
+  if (i0 > 0) {
+    xn = x.make(x.load(i0 - 1, j));
+    vn = ld2(V, (size_t)(i0 - 1) * P + j);
+  }
+  double2 xc = x.make(x.load(i0, j));
+  Raw rs = (i0 + 1 < M.H) ? x.load(i0 + 1, j) : X::zero();   // row i+1, raw
+  size_t off = (size_t)i0 * P + j;
+  double2 u = ld2(U, off), v = ld2(V, off), dd = ld2(D, off);
+  double h = halo ? x.at(i0, hc) : 0.0;
+  double uwh = hw ? ld1(U, (size_t)i0 * P + hc) : 0.0;
+  for (int i = i0; i < i1; ++i) {
+    // loads for the next row, issued before this row's arithmetic
+    const bool more = i + 1 < i1;
+    const size_t off2 = off + P;
+    Raw rs2 = (more && i + 2 < M.H) ? x.load(i + 2, j) : X::zero();
+    double2 u2 = z2, v2 = z2, dd2 = z2;
+    double h2 = 0.0, uwh2 = 0.0;
+    if (more) {
+      u2 = ld2(U, off2);
+      v2 = ld2(V, off2);
+      dd2 = ld2(D, off2);
+      if (halo) h2 = x.at(i + 1, hc);
+      if (hw) uwh2 = ld1(U, (size_t)(i + 1) * P + hc);
+    }
+    const double2 xs = (i + 1 < M.H) ? x.make(rs) : z2;
+    double west = __shfl_up_sync(kFull, xc.y, 1);
+    double east = __shfl_down_sync(kFull, xc.x, 1);
+    double uw = __shfl_up_sync(kFull, u.y, 1);
+    if (lane == 0) { west = h; uw = uwh; }
+    if (lane == 31) east = h;
+    double2 ax;
+    ax.x = dd.x * xc.x;
+    ax.x = fma(-u.x, xc.y, ax.x);
+    ax.x = fma(-uw, west, ax.x);
+    ax.x = fma(-v.x, xs.x, ax.x);
+    ax.x = fma(-vn.x, xn.x, ax.x);
+    ax.y = dd.y * xc.y;
+    ax.y = fma(-u.y, east, ax.y);
+    ax.y = fma(-u.x, xc.x, ax.y);
+    ax.y = fma(-v.y, xs.y, ax.y);
+    ax.y = fma(-vn.y, xn.y, ax.y);
+    epi(off, xc, ax);
+    xn = xc;
+    xc = xs;
+    vn = v;
+    rs = rs2;
+    u = u2;
+    v = v2;
+    dd = dd2;
+    h = h2;
+    uwh = uwh2;
+    off = off2;
+  }
+}
+
+struct XPlane {  // plain vector
+  const double* x;
+  size_t P;
+  using Raw = double2;
+  __device__ __forceinline__ static Raw zero() { return make_double2(0.0, 0.0); }
+  __device__ __forceinline__ Raw load(int i, int j) const { return ld2(x, (size_t)i * P + j); }
+  __device__ __forceinline__ double2 make(const Raw& r) const { return r; }
+  __device__ __forceinline__ double at(int i, int c) const { return ld1(x, (size_t)i * P + c); }
+};
+
+struct XDir {  // d = s + beta d_old, or d = s on the first iteration (Algorithm 1)
+  const double* s;
+  const double* dold;
+  double beta;
+  bool first;
+  size_t P;
+  struct Raw {
+    double2 s, d;
+  };
+  __device__ __forceinline__ static Raw zero() { return Raw{make_double2(0.0, 0.0), make_double2(0.0, 0.0)}; }
+  __device__ __forceinline__ Raw load(int i, int j) const {
+    const size_t off = (size_t)i * P + j;
+    Raw r;
+    r.s = ld2(s, off);
+    r.d = first ? make_double2(0.0, 0.0) : ld2(dold, off);
+    return r;
+  }
+  __device__ __forceinline__ double2 make(const Raw& r) const {
+    if (first) return r.s;
+    return make_double2(fma(beta, r.d.x, r.s.x), fma(beta, r.d.y, r.s.y));
+  }
+  __device__ __forceinline__ double at(int i, int c) const {
+    const size_t off = (size_t)i * P + c;
+    const double sv = ld1(s, off);
+    return first ? sv : fma(beta, ld1(dold, off), sv);
+  }
+};
+
+struct TileGeo {
+  int i0, i1, j0;
+};
+__device__ __forceinline__ TileGeo tile_geo(const MapDesc& M, int t, int R) {
+  const int lt = t - M.tile_base;
+  const int sy = lt / M.nsx, sx = lt - sy * M.nsx;
+  TileGeo g;
+  g.i0 = sy * R;
+  g.i1 = min(g.i0 + R, M.H);
+  g.j0 = sx * kStrip;
+  return g;
+}
+
+// ------------------------------------------------------------------ PCG engine
+enum Phase { kPhResInit = 0, kPhA = 1, kPhB = 2, kPhRes = 3 };
+
+// Runs in the warp whose tile arrival completed phase `ph` for map m: reduces
+// the map's tile partials in a fixed order and advances its scalars
+// (alpha = delta_new / d^T q; delta_old, delta_new, beta; stop tests).
+__device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, MapState* Sp, int ph, int lane) {
+  volatile MapState* S = Sp;
+  const int base = M.tile_base, n = M.ntiles;
+  const double v0 = warp_sum_partials(a.P0 + base, n, lane);
+  double v1 = 0.0, v2 = 0.0;
+  if (ph != kPhA) v1 = warp_sum_partials(a.P1 + base, n, lane);
+  if (ph == kPhResInit) v2 = warp_sum_partials(a.P2 + base, n, lane);
+  if (lane == 0) {
+    bool done = false;
+    if (ph == kPhA) {
+      S->dq = v0;
+      if (!(v0 > 0.0) || !isfinite(v0)) {  // breakdown: stop after this iteration
+        S->status = -3;
+        S->alpha = 0.0;
+        S->stop_after = 1;
+      } else {
+        S->alpha = S->delta / v0;
+      }
+    } else {
+      if (ph == kPhResInit) {
+        S->delta = v0;
+        S->delta0 = v0;
+        S->rr = v1;
+        S->bb = v2;
+        S->iter = 0;
+      } else {
+        const double dold = S->delta;
+        S->delta = v0;
+        S->rr = v1;
+        S->beta = v0 / dold;
+        S->iter += 1;
+      }
+      const double tol2 = a.tol2;
+      const bool conv = (a.stop_mode == 1) ? !(S->delta > tol2 * S->delta0) : !(S->rr > tol2 * S->bb);
+      S->relres = (S->bb > 0.0) ? sqrt(S->rr / S->bb) : 0.0;
+      if (S->stop_after) {
+        done = true;
+      } else if (S->bb == 0.0 || conv) {
+        done = true;
+        S->status = 0;
+      } else if (S->iter >= (a.lmax > 0 ? a.lmax : 2LL * M.H * M.W)) {
+        done = true;
+        S->status = 1;
+      }
+    }
+    S->arrive = 0u;
+    if (done) {
+      S->done = 1;
+      __threadfence();
+      atomicSub(a.n_active, 1);
+    }
+    __threadfence();
+  }
+  __syncwarp();
+}
+
+// Publishes this warp's tile partials and runs the map's finisher if this was
+// the last tile of the map in this phase.
+__device__ __forceinline__ void tile_arrive(const PcgArgs& a, const MapDesc& M, MapState* S, int t,
+                                            int ph, double v0, double v1, double v2, int lane) {
+  v0 = warp_sum(v0);
+  if (ph != kPhA) v1 = warp_sum(v1);
+  if (ph == kPhResInit) v2 = warp_sum(v2);
+  unsigned old = 0;
+  if (lane == 0) {
+    __stcg(a.P0 + t, v0);
+    if (ph != kPhA) __stcg(a.P1 + t, v1);
+    if (ph == kPhResInit) __stcg(a.P2 + t, v2);
+    __threadfence();
+    old = atomicAdd(&S->arrive, 1u);
+  }
+  old = __shfl_sync(kFull, old, 0);
+  if (old == (unsigned)M.ntiles - 1u) {
+    __threadfence();
+    finish_map(a, M, S, ph, lane);
+  }
+}
+
+}  // namespace ulp

@@ -5,6 +5,7 @@
 #include "ulp_internal.cuh"
 #include "ulp_host.h"
 #include "ulp_sweep.cuh"
+#include "ulp_engine.cuh"
 
 #include <math.h>
 
@@ -116,218 +117,6 @@ __global__ void k_system(const MapDesc* __restrict__ maps, MapState* S) {
     M.f.D[t] = d;
     M.f.Dinv[t] = (d > 0.0) ? __drcp_rn(d) : 0.0;
     M.f.b[t] = bk;
-  }
-}
-
-// ------------------------------------------------------------------ stencil walker
-// Sliding-window 5-point stencil over one warp tile (64 columns x rows i0..i1-1):
-// each lane owns columns j, j+1; north/south neighbours come from the window,
-// east/west from the neighbouring lanes, the two tile-edge columns from a halo
-// load by lanes 0 and 31.  X supplies the vector being multiplied in two
-// stages so that loads run one row ahead of the arithmetic:
-//   X::Raw X::load(i, j)   -- the planes behind x at (i, j), (i, j+1)
-//   double2 X::make(raw)   -- x itself
-//   double X::at(i, c)     -- x at one column (halo lanes)
-template <class X, class Epi>
-__device__ __forceinline__ void stencil_tile(const MapDesc& M, int i0, int i1, int j0, int lane,
-                                             const double* U, const double* V, const double* D,
-                                             const X& x, Epi& epi) {
-  using Raw = typename X::Raw;
-  const int j = j0 + 2 * lane;
-  const bool hw = (lane == 0) && (j0 > 0);
-  const bool he = (lane == 31) && (j0 + kStrip < M.pitch);
-  const bool halo = hw || he;
-  const int hc = (lane == 0) ? j0 - 1 : j0 + kStrip;
-  const size_t P = (size_t)M.pitch;
-  const double2 z2 = make_double2(0.0, 0.0);
-  double2 xn = z2, vn = z2;
-  if (i0 > 0) {
-    xn = x.make(x.load(i0 - 1, j));
-    vn = ld2(V, (size_t)(i0 - 1) * P + j);
-  }
-  double2 xc = x.make(x.load(i0, j));
-  Raw rs = (i0 + 1 < M.H) ? x.load(i0 + 1, j) : X::zero();   // row i+1, raw
-  size_t off = (size_t)i0 * P + j;
-  double2 u = ld2(U, off), v = ld2(V, off), dd = ld2(D, off);
-  double h = halo ? x.at(i0, hc) : 0.0;
-  double uwh = hw ? ld1(U, (size_t)i0 * P + hc) : 0.0;
-  for (int i = i0; i < i1; ++i) {
-    // loads for the next row, issued before this row's arithmetic
-    const bool more = i + 1 < i1;
-    const size_t off2 = off + P;
-    Raw rs2 = (more && i + 2 < M.H) ? x.load(i + 2, j) : X::zero();
-    double2 u2 = z2, v2 = z2, dd2 = z2;
-    double h2 = 0.0, uwh2 = 0.0;
-    if (more) {
-      u2 = ld2(U, off2);
-      v2 = ld2(V, off2);
-      dd2 = ld2(D, off2);
-      if (halo) h2 = x.at(i + 1, hc);
-      if (hw) uwh2 = ld1(U, (size_t)(i + 1) * P + hc);
-    }
-    const double2 xs = (i + 1 < M.H) ? x.make(rs) : z2;
-    double west = __shfl_up_sync(kFull, xc.y, 1);
-    double east = __shfl_down_sync(kFull, xc.x, 1);
-    double uw = __shfl_up_sync(kFull, u.y, 1);
-    if (lane == 0) { west = h; uw = uwh; }
-    if (lane == 31) east = h;
-    double2 ax;
-    ax.x = dd.x * xc.x;
-    ax.x = fma(-u.x, xc.y, ax.x);
-    ax.x = fma(-uw, west, ax.x);
-    ax.x = fma(-v.x, xs.x, ax.x);
-    ax.x = fma(-vn.x, xn.x, ax.x);
-    ax.y = dd.y * xc.y;
-    ax.y = fma(-u.y, east, ax.y);
-    ax.y = fma(-u.x, xc.x, ax.y);
-    ax.y = fma(-v.y, xs.y, ax.y);
-    ax.y = fma(-vn.y, xn.y, ax.y);
-    epi(off, xc, ax);
-    xn = xc;
-    xc = xs;
-    vn = v;
-    rs = rs2;
-    u = u2;
-    v = v2;
-    dd = dd2;
-    h = h2;
-    uwh = uwh2;
-    off = off2;
-  }
-}
-
-struct XPlane {  // plain vector
-  const double* x;
-  size_t P;
-  using Raw = double2;
-  __device__ __forceinline__ static Raw zero() { return make_double2(0.0, 0.0); }
-  __device__ __forceinline__ Raw load(int i, int j) const { return ld2(x, (size_t)i * P + j); }
-  __device__ __forceinline__ double2 make(const Raw& r) const { return r; }
-  __device__ __forceinline__ double at(int i, int c) const { return ld1(x, (size_t)i * P + c); }
-};
-
-struct XDir {  // d = s + beta d_old, or d = s on the first iteration (Algorithm 1)
-  const double* s;
-  const double* dold;
-  double beta;
-  bool first;
-  size_t P;
-  struct Raw {
-    double2 s, d;
-  };
-  __device__ __forceinline__ static Raw zero() { return Raw{make_double2(0.0, 0.0), make_double2(0.0, 0.0)}; }
-  __device__ __forceinline__ Raw load(int i, int j) const {
-    const size_t off = (size_t)i * P + j;
-    Raw r;
-    r.s = ld2(s, off);
-    r.d = first ? make_double2(0.0, 0.0) : ld2(dold, off);
-    return r;
-  }
-  __device__ __forceinline__ double2 make(const Raw& r) const {
-    if (first) return r.s;
-    return make_double2(fma(beta, r.d.x, r.s.x), fma(beta, r.d.y, r.s.y));
-  }
-  __device__ __forceinline__ double at(int i, int c) const {
-    const size_t off = (size_t)i * P + c;
-    const double sv = ld1(s, off);
-    return first ? sv : fma(beta, ld1(dold, off), sv);
-  }
-};
-
-struct TileGeo {
-  int i0, i1, j0;
-};
-__device__ __forceinline__ TileGeo tile_geo(const MapDesc& M, int t, int R) {
-  const int lt = t - M.tile_base;
-  const int sy = lt / M.nsx, sx = lt - sy * M.nsx;
-  TileGeo g;
-  g.i0 = sy * R;
-  g.i1 = min(g.i0 + R, M.H);
-  g.j0 = sx * kStrip;
-  return g;
-}
-
-// ------------------------------------------------------------------ PCG engine
-enum Phase { kPhResInit = 0, kPhA = 1, kPhB = 2, kPhRes = 3 };
-
-// Runs in the warp whose tile arrival completed phase `ph` for map m: reduces
-// the map's tile partials in a fixed order and advances its scalars
-// (alpha = delta_new / d^T q; delta_old, delta_new, beta; stop tests).
-__device__ void finish_map(const PcgArgs& a, const MapDesc& M, MapState* Sp, int ph, int lane) {
-  volatile MapState* S = Sp;
-  const int base = M.tile_base, n = M.ntiles;
-  const double v0 = warp_sum_partials(a.P0 + base, n, lane);
-  double v1 = 0.0, v2 = 0.0;
-  if (ph != kPhA) v1 = warp_sum_partials(a.P1 + base, n, lane);
-  if (ph == kPhResInit) v2 = warp_sum_partials(a.P2 + base, n, lane);
-  if (lane == 0) {
-    bool done = false;
-    if (ph == kPhA) {
-      S->dq = v0;
-      if (!(v0 > 0.0) || !isfinite(v0)) {  // breakdown: stop after this iteration
-        S->status = -3;
-        S->alpha = 0.0;
-        S->stop_after = 1;
-      } else {
-        S->alpha = S->delta / v0;
-      }
-    } else {
-      if (ph == kPhResInit) {
-        S->delta = v0;
-        S->delta0 = v0;
-        S->rr = v1;
-        S->bb = v2;
-        S->iter = 0;
-      } else {
-        const double dold = S->delta;
-        S->delta = v0;
-        S->rr = v1;
-        S->beta = v0 / dold;
-        S->iter += 1;
-      }
-      const double tol2 = a.tol2;
-      const bool conv = (a.stop_mode == 1) ? !(S->delta > tol2 * S->delta0) : !(S->rr > tol2 * S->bb);
-      S->relres = (S->bb > 0.0) ? sqrt(S->rr / S->bb) : 0.0;
-      if (S->stop_after) {
-        done = true;
-      } else if (S->bb == 0.0 || conv) {
-        done = true;
-        S->status = 0;
-      } else if (S->iter >= (a.lmax > 0 ? a.lmax : 2LL * M.H * M.W)) {
-        done = true;
-        S->status = 1;
-      }
-    }
-    S->arrive = 0u;
-    if (done) {
-      S->done = 1;
-      __threadfence();
-      atomicSub(a.n_active, 1);
-    }
-    __threadfence();
-  }
-  __syncwarp();
-}
-
-// Publishes this warp's tile partials and runs the map's finisher if this was
-// the last tile of the map in this phase.
-__device__ __forceinline__ void tile_arrive(const PcgArgs& a, const MapDesc& M, MapState* S, int t,
-                                            int ph, double v0, double v1, double v2, int lane) {
-  v0 = warp_sum(v0);
-  if (ph != kPhA) v1 = warp_sum(v1);
-  if (ph == kPhResInit) v2 = warp_sum(v2);
-  unsigned old = 0;
-  if (lane == 0) {
-    __stcg(a.P0 + t, v0);
-    if (ph != kPhA) __stcg(a.P1 + t, v1);
-    if (ph == kPhResInit) __stcg(a.P2 + t, v2);
-    __threadfence();
-    old = atomicAdd(&S->arrive, 1u);
-  }
-  old = __shfl_sync(kFull, old, 0);
-  if (old == (unsigned)M.ntiles - 1u) {
-    __threadfence();
-    finish_map(a, M, S, ph, lane);
   }
 }
 
@@ -617,8 +406,7 @@ __device__ __forceinline__ void coef_tile(const PcgArgs& a, const MapDesc& M, in
 // backward sweeps in decreasing order, so every wait is on a band that an
 // earlier-ordered slot step has already been given (no cycle).
 template <int MODE>
-__device__ bool sweep_phase(const PcgArgs& a, const int* s_bbase, unsigned long long epoch,
-                            bool (*want)(const MapState*)) {
+__device__ bool sweep_phase(const PcgArgs& a, const int* s_bbase, bool (*want)(const MapState*)) {
   const int lane = threadIdx.x & 31;
   const int slot = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   const int NS = gridDim.x * kWarps;
@@ -628,20 +416,45 @@ __device__ bool sweep_phase(const PcgArgs& a, const int* s_bbase, unsigned long 
     MapState* S = a.st + m;
     if (!want(S)) continue;
     const MapDesc& M = a.maps[m];
+    const int band = gb - M.band_base, nb = M.nbands;
+    const size_t P = M.pitch;
     SweepIO io;
-    if (MODE == kSweepPiv) io = SweepIO{M.f.D, M.f.U, M.f.V, M.f.piv};
-    else if (MODE == kSweepFwd) io = SweepIO{M.f.s, M.f.cw, M.f.cn, M.f.y};
-    else io = SweepIO{M.f.y, M.f.ce, M.f.cs, M.f.s};
-    if (!band_sweep<MODE>(M, gb - M.band_base, lane, M.prog, epoch, io, a.timeout_ns, &a.bar->err))
+    if (MODE == kSweepBwd) {
+      io = SweepIO{M.f.y, M.f.ce, M.f.cs, M.f.s, nullptr, nullptr};
+      if (band + 1 < nb) io.xin = M.xb + (size_t)(band + 1) * P;
+      if (band > 0) io.xout = M.xb + (size_t)band * P;
+    } else {
+      if (MODE == kSweepPiv) io = SweepIO{M.f.D, M.f.U, M.f.V, M.f.piv, nullptr, nullptr};
+      else io = SweepIO{M.f.s, M.f.cw, M.f.cn, M.f.y, nullptr, nullptr};
+      if (band > 0) io.xin = M.xf + (size_t)(band - 1) * P;
+      if (band + 1 < nb) io.xout = M.xf + (size_t)band * P;
+    }
+    if (!band_sweep<MODE>(M, band, lane, io, a.timeout_ns, &a.bar->err))
       return false;  // the error flag is set: the next grid barrier ends every block
   }
   return true;
 }
 
+// Fills every exchange row with the sentinel (start of a launch).
+__device__ void reset_exchange(const PcgArgs& a, const int* s_bbase) {
+  const int lane = threadIdx.x & 31;
+  const int slot = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const int NS = gridDim.x * kWarps;
+  for (int gb = slot; gb < a.nbands; gb += NS) {
+    const int m = find_map(s_bbase, a.nmaps, gb);
+    const MapDesc& M = a.maps[m];
+    const size_t off = (size_t)(gb - M.band_base) * M.pitch;
+    for (int j = lane; j < M.pitch; j += 32) {
+      st_relaxed(M.xf + off + j, sentinel());
+      st_relaxed(M.xb + off + j, sentinel());
+    }
+  }
+}
+
 __device__ bool map_active(const MapState* S) { return *(volatile const int*)&S->done == 0; }
 
 template <int KIND>
-__global__ void __launch_bounds__(kThreads, 2) k_pcg64_sweep(PcgArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) k_pcg64_sweep(PcgArgs a) {
   __shared__ int s_base[kMaxMaps + 1];
   __shared__ int s_bbase[kMaxMaps + 1];
   __shared__ int s_any;
@@ -653,7 +466,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_pcg64_sweep(PcgArgs a) {
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int NW = gridDim.x * kWarps;
-  unsigned long long epoch = 0;
   auto for_tiles = [&](auto&& body) {
     for (int t = gw; t < a.ntiles; t += NW) {
       const int m = find_map(s_base, a.nmaps, t);
@@ -663,9 +475,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_pcg64_sweep(PcgArgs a) {
     }
   };
 
+  reset_exchange(a, s_bbase);
+  if (!grid_sync(a.bar, a.timeout_ns)) return;
   // preconditioner set-up (Algorithm 1: estimate M from A)
   if (KIND == kIlu) {
-    sweep_phase<kSweepPiv>(a, s_bbase, ++epoch, map_active);
+    sweep_phase<kSweepPiv>(a, s_bbase, map_active);
     if (!grid_sync(a.bar, a.timeout_ns)) return;
   }
   for_tiles([&](const MapDesc& M, MapState*, int t) { coef_tile<KIND>(a, M, t, lane); });
@@ -673,9 +487,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_pcg64_sweep(PcgArgs a) {
   // r = b - A phi, d = M^-1 r, delta_new = r^T d
   for_tiles([&](const MapDesc& M, MapState*, int t) { res_tile_sweep<KIND>(a, M, t, lane); });
   if (!grid_sync(a.bar, a.timeout_ns)) return;
-  sweep_phase<kSweepFwd>(a, s_bbase, ++epoch, map_active);
+  sweep_phase<kSweepFwd>(a, s_bbase, map_active);
   if (!grid_sync(a.bar, a.timeout_ns)) return;
-  sweep_phase<kSweepBwd>(a, s_bbase, ++epoch, map_active);
+  sweep_phase<kSweepBwd>(a, s_bbase, map_active);
   if (!grid_sync(a.bar, a.timeout_ns)) return;
   for_tiles([&](const MapDesc& M, MapState* S, int t) { dots_tile(a, M, S, t, true, lane); });
   if (!grid_sync(a.bar, a.timeout_ns)) return;
@@ -701,9 +515,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_pcg64_sweep(PcgArgs a) {
       });
       if (!grid_sync(a.bar, a.timeout_ns)) return;
     }
-    sweep_phase<kSweepFwd>(a, s_bbase, ++epoch, map_active);
+    sweep_phase<kSweepFwd>(a, s_bbase, map_active);
     if (!grid_sync(a.bar, a.timeout_ns)) return;
-    sweep_phase<kSweepBwd>(a, s_bbase, ++epoch, map_active);
+    sweep_phase<kSweepBwd>(a, s_bbase, map_active);
     if (!grid_sync(a.bar, a.timeout_ns)) return;
     for_tiles([&](const MapDesc& M, MapState* S, int t) { dots_tile(a, M, S, t, false, lane); });
     if (!grid_sync(a.bar, a.timeout_ns)) return;
@@ -711,11 +525,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_pcg64_sweep(PcgArgs a) {
 }
 
 // Resets the per-map solver state before a PCG launch.
-__global__ void k_pcg_reset(MapState* S, int nmaps, int* n_active, Barrier* bar, unsigned long long* prog,
-                            int nbands) {
+__global__ void k_pcg_reset(MapState* S, int nmaps, int* n_active, Barrier* bar) {
   __shared__ int s_cnt;
   if (threadIdx.x == 0) s_cnt = 0;
-  for (int k = threadIdx.x; k < nbands; k += blockDim.x) prog[k] = 0ull;
   __syncthreads();
   for (int m = threadIdx.x; m < nmaps; m += blockDim.x) {
     MapState* s = S + m;
@@ -944,11 +756,15 @@ int pcg64_max_blocks_per_sm(int kind) {
   return nb;
 }
 
+void launch_pcg_reset(const Plan& pl, cudaStream_t st) {
+  k_pcg_reset<<<1, kThreads, 0, st>>>(pl.dstate, pl.nmaps, pl.n_active, pl.bar);
+}
+
 cudaError_t launch_pcg64(const Plan& pl, int kind, const PcgArgs& a, cudaStream_t st, cudaEvent_t e0,
                          cudaEvent_t e1) {
   pl.kernel_launches += 2;
   pl.solver_launches += 1;
-  k_pcg_reset<<<1, kThreads, 0, st>>>(pl.dstate, pl.nmaps, pl.n_active, pl.bar, pl.prog, pl.nbands);
+  k_pcg_reset<<<1, kThreads, 0, st>>>(pl.dstate, pl.nmaps, pl.n_active, pl.bar);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (e0) cudaEventRecord(e0, st);
@@ -959,12 +775,12 @@ cudaError_t launch_pcg64(const Plan& pl, int kind, const PcgArgs& a, cudaStream_
     case kIlu:
     case kIc: {
       void* args[] = {(void*)&a};
-      e = cudaLaunchCooperativeKernel((void*)k_pcg64_sweep<kIlu>, blocks, kThreads, args, 0, st);
+      e = cudaLaunchCooperativeKernel((void*)k_pcg64_sweep<kIlu>, pl.nsm * pl.bps_sweep, kThreads, args, 0, st);
       break;
     }
     case kSsor: {
       void* args[] = {(void*)&a};
-      e = cudaLaunchCooperativeKernel((void*)k_pcg64_sweep<kSsor>, blocks, kThreads, args, 0, st);
+      e = cudaLaunchCooperativeKernel((void*)k_pcg64_sweep<kSsor>, pl.nsm * pl.bps_sweep, kThreads, args, 0, st);
       break;
     }
     default: e = cudaErrorInvalidValue;

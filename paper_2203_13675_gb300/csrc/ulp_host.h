@@ -25,8 +25,8 @@ struct Plan {
   double* outer_part = nullptr;
   Barrier* bar = nullptr;
   int* n_active = nullptr;
-  unsigned long long* prog = nullptr;  // sweep progress flags of all bands
   int nbands = 0;
+  int bps_sweep = 1;         // resident blocks per SM of the sweep solvers
   double *d_p = nullptr, *d_tau = nullptr;
   void* arena = nullptr;
   size_t arena_bytes = 0;
@@ -37,12 +37,21 @@ struct Plan {
   mutable long long solver_launches = 0;
   std::vector<cudaEvent_t> ev_pool;      // pairs (start, stop) recorded around solver launches
   size_t ev_used = 0;
+  // captured call (options.graph): the executable graph, the arguments it was captured with
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<unsigned char> graph_key;
+  long long graph_kernels = 0;
 };
 
 // ulp_api.cu: records msg as the calling thread's last error and returns code.
 int set_error(int code, const char* msg);
 // ulp_api.cu: rows per warp tile for n maps and the solver's resident warps.
 int default_tile_rows(int n, const int* H, const int* W, int resident_warps);
+// ulp_api.cu: resident blocks per SM that fix the tile geometry (FP64 and mixed
+// Jacobi / identity solvers), and those of the sweep solvers.
+int solver_blocks_per_sm();
+int sweep_blocks_per_sm();
 
 // ulp_fp64.cu
 cudaError_t launch_pack(const Plan& pl, int m, const double* psi, const uint8_t* mask, const double* phi0,
@@ -56,6 +65,12 @@ cudaError_t launch_outer_error(const Plan& pl, double outer_tol, int max_outer, 
 cudaError_t launch_pcg64(const Plan& pl, int kind, const PcgArgs& a, cudaStream_t st, cudaEvent_t e0 = nullptr,
                          cudaEvent_t e1 = nullptr);
 int pcg64_max_blocks_per_sm(int kind);
+void launch_pcg_reset(const Plan& pl, cudaStream_t st);
+
+// ulp_mixed.cu
+cudaError_t launch_pcg32(const Plan& pl, int kind, const PcgArgs& a, cudaStream_t st, cudaEvent_t e0 = nullptr,
+                         cudaEvent_t e1 = nullptr);
+int pcg32_max_blocks_per_sm(int kind);
 cudaError_t launch_matvec(const Plan& pl, const double* x, double* y, cudaStream_t st);
 cudaError_t launch_jacobi_apply(const Plan& pl, int kind, const double* r, double* s, cudaStream_t st);
 cudaError_t launch_to_plane(const Plan& pl, const double* src, double* dst, cudaStream_t st);

@@ -56,7 +56,7 @@ struct MapDesc {
   int nbands, band_base;    // 32-row bands of the triangular sweeps
   Planes64 f;
   Planes32 h;
-  unsigned long long* prog; // per-band sweep progress flags (epoch << 32 | columns)
+  double *xf, *xb;          // sweep exchange rows: last row of each band (forward), first row (backward)
 };
 
 // Mutable per-map solver state (device).

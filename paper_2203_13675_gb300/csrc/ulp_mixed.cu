@@ -1,0 +1,360 @@
+// ulp_mixed.cu -- mixed-precision inner solve of Algorithm 1 (reliable-update PCG).
+//
+// The Krylov recurrence runs on FP32 planes: search direction d, A d, the
+// residual r, the preconditioned residual s and the correction x gathered
+// since the last refresh, with FP32 copies of the Eq. (UV) weights and the
+// diagonal formed on the fly from them.  FP64 is kept where it decides the
+// answer:
+//   - the inner products behind alpha and beta are accumulated per lane as
+//     double-float pairs (exact FP32 products, compensated sums) and summed
+//     across lanes and tiles in FP64, so they are FP64-accurate;
+//   - alpha, beta, delta and the stop tests are FP64 (the shared finisher);
+//   - phi itself stays FP64: every refresh period (Algorithm 1's true-residual
+//     step, every 20 iterations here) the FP32 correction is folded into phi
+//     and r = b - A phi is recomputed with the FP64 weights and FP64 phi.
+// Bytes per pixel per iteration: 24 (phase A) + 32 (phase B) versus 112 in FP64.
+#include "ulp_engine.cuh"
+#include "ulp_host.h"
+
+namespace ulp {
+
+// Double-float accumulator of FP32 products: a*b = p + e exactly (FMA), and
+// the running sum is carried as hi + lo with Knuth's two-sum.
+struct DF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ float2 ldf2(const float* base, size_t off) {
+  return __ldcg(reinterpret_cast<const float2*>(base + off));
+}
+__device__ __forceinline__ void stf2(float* base, size_t off, float2 v) {
+  __stcg(reinterpret_cast<float2*>(base + off), v);
+}
+
+struct XDir32 {  // d = s + beta d_old (FP32), d = s on the first iteration
+  const float* s;
+  const float* dold;
+  float beta;
+  bool first;
+  size_t P;
+  struct Raw {
+    float2 s, d;
+  };
+  __device__ __forceinline__ static Raw zero() { return Raw{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+  __device__ __forceinline__ Raw load(int i, int j) const {
+    const size_t off = (size_t)i * P + j;
+    Raw r;
+    r.s = ldf2(s, off);
+    r.d = first ? make_float2(0.f, 0.f) : ldf2(dold, off);
+    return r;
+  }
+  __device__ __forceinline__ float2 make(const Raw& r) const {
+    if (first) return r.s;
+    return make_float2(__fmaf_rn(beta, r.d.x, r.s.x), __fmaf_rn(beta, r.d.y, r.s.y));
+  }
+  __device__ __forceinline__ float at(int i, int c) const {
+    const size_t off = (size_t)i * P + c;
+    const float sv = __ldcg(s + off);
+    return first ? sv : __fmaf_rn(beta, __ldcg(dold + off), sv);
+  }
+};
+
+// FP32 sliding-window stencil (same tiling as the FP64 walker); the diagonal
+// is D = U_{i,j-1} + U_{i,j} + V_{i-1,j} + V_{i,j} from the FP32 weights, so the
+// FP32 operator keeps A 1 = 0 exactly.
+template <class X, class Epi>
+__device__ __forceinline__ void stencil_tile32(const MapDesc& M, int i0, int i1, int j0, int lane,
+                                               const float* U, const float* V, const X& x, Epi& epi) {
+  using Raw = typename X::Raw;
+  const int j = j0 + 2 * lane;
+  const bool hw = (lane == 0) && (j0 > 0);
+  const bool he = (lane == 31) && (j0 + kStrip < M.pitch);
+  const bool halo = hw || he;
+  const int hc = (lane == 0) ? j0 - 1 : j0 + kStrip;
+  const size_t P = (size_t)M.pitch;
+  const float2 z2 = make_float2(0.f, 0.f);
+  float2 xn = z2, vn = z2;
+  if (i0 > 0) {
+    xn = x.make(x.load(i0 - 1, j));
+    vn = ldf2(V, (size_t)(i0 - 1) * P + j);
+  }
+  float2 xc = x.make(x.load(i0, j));
+  Raw rs = (i0 + 1 < M.H) ? x.load(i0 + 1, j) : X::zero();
+  size_t off = (size_t)i0 * P + j;
+  float2 u = ldf2(U, off), v = ldf2(V, off);
+  float h = halo ? x.at(i0, hc) : 0.f;
+  float uwh = hw ? __ldcg(U + (size_t)i0 * P + hc) : 0.f;
+  for (int i = i0; i < i1; ++i) {
+    const bool more = i + 1 < i1;
+    const size_t off2 = off + P;
+    Raw rs2 = (more && i + 2 < M.H) ? x.load(i + 2, j) : X::zero();
+    float2 u2 = z2, v2 = z2;
+    float h2 = 0.f, uwh2 = 0.f;
+    if (more) {
+      u2 = ldf2(U, off2);
+      v2 = ldf2(V, off2);
+      if (halo) h2 = x.at(i + 1, hc);
+      if (hw) uwh2 = __ldcg(U + (size_t)(i + 1) * P + hc);
+    }
+    const float2 xs = (i + 1 < M.H) ? x.make(rs) : z2;
+    float west = __shfl_up_sync(kFull, xc.y, 1);
+    float east = __shfl_down_sync(kFull, xc.x, 1);
+    float uw = __shfl_up_sync(kFull, u.y, 1);
+    if (lane == 0) { west = h; uw = uwh; }
+    if (lane == 31) east = h;
+    const float dx = __fadd_rn(__fadd_rn(__fadd_rn(uw, u.x), vn.x), v.x);
+    const float dy = __fadd_rn(__fadd_rn(__fadd_rn(u.x, u.y), vn.y), v.y);
+    float2 ax;
+    ax.x = dx * xc.x;
+    ax.x = fmaf(-u.x, xc.y, ax.x);
+    ax.x = fmaf(-uw, west, ax.x);
+    ax.x = fmaf(-v.x, xs.x, ax.x);
+    ax.x = fmaf(-vn.x, xn.x, ax.x);
+    ax.y = dy * xc.y;
+    ax.y = fmaf(-u.y, east, ax.y);
+    ax.y = fmaf(-u.x, xc.x, ax.y);
+    ax.y = fmaf(-v.y, xs.y, ax.y);
+    ax.y = fmaf(-vn.y, xn.y, ax.y);
+    epi(off, xc, ax);
+    xn = xc;
+    xc = xs;
+    vn = v;
+    rs = rs2;
+    u = u2;
+    v = v2;
+    h = h2;
+    uwh = uwh2;
+    off = off2;
+  }
+}
+
+// FP32 copies of the weights and the Jacobi inverse; the correction starts at 0.
+template <int KIND>
+__device__ __forceinline__ void conv_tile(const PcgArgs& a, const MapDesc& M, int t, int lane) {
+  const TileGeo g = tile_geo(M, t, a.R);
+  const size_t P = M.pitch;
+  const int j = g.j0 + 2 * lane;
+  for (int i = g.i0; i < g.i1; ++i) {
+    const size_t off = (size_t)i * P + j;
+    const double2 u = ld2(M.f.U, off), v = ld2(M.f.V, off);
+    stf2(M.h.U, off, make_float2((float)u.x, (float)u.y));
+    stf2(M.h.V, off, make_float2((float)v.x, (float)v.y));
+    if (KIND == kJacobi) {
+      const double2 di = ld2(M.f.Dinv, off);
+      stf2(M.h.Dinv, off, make_float2((float)di.x, (float)di.y));
+    }
+    stf2(M.h.x, off, make_float2(0.f, 0.f));
+  }
+}
+
+// True residual in FP64: r = b - A phi (FP64 weights, FP64 phi), rounded to
+// FP32 for the recurrence; s = M^-1 r; partials r^T s, r^T r (and b^T b).
+template <int KIND>
+__device__ __forceinline__ void res64_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t, bool init,
+                                           int lane) {
+  const TileGeo g = tile_geo(M, t, a.R);
+  XPlane x{M.f.phi, (size_t)M.pitch};
+  DF rs, rr;
+  double bb = 0.0;
+  auto epi = [&](size_t off, double2, double2 ax) {
+    const double2 bv = ld2(M.f.b, off);
+    const float2 r = make_float2((float)(bv.x - ax.x), (float)(bv.y - ax.y));
+    stf2(M.h.r, off, r);
+    if (KIND == kJacobi) {
+      const float2 di = ldf2(M.h.Dinv, off);
+      const float2 s = make_float2(di.x * r.x, di.y * r.y);
+      stf2(M.h.s, off, s);
+      rs.add_prod(r.x, s.x);
+      rs.add_prod(r.y, s.y);
+    }
+    rr.add_prod(r.x, r.x);
+    rr.add_prod(r.y, r.y);
+    if (init) {
+      bb = fma(bv.x, bv.x, bb);
+      bb = fma(bv.y, bv.y, bb);
+    }
+  };
+  stencil_tile(M, g.i0, g.i1, g.j0, lane, M.f.U, M.f.V, M.f.D, x, epi);
+  const double vrr = rr.value();
+  const double vrs = (KIND == kIdentity) ? vrr : rs.value();
+  tile_arrive(a, M, S, t, init ? kPhResInit : kPhRes, vrs, vrr, bb, lane);
+}
+
+// d = s + beta d_old, q = A d in FP32, d^T q FP64-accurate.
+template <int KIND>
+__device__ __forceinline__ void a32_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t, int lane) {
+  const TileGeo g = tile_geo(M, t, a.R);
+  const long long it = *(volatile long long*)&S->iter;
+  const float* sv = (KIND == kIdentity) ? M.h.r : M.h.s;
+  const float* dold = (it & 1) ? M.h.d1 : M.h.d0;
+  float* dnew = (it & 1) ? M.h.d0 : M.h.d1;
+  XDir32 x{sv, dold, (float)*(volatile double*)&S->beta, it == 0, (size_t)M.pitch};
+  DF dq;
+  auto epi = [&](size_t off, float2 xc, float2 ax) {
+    stf2(dnew, off, xc);
+    stf2(M.h.q, off, ax);
+    dq.add_prod(xc.x, ax.x);
+    dq.add_prod(xc.y, ax.y);
+  };
+  stencil_tile32(M, g.i0, g.i1, g.j0, lane, M.h.U, M.h.V, x, epi);
+  tile_arrive(a, M, S, t, kPhA, dq.value(), 0.0, 0.0, lane);
+}
+
+// x += alpha d; then either r -= alpha q, s = M^-1 r (partials) or, on a
+// refresh iteration, phi += x, x = 0 (the residual is then recomputed in FP64).
+template <int KIND>
+__device__ __forceinline__ void b32_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t, bool refresh,
+                                         int lane) {
+  const TileGeo g = tile_geo(M, t, a.R);
+  const size_t P = M.pitch;
+  const long long it = *(volatile long long*)&S->iter;
+  const float* d = (it & 1) ? M.h.d0 : M.h.d1;
+  const float alpha = (float)*(volatile double*)&S->alpha;
+  const int j = g.j0 + 2 * lane;
+  DF rs, rr;
+  for (int i = g.i0; i < g.i1; ++i) {
+    const size_t off = (size_t)i * P + j;
+    const float2 dv = ldf2(d, off);
+    float2 xv = ldf2(M.h.x, off);
+    xv.x = __fmaf_rn(alpha, dv.x, xv.x);
+    xv.y = __fmaf_rn(alpha, dv.y, xv.y);
+    if (refresh) {
+      double2 ph = ld2(M.f.phi, off);
+      ph.x += (double)xv.x;
+      ph.y += (double)xv.y;
+      st2(M.f.phi, off, ph);
+      stf2(M.h.x, off, make_float2(0.f, 0.f));
+    } else {
+      stf2(M.h.x, off, xv);
+      const float2 qv = ldf2(M.h.q, off);
+      float2 r = ldf2(M.h.r, off);
+      r.x = __fmaf_rn(-alpha, qv.x, r.x);
+      r.y = __fmaf_rn(-alpha, qv.y, r.y);
+      stf2(M.h.r, off, r);
+      if (KIND == kJacobi) {
+        const float2 di = ldf2(M.h.Dinv, off);
+        const float2 s = make_float2(di.x * r.x, di.y * r.y);
+        stf2(M.h.s, off, s);
+        rs.add_prod(r.x, s.x);
+        rs.add_prod(r.y, s.y);
+      }
+      rr.add_prod(r.x, r.x);
+      rr.add_prod(r.y, r.y);
+    }
+  }
+  if (!refresh) {
+    const double vrr = rr.value();
+    tile_arrive(a, M, S, t, kPhB, (KIND == kIdentity) ? vrr : rs.value(), vrr, 0.0, lane);
+  }
+}
+
+// phi += x, x = 0 (end of the solve).
+__device__ __forceinline__ void fold_tile(const PcgArgs& a, const MapDesc& M, int t, int lane) {
+  const TileGeo g = tile_geo(M, t, a.R);
+  const size_t P = M.pitch;
+  const int j = g.j0 + 2 * lane;
+  for (int i = g.i0; i < g.i1; ++i) {
+    const size_t off = (size_t)i * P + j;
+    const float2 xv = ldf2(M.h.x, off);
+    double2 ph = ld2(M.f.phi, off);
+    ph.x += (double)xv.x;
+    ph.y += (double)xv.y;
+    st2(M.f.phi, off, ph);
+    stf2(M.h.x, off, make_float2(0.f, 0.f));
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads, 2) k_pcg32(PcgArgs a) {
+  __shared__ int s_base[kMaxMaps + 1];
+  __shared__ int s_any;
+  for (int m = threadIdx.x; m <= a.nmaps; m += blockDim.x)
+    s_base[m] = (m < a.nmaps) ? a.maps[m].tile_base : a.ntiles;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int NW = gridDim.x * kWarps;
+  auto for_tiles = [&](auto&& body) {
+    for (int t = gw; t < a.ntiles; t += NW) {
+      const int m = find_map(s_base, a.nmaps, t);
+      MapState* S = a.st + m;
+      if (*(volatile int*)&S->done) continue;
+      body(a.maps[m], S, t);
+    }
+  };
+  // maps active at the start: the final fold must reach them after they stop
+  auto for_tiles_started = [&](auto&& body) {
+    for (int t = gw; t < a.ntiles; t += NW) {
+      const int m = find_map(s_base, a.nmaps, t);
+      if (!a.st[m].outer_active) continue;
+      body(a.maps[m], t);
+    }
+  };
+
+  for_tiles([&](const MapDesc& M, MapState*, int t) { conv_tile<KIND>(a, M, t, lane); });
+  if (!grid_sync(a.bar, a.timeout_ns)) return;
+  for_tiles([&](const MapDesc& M, MapState* S, int t) { res64_tile<KIND>(a, M, S, t, true, lane); });
+  if (!grid_sync(a.bar, a.timeout_ns)) return;
+
+  for (int g = 0;; ++g) {
+    if (*(volatile int*)a.n_active == 0) break;
+    for_tiles([&](const MapDesc& M, MapState* S, int t) { a32_tile<KIND>(a, M, S, t, lane); });
+    if (!grid_sync(a.bar, a.timeout_ns)) return;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    for (int m = threadIdx.x; m < a.nmaps; m += blockDim.x)
+      if (g % a.maps[m].refresh == 0) s_any = 1;
+    __syncthreads();
+    const bool any_refresh = s_any != 0;
+    for_tiles([&](const MapDesc& M, MapState* S, int t) {
+      b32_tile<KIND>(a, M, S, t, (g % M.refresh) == 0, lane);
+    });
+    if (!grid_sync(a.bar, a.timeout_ns)) return;
+    if (any_refresh) {
+      for_tiles([&](const MapDesc& M, MapState* S, int t) {
+        if ((g % M.refresh) == 0) res64_tile<KIND>(a, M, S, t, false, lane);
+      });
+      if (!grid_sync(a.bar, a.timeout_ns)) return;
+    }
+  }
+  for_tiles_started([&](const MapDesc& M, int t) { fold_tile(a, M, t, lane); });
+}
+
+int pcg32_max_blocks_per_sm(int kind) {
+  int nb = 0;
+  if (kind == kIdentity) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg32<kIdentity>, kThreads, 0);
+  else if (kind == kJacobi) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg32<kJacobi>, kThreads, 0);
+  return nb;
+}
+
+cudaError_t launch_pcg32(const Plan& pl, int kind, const PcgArgs& a, cudaStream_t st, cudaEvent_t e0,
+                         cudaEvent_t e1) {
+  pl.kernel_launches += 2;
+  pl.solver_launches += 1;
+  launch_pcg_reset(pl, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (e0) cudaEventRecord(e0, st);
+  const int blocks = pl.nsm * pl.bps;
+  void* args[] = {(void*)&a};
+  if (kind == kIdentity)
+    e = cudaLaunchCooperativeKernel((void*)k_pcg32<kIdentity>, blocks, kThreads, args, 0, st);
+  else if (kind == kJacobi)
+    e = cudaLaunchCooperativeKernel((void*)k_pcg32<kJacobi>, blocks, kThreads, args, 0, st);
+  else
+    e = cudaErrorInvalidValue;
+  if (e == cudaSuccess && e1) e = cudaEventRecord(e1, st);
+  return e;
+}
+
+}  // namespace ulp

@@ -87,11 +87,7 @@ extern "C" int ulp_pcg_noalloc(const double* U, const double* V, const double* b
     if (cudaDeviceGetAttribute(&D.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
       return nfail(ULP_ERR_CUDA, "ulp_pcg_noalloc: device attributes unavailable");
-    D.bps = 1 << 30;  // the same resident blocks per SM as a plan (minimum over the solvers)
-    for (int kind : {kIdentity, kJacobi, kIlu, kSsor}) {
-      const int o = pcg64_max_blocks_per_sm(kind);
-      D.bps = o < D.bps ? o : D.bps;
-    }
+    D.bps = solver_blocks_per_sm();  // the same resident blocks per SM as a plan
     if (D.bps < 1) return nfail(ULP_ERR_CUDA, "ulp_pcg_noalloc: solver does not fit on an SM");
     D.base = p;
     D.plan.hmaps.resize(1);  // the only host allocation, once per device

@@ -16,22 +16,32 @@
 // runs one column behind lane i-1 (forward) or lane i+1 (backward), so the
 // neighbour row's value for the same column arrives by a shuffle of the
 // previous step.  Band b needs the last row of band b-1 (forward) or the first
-// row of band b+1 (backward): the producing band publishes how many columns of
-// that row it has finished (64-bit flag: epoch << 32 | columns, release order)
-// and the consuming band waits on it with an acquire load and a time limit.
-// Inputs are loaded PF steps ahead through a register ring.
+// row of band b+1 (backward).  The producing band writes that row a second
+// time into an exchange row that holds a signalling-NaN sentinel until the
+// value lands, so the value itself is the flag: the consuming band reads the
+// values it will need one block of steps ahead with relaxed loads, re-reads
+// any that still hold the sentinel (with a time limit), and puts the sentinel
+// back after use.  Inputs are loaded PF steps ahead through a register ring.
 #pragma once
+#include <type_traits>
+
 #include "ulp_internal.cuh"
 
 namespace ulp {
 
-__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+constexpr unsigned long long kSentinelBits = 0x7ff4dead5eed0001ull;  // a NaN no arithmetic produces
+
+__device__ __forceinline__ double sentinel() { return __longlong_as_double((long long)kSentinelBits); }
+__device__ __forceinline__ bool is_sentinel(double v) {
+  return (unsigned long long)__double_as_longlong(v) == kSentinelBits;
+}
+__device__ __forceinline__ double ld_relaxed(const double* p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_relaxed(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
 
 enum SweepMode { kSweepFwd = 0, kSweepBwd = 1, kSweepPiv = 2 };
@@ -41,33 +51,31 @@ struct SweepIO {
   const double* b;   // FWD: cw            BWD: ce     PIV: U (read at j-1)
   const double* c;   // FWD: cn            BWD: cs     PIV: V (read at i-1)
   double* out;       // FWD: z             BWD: s      PIV: pinv
+  double* xin;       // exchange row of the neighbour band (read, then reset), or null
+  double* xout;      // this band's exchange row for its neighbour (written), or null
 };
 
 // Sweeps one band of one map.  Returns false if a wait ran out (error flag set).
 template <int MODE>
-__device__ bool band_sweep(const MapDesc& M, int band, int lane, unsigned long long* prog,
-                           unsigned long long epoch, const SweepIO& io,
+__device__ bool band_sweep(const MapDesc& M, int band, int lane, const SweepIO& io,
                            unsigned long long timeout_ns, int* err) {
   constexpr bool FWD = (MODE != kSweepBwd);
-  constexpr int PF = 4;  // prefetch distance in steps (one boundary fetch covers PF columns)
-  const int H = M.H, W = M.W, nb = M.nbands;
+  constexpr int PF = 16;  // input prefetch distance in steps
+  constexpr int PB = 8;   // boundary block: steps served by one set of exchange reads
+  const int H = M.H, W = M.W;
   const size_t P = (size_t)M.pitch;
   const int row0 = band * 32;
   const int nrows = min(32, H - row0);
   const bool act = lane < nrows;
   const int row = act ? row0 + lane : row0;
-  const bool has_nb = FWD ? (band > 0) : (band + 1 < nb);
-  const int nbrow = FWD ? row0 - 1 : row0 + 32;
-  const int edge = FWD ? 0 : nrows - 1;               // lane that reads the neighbour band
-  const int pub = FWD ? nrows - 1 : 0;                // lane whose row the neighbour band needs
-  const bool publish = FWD ? (band + 1 < nb) : (band > 0);
+  const bool has_nb = io.xin != nullptr;
+  const int edge = FWD ? 0 : nrows - 1;               // lane that consumes the neighbour's row
+  const int pub = FWD ? nrows - 1 : 0;                // lane whose row the neighbour consumes
+  const bool publish = io.xout != nullptr;
   const int skew = FWD ? lane : (nrows - 1 - lane);  // steps behind the leading lane
   const int nsteps = W + nrows - 1;
-  unsigned long long* my_flag = prog + band;
-  const unsigned long long* nb_flag = prog + (FWD ? band - 1 : band + 1);
 
-  // column processed at step t, or -1
-  auto col = [&](int t) -> int {
+  auto col = [&](int t) -> int {  // column processed at step t, or -1
     const int c = t - skew;
     if (!act || c < 0 || c >= W) return -1;
     return FWD ? c : W - 1 - c;
@@ -86,39 +94,59 @@ __device__ bool band_sweep(const MapDesc& M, int band, int lane, unsigned long l
       vc = __ldcg(io.c + off);
     }
   };
+  // exchange column read by lane l (< PB) for the block starting at step t0 (edge lane: column t0 + l)
+  auto xcol = [&](int t0) -> int {
+    const int je = t0 + lane;
+    if (lane >= PB || je >= W) return -1;
+    return FWD ? je : W - 1 - je;
+  };
 
   double ra[PF], rb[PF], rc[PF];
 #pragma unroll
   for (int k = 0; k < PF; ++k) load(k, ra[k], rb[k], rc[k]);
-  double prev = 0.0, carry = 0.0, buf = 0.0;
-  for (int t0 = 0; t0 < nsteps; t0 += PF) {
-    // neighbour band's boundary row for the edge lane's next PF columns
+  double bcur = 0.0, bnxt = 0.0;
+  if (has_nb) {
+    const int c0 = xcol(0), c1 = xcol(PB);
+    if (c0 >= 0) bcur = ld_relaxed(io.xin + c0);
+    if (c1 >= 0) bnxt = ld_relaxed(io.xin + c1);
+  }
+  double prev = 0.0, carry = 0.0;
+
+  auto block = [&](int t0, auto slot0) -> bool {
+    constexpr int S0 = decltype(slot0)::value;
     if (has_nb) {
+      // wait for the exchange values of this block, then hand the slots back
+      const int c = xcol(t0);
       bool ok = true;
-      if (lane < PF && t0 < W) {
-        const unsigned long long need = (epoch << 32) | (unsigned long long)min(t0 + PF, W);
+      if (c >= 0 && is_sentinel(bcur)) {
         const unsigned long long t_start = globaltimer();
-        while (ld_acquire64(nb_flag) < need) {
+        do {
           if (*(volatile int*)err) { ok = false; break; }
           if (globaltimer() - t_start > timeout_ns) {
             atomicExch(err, 1);
             ok = false;
             break;
           }
-        }
-        const int je = t0 + lane;  // edge lane's step -> column
-        buf = 0.0;
-        if (ok && je < W) buf = __ldcg(io.out + (size_t)nbrow * P + (FWD ? je : W - 1 - je));
+          bcur = ld_relaxed(io.xin + c);
+        } while (is_sentinel(bcur));
       }
       if (!__all_sync(kFull, ok)) return false;
+      if (c >= 0) st_relaxed(io.xin + c, sentinel());
+    }
+    const double bblk = bcur;
+    // exchange reads for the block after next are issued now, a block ahead of use
+    bcur = bnxt;
+    if (has_nb) {
+      const int c2 = xcol(t0 + 2 * PB);
+      bnxt = (c2 >= 0) ? ld_relaxed(io.xin + c2) : 0.0;
     }
 #pragma unroll
-    for (int k = 0; k < PF; ++k) {
+    for (int k = 0; k < PB; ++k) {
       const int t = t0 + k;
-      const double va = ra[k], vb = rb[k], vc = rc[k];
-      load(t + PF, ra[k], rb[k], rc[k]);
+      const double va = ra[S0 + k], vb = rb[S0 + k], vc = rc[S0 + k];
+      load(t + PF, ra[S0 + k], rb[S0 + k], rc[S0 + k]);
       double nbv = FWD ? __shfl_up_sync(kFull, carry, 1) : __shfl_down_sync(kFull, carry, 1);
-      const double bv = __shfl_sync(kFull, buf, k);
+      const double bv = __shfl_sync(kFull, bblk, k);
       if (lane == edge) nbv = has_nb ? bv : 0.0;
       const int j = col(t);
       double v = 0.0;
@@ -132,14 +160,17 @@ __device__ bool band_sweep(const MapDesc& M, int band, int lane, unsigned long l
           v = fma(vc, nbv, fma(vb, prev, va));
         }
         __stcg(io.out + (size_t)row * P + j, v);
+        if (publish && lane == pub) st_relaxed(io.xout + j, v);
         prev = v;
       }
       carry = v;
-      if (publish && lane == pub && j >= 0) {
-        const int cnt = t - skew + 1;
-        if ((cnt & 7) == 0 || cnt == W) st_release64(my_flag, (epoch << 32) | (unsigned long long)cnt);
-      }
     }
+    return true;
+  };
+
+  for (int t0 = 0; t0 < nsteps; t0 += 2 * PB) {
+    if (!block(t0, std::integral_constant<int, 0>{})) return false;
+    if (t0 + PB < nsteps && !block(t0 + PB, std::integral_constant<int, PB>{})) return false;
   }
   return true;
 }

@@ -39,7 +39,7 @@ class ulp_options(ctypes.Structure):
                 ("refresh", ctypes.c_longlong), ("omega", ctypes.c_double),
                 ("precision", ctypes.c_int), ("phi0_mode", ctypes.c_int),
                 ("tile_rows", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("spin_timeout_s", ctypes.c_double), ("profile", ctypes.c_int)]
+                ("spin_timeout_s", ctypes.c_double), ("profile", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class ulp_stats(ctypes.Structure):

@@ -29,11 +29,19 @@ def main():
     H, W = m.psi.shape
     plan = native.Plan(H, W, outer_tol=0.0,
                        precision=native.ULP_PRECISION_MIXED if a.precision == "mixed" else 0)
+    ms = []
     for _ in range(a.calls):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
         phi, st = plan.unwrap(psi, mask, p=w["p"], eps=w["tau"], precond=a.precond, tol=w["tol"],
                               max_outer=a.max_outer, max_inner=a.max_inner)
-    torch.cuda.synchronize()
-    print(f"profile_case {a.workload} {a.precond} {a.precision}: inner {st['inner']} status {st['status']}")
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    it = max(1, st["inner_total"])
+    print(f"profile_case {a.workload} {a.precond} {a.precision}: inner {st['inner']} status {st['status']} "
+          f"ms/call {ms} -> {1e3 * ms[-1] / it:.1f} us per inner iteration")
 
 
 if __name__ == "__main__":

@@ -41,8 +41,13 @@ UNIT = "Mpixel/s"
 # phi, d, r, q, D^-1 and writes phi, r, s (64 B).  M = I has no s and no D^-1.
 # Mixed precision: phase A reads s, d_old, U, V and writes d, q in FP32 (24 B);
 # phase B reads x, d, r, q, D^-1 and writes x, r, s (32 B).
-ALG_BYTES = {("f64", "jacobi"): 112, ("f64", "identity"): 96, ("mixed", "jacobi"): 56, ("mixed", "identity"): 48}
-KERNEL = {"f64": "k_pcg64", "mixed": "k_pcg32"}
+# DCT-preconditioned flexible CG (FP64 vectors): phase A 56 B (as FP64 with the D plane),
+# B 56 B (phi, d, q, s, r in; phi, r out), dots 16 B, BF16 pack 10 B, plus the four BF16
+# GEMM operands (about 8 B/px); the GEMMs do 8 H W (H + W) flop per application.
+ALG_BYTES = {("f64", "jacobi"): 112, ("f64", "identity"): 96, ("mixed", "jacobi"): 56, ("mixed", "identity"): 48,
+             ("f64", "dct"): 146}
+KERNEL = {("f64", "jacobi"): "k_pcg64", ("f64", "identity"): "k_pcg64", ("mixed", "jacobi"): "k_pcg32",
+          ("mixed", "identity"): "k_pcg32", ("f64", "dct"): "flexible-CG graph (k_f_*, k_gemm_nt x4)"}
 DTYPE = {"f64": "f64", "mixed": "f32+f64"}
 
 
@@ -238,13 +243,14 @@ def run_ours(args):
 
     # plain form: FP64 Jacobi PCG (the paper's method as written); chosen form: the
     # fastest of the forms below that reaches the same tolerance
-    forms = [("f64", "jacobi"), ("mixed", "jacobi")]
+    forms = [("f64", "jacobi"), ("mixed", "jacobi"), ("f64", "dct")]
     res = {}
     plans = {}
     with ClockSampler(uuid) as clk:
         for prec, pc in forms:
-            plans[prec] = native.Plan(H, W, outer_tol=0.0, profile=1,
-                                      precision=native.ULP_PRECISION_MIXED if prec == "mixed" else 0)
+            if prec not in plans:
+                plans[prec] = native.Plan(H, W, outer_tol=0.0, profile=1,
+                                          precision=native.ULP_PRECISION_MIXED if prec == "mixed" else 0)
             res[(prec, pc)] = run_form(plans[prec], psi, mask, phi, w, pc, args.steps, args.warmup, dist)
     ms_plain, st_plain, cnt_plain = res[("f64", "jacobi")]
     chosen = min(res, key=lambda k: res[k][0])
@@ -257,7 +263,8 @@ def run_ours(args):
     solver_s = cnt["solver_ms"] / 1e3
     achieved = alg / solver_s / 1e9 if solver_s > 0 else None
     peak, peak_kind = load_peaks()
-    tpx = profile_traffic(f"{KERNEL[chosen[0]][2:]}_{chosen[1]}_c2_2048")
+    tag = {"k_pcg64": "pcg64", "k_pcg32": "pcg32"}.get(KERNEL[chosen], "fcg_dct")
+    tpx = profile_traffic(f"{tag}_{chosen[1]}_c2_2048")
     traffic = None
     if tpx is not None and cnt["timed_launches"]:
         traffic = tpx * H * W * iters / cnt["timed_launches"]
@@ -313,10 +320,12 @@ def run_ours(args):
                   "dtype": "f64", "inner_iterations": st_plain["inner"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": f"{KERNEL[chosen[0]]}<{chosen[1]}> (persistent PCG)",
+                     "kernel": KERNEL[chosen] if chosen[1] == "dct" else f"{KERNEL[chosen]}<{chosen[1]}> (persistent PCG)",
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "alg_bytes_per_px_iter": ALG_BYTES[chosen],
-                     "solver_ms_per_step": cnt["solver_ms"] / args.steps},
+                     "solver_ms_per_step": cnt["solver_ms"] / args.steps,
+                     "gemm_tflop_per_step": (8.0 * H * W * (H + W) * (iters + st["outer"]) / args.steps / 1e12
+                                             if chosen[1] == "dct" else 0.0)},
         "e2e": {"value": px / (ms_e2e * 1e3), "unit": UNIT, "h2d_bytes_per_step": H * W * 8 + (H * W if mask is not None else 0),
                 "d2h_bytes_per_step": H * W * 8, "ms_per_step": ms_e2e},
         "forms": {f"{k[0]}_{k[1]}": {"value": px / (v[0] * 1e3), "ms_per_step": v[0],
@@ -327,11 +336,58 @@ def run_ours(args):
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(wl_name, w["p"], chosen[1], st["inner"])
+        # the oracle's plain FP64 Jacobi PCG on one core (its DCT form applies explicit cosine
+        # matrices, O(N^1.5) per application: tens of seconds per iteration at 2048^2)
+        line["cpu_baseline"] = oracle_sample(wl_name, w["p"], "jacobi", st_plain["inner"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ batched workload
+def run_batch(args):
+    """64 maps of uneven sizes (256..2048 square, own seed, p in {0, 1}, noise 0.1-0.8),
+    solved together: one persistent launch per outer pass, the whole call captured in a
+    CUDA graph and replayed, tile shape from ulp_autotune.  Mpixel/s = sum of H W / time."""
+    import torch
+    from paper_2203_13675_gb300 import native, synth
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    native.load()
+    specs = synth.batch_specs(64)
+    pm = synth.batch_maps(specs)
+    maps = [{"psi": torch.from_numpy(m.psi).cuda(), "mask": None,
+             "phi": torch.empty(m.psi.shape, dtype=torch.float64, device="cuda"), "p": sp["p"], "eps": 1e-2}
+            for m, sp in zip(pm, specs)]
+    sizes = [tuple(m.psi.shape) for m in pm]
+    px = sum(h * w for h, w in sizes)
+    tuned = native.ulp_autotune(maps, "jacobi", native.ULP_PRECISION_FP64, iters=30)
+    tuned.outer_tol = 0.0
+    tuned.graph = 1
+    plan = native.Plan(None, sizes=sizes, options=tuned)
+    for _ in range(args.warmup):
+        plan.unwrap_batched(maps, precond="jacobi", tol=1e-6, max_outer=5, stats=False)
+    torch.cuda.synchronize()
+    rc, stats = plan.last_status()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        plan.unwrap_batched(maps, precond="jacobi", tol=1e-6, max_outer=5, stats=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    rc, per = plan.unwrap_batched(maps, precond="jacobi", tol=1e-6, max_outer=5, stats=True)
+    line = {"metric": METRIC, "value": px / (ms * 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batch64_jacobi", "maps": len(sizes), "total_px": px,
+                       "tile_rows": tuned.tile_rows, "blocks_per_sm": tuned.blocks_per_sm,
+                       "graph": True, "inner_iterations_max_map": max(max(p["inner"]) for p in per),
+                       "worst_status": min(p["status"] for p in per)}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------ reference arm
@@ -378,6 +434,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_ours(args)
 

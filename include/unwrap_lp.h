@@ -92,7 +92,8 @@ typedef struct ulp_options {
   int tile_rows;          /* rows per warp tile; 0 = autotuned table */
   int blocks_per_sm;      /* resident blocks per SM of the persistent solver; 0 = autotuned */
   double spin_timeout_s;  /* bound on any in-kernel wait, default 2.0 s */
-  int profile;            /* 1: record CUDA events around every persistent solver launch (ulp_plan_counters) */
+  int profile;            /* 1: record CUDA events around every persistent solver launch (ulp_plan_counters);
+                             2: as 1, and the DCT solve runs host-driven (each kernel a host launch) */
   int graph;              /* 1: ulp_unwrap / ulp_unwrap_batched capture their kernel sequence into a CUDA
                              graph on the first call and replay it while the arguments stay the same
                              (ignored when profile = 1) */
@@ -193,6 +194,18 @@ typedef struct ulp_counters {
   long long timed_launches;   /* solver launches included in solver_ms */
 } ulp_counters;
 ULP_API int ulp_plan_counters(ulp_plan plan, int reset, ulp_counters* out);
+
+/* ulp_autotune: picks options.tile_rows and options.blocks_per_sm of the
+ * persistent solvers for n maps of sizes H[t] x W[t] by timing, for each
+ * candidate, one outer pass of maps (device data, as in ulp_unwrap_batched)
+ * capped at iters inner iterations (<= 0: 40) with CUDA events around the
+ * solver launch.  precision is ulp_precision.  Writes the fastest into *best
+ * (other fields default); when cache_path is non-NULL appends one JSON line
+ * (GPU name, precision, preconditioner, a hash of the sizes, the choice and its
+ * time).  Allocates and frees a plan per candidate; synchronises the default
+ * stream.  No counterpart in the paper: it tunes the launch shape only. */
+ULP_API int ulp_autotune(int n, const int* H, const int* W, const ulp_map* maps, int precond, int precision,
+                         int iters, const char* cache_path, ulp_options* best);
 
 /* ---------------------------------------------------------------------------
  * Single steps of the method (device pointers, contiguous H*W arrays,

@@ -58,6 +58,11 @@ extern "C" const char* ulp_last_error(void) { return g_err.c_str(); }
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static void destroy_plan(Plan& pl) {
+  destroy_fcg(pl);
+  if (pl.dct) dct_destroy(pl.dct);
+  if (pl.dct_mem) cudaFree(pl.dct_mem);
+  pl.dct = nullptr;
+  pl.dct_mem = nullptr;
   if (pl.graph_exec) cudaGraphExecDestroy(pl.graph_exec);
   if (pl.cap_stream) cudaStreamDestroy(pl.cap_stream);
   pl.graph_exec = nullptr;
@@ -179,6 +184,8 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
   bytes += align256(sizeof(Barrier)) + align256(sizeof(int));
   const size_t off_pt = bytes;
   bytes += 2 * align256(sizeof(double) * n);
+  const size_t off_args = bytes;
+  bytes += align256(sizeof(PcgArgs));
 
   cudaError_t e = cudaMalloc(&pl.arena, bytes);
   if (e != cudaSuccess) {
@@ -218,7 +225,18 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
   pl.n_active = reinterpret_cast<int*>(base + off_bar + align256(sizeof(Barrier)));
   pl.d_p = reinterpret_cast<double*>(base + off_pt);
   pl.d_tau = reinterpret_cast<double*>(base + off_pt + align256(sizeof(double) * n));
+  pl.dargs = reinterpret_cast<PcgArgs*>(base + off_args);
   ULP_CU(cudaMemcpy(pl.dmaps, pl.hmaps.data(), sizeof(MapDesc) * n, cudaMemcpyHostToDevice));
+  if (n == 1) {  // DCT preconditioner matrices and buffers (single-map plans)
+    e = cudaMalloc(&pl.dct_mem, dct_bytes(H[0], W[0]));
+    if (e != cudaSuccess) {
+      pl.dct_mem = nullptr;
+      cudaGetLastError();
+      return fail(ULP_ERR_NOMEM, "cudaMalloc(DCT buffers): %s", cudaGetErrorString(e));
+    }
+    pl.dct = dct_create(H[0], W[0], pl.dct_mem);
+    if (!pl.dct) return fail(ULP_ERR_CUDA, "DCT preconditioner set-up failed");
+  }
   ULP_CU(cudaDeviceSynchronize());  // workspace zeroed before any stream may use it
   return ULP_OK;
 }
@@ -264,8 +282,7 @@ __global__ void k_set_pt(PT pt, double* p, double* tau, int first, int n) {
 static int check_solver_args(int precond, double tol, int max_outer) {
   if (precond < ULP_PRECOND_IDENTITY || precond > ULP_PRECOND_DCT)
     return fail(ULP_ERR_INVALID, "unknown preconditioner %d", precond);
-  if (precond == ULP_PRECOND_DCT)
-    return fail(ULP_ERR_UNSUPPORTED, "preconditioner %d not available in this build", precond);
+
   if (!(tol > 0.0)) return fail(ULP_ERR_INVALID, "tol must be > 0");
   if (max_outer < 1) return fail(ULP_ERR_INVALID, "max_outer must be >= 1");
   return ULP_OK;
@@ -350,7 +367,8 @@ static int enqueue_call(Plan& pl, const ulp_map* maps, int precond, double tol, 
     ULP_CU(launch_system(pl, pl.d_p, pl.d_tau, st));
     cudaEvent_t e0, e1;
     next_events(pl, &e0, &e1);
-    if (mixed) ULP_CU(launch_pcg32(pl, precond, a, st, e0, e1));
+    if (precond == ULP_PRECOND_DCT) ULP_CU(launch_fcg(pl, a, st, e0, e1));
+    else if (mixed) ULP_CU(launch_pcg32(pl, precond, a, st, e0, e1));
     else ULP_CU(launch_pcg64(pl, precond, a, st, e0, e1));
     ULP_CU(launch_outer_error(pl, pl.opt.outer_tol, max_outer, st));
   }
@@ -410,6 +428,8 @@ extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precon
   const bool mixed = pl.opt.precision == ULP_PRECISION_MIXED;
   if (mixed && precond != ULP_PRECOND_IDENTITY && precond != ULP_PRECOND_JACOBI)
     return fail(ULP_ERR_UNSUPPORTED, "mixed precision supports the identity and Jacobi preconditioners");
+  if (precond == ULP_PRECOND_DCT && (pl.nmaps != 1 || !pl.dct))
+    return fail(ULP_ERR_UNSUPPORTED, "the DCT preconditioner is available on single-map plans");
   for (int m = 0; m < pl.nmaps; ++m) {
     if (!maps[m].psi || !maps[m].phi) return fail(ULP_ERR_INVALID, "map %d: null psi or phi", m);
     if (!(maps[m].p >= 0.0 && maps[m].p <= 2.0)) return fail(ULP_ERR_INVALID, "map %d: p outside [0, 2]", m);
@@ -418,7 +438,9 @@ extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precon
   ULP_CU(cudaSetDevice(pl.device));
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   pl.last_stream = st;
-  if (pl.opt.graph && !pl.opt.profile) rc = graph_call(pl, maps, precond, tol, max_outer, max_inner, st, mixed);
+  // the DCT solve is itself a graph with a WHILE node, which cannot be nested: it runs eagerly
+  if (pl.opt.graph && !pl.opt.profile && precond != ULP_PRECOND_DCT)
+    rc = graph_call(pl, maps, precond, tol, max_outer, max_inner, st, mixed);
   else rc = enqueue_call(pl, maps, precond, tol, max_outer, max_inner, st, mixed);
   if (rc != ULP_OK) return rc;
   if (per_map) return collect(pl, st, per_map);
@@ -602,7 +624,6 @@ extern "C" int ulp_precond_apply(int precond, const double* U, const double* V, 
   if (!U || !V || !r || !s) return fail(ULP_ERR_INVALID, "null argument");
   int rc = check_solver_args(precond, 1.0, 1);
   if (rc != ULP_OK) return rc;
-  (void)mask;
   ulp_options o;
   ulp_options_default(&o);
   o.omega = omega;
@@ -616,6 +637,12 @@ extern "C" int ulp_precond_apply(int precond, const double* U, const double* V, 
   if (precond == ULP_PRECOND_IDENTITY || precond == ULP_PRECOND_JACOBI) {
     ULP_CU(launch_to_plane(pl, r, M.f.r, tp.st));
     ULP_CU(launch_jacobi_apply(pl, precond, M.f.r, M.f.s, tp.st));
+  } else if (precond == ULP_PRECOND_DCT) {
+    ULP_CU(launch_to_plane(pl, r, M.f.r, tp.st));
+    if (mask) ULP_CU(launch_mask_to_plane(pl, mask, tp.st));
+    ULP_CU(dct_apply(*pl.dct, M.f.r, M.pitch, mask ? M.f.mask : nullptr, M.f.s, tp.st));
+    ULP_CU(cudaStreamSynchronize(tp.st));
+    if (dct_error(*pl.dct)) return fail(ULP_ERR_TIMEOUT, "DCT GEMM wait ran out");
   } else {
     // the sweep solver's set-up and first s = M^-1 r, with b = r and phi = 0
     ULP_CU(launch_to_plane(pl, r, M.f.b, tp.st));
@@ -643,7 +670,8 @@ extern "C" int ulp_pcg(const double* U, const double* V, const double* b, int H,
   if (rc != ULP_OK) return rc;
   ULP_CU(launch_to_plane(pl, b, M.f.b, tp.st));
   ULP_CU(launch_to_plane(pl, phi, M.f.phi, tp.st));
-  ULP_CU(launch_pcg64(pl, precond, pcg_args(pl, tol, max_inner), tp.st, nullptr, nullptr));
+  if (precond == ULP_PRECOND_DCT) ULP_CU(launch_fcg(pl, pcg_args(pl, tol, max_inner), tp.st));
+  else ULP_CU(launch_pcg64(pl, precond, pcg_args(pl, tol, max_inner), tp.st, nullptr, nullptr));
   ULP_CU(launch_outer_error(pl, 0.0, 1, tp.st));
   ULP_CU(launch_from_plane(pl, M.f.phi, phi, tp.st));
   if (stats) return collect(pl, tp.st, stats);

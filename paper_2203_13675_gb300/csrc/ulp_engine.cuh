@@ -136,7 +136,7 @@ __device__ __forceinline__ TileGeo tile_geo(const MapDesc& M, int t, int R) {
 }
 
 // ------------------------------------------------------------------ PCG engine
-enum Phase { kPhResInit = 0, kPhA = 1, kPhB = 2, kPhRes = 3 };
+enum Phase { kPhResInit = 0, kPhA = 1, kPhB = 2, kPhRes = 3, kPhFcg = 4 };
 
 // Runs in the warp whose tile arrival completed phase `ph` for map m: reduces
 // the map's tile partials in a fixed order and advances its scalars
@@ -147,7 +147,7 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
   const double v0 = warp_sum_partials(a.P0 + base, n, lane);
   double v1 = 0.0, v2 = 0.0;
   if (ph != kPhA) v1 = warp_sum_partials(a.P1 + base, n, lane);
-  if (ph == kPhResInit) v2 = warp_sum_partials(a.P2 + base, n, lane);
+  if (ph == kPhResInit || ph == kPhFcg) v2 = warp_sum_partials(a.P2 + base, n, lane);
   if (lane == 0) {
     bool done = false;
     if (ph == kPhA) {
@@ -166,6 +166,13 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
         S->rr = v1;
         S->bb = v2;
         S->iter = 0;
+      } else if (ph == kPhFcg) {
+        // flexible CG (Polak-Ribiere): beta = r_{k+1}^T (s_{k+1} - s_k) / (r_k^T s_k), v2 = r_{k+1}^T s_k
+        const double dold = S->delta;
+        S->delta = v0;
+        S->rr = v1;
+        S->beta = (v0 - v2) / dold;
+        S->iter += 1;
       } else {
         const double dold = S->delta;
         S->delta = v0;
@@ -191,6 +198,7 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
       S->done = 1;
       __threadfence();
       atomicSub(a.n_active, 1);
+      if (a.cond) cudaGraphSetConditional(a.cond, 0);  // ends the graph's WHILE loop
     }
     __threadfence();
   }
@@ -208,7 +216,7 @@ __device__ __forceinline__ void tile_arrive(const PcgArgs& a, const MapDesc& M, 
   if (lane == 0) {
     __stcg(a.P0 + t, v0);
     if (ph != kPhA) __stcg(a.P1 + t, v1);
-    if (ph == kPhResInit) __stcg(a.P2 + t, v2);
+    if (ph == kPhResInit) __stcg(a.P2 + t, v2);  // kPhFcg: P2 holds r_{k+1}^T s_k from phase B
     __threadfence();
     old = atomicAdd(&S->arrive, 1u);
   }
@@ -217,6 +225,27 @@ __device__ __forceinline__ void tile_arrive(const PcgArgs& a, const MapDesc& M, 
     __threadfence();
     finish_map(a, M, S, ph, lane);
   }
+}
+
+// d = s + beta d_old, q = A d, partial d^T q (Algorithm 1: q <- A d, d^T q).
+template <int KIND>
+__device__ __forceinline__ void a_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t, int lane) {
+  const TileGeo g = tile_geo(M, t, a.R);
+  const size_t P = M.pitch;
+  const long long it = *(volatile long long*)&S->iter;
+  const double* sv = (KIND == kIdentity) ? M.f.r : M.f.s;
+  const double* dold = (it & 1) ? M.f.d1 : M.f.d0;
+  double* dnew = (it & 1) ? M.f.d0 : M.f.d1;
+  XDir x{sv, dold, *(volatile double*)&S->beta, it == 0, P};
+  double dq = 0.0;
+  auto epi = [&](size_t off, double2 xc, double2 ax) {
+    st2(dnew, off, xc);
+    st2(M.f.q, off, ax);
+    dq = fma(xc.x, ax.x, dq);
+    dq = fma(xc.y, ax.y, dq);
+  };
+  stencil_tile(M, g.i0, g.i1, g.j0, lane, M.f.U, M.f.V, M.f.D, x, epi);
+  tile_arrive(a, M, S, t, kPhA, dq, 0.0, 0.0, lane);
 }
 
 }  // namespace ulp

@@ -1,0 +1,287 @@
+// ulp_fcg.cu -- inner solve with the DCT Poisson preconditioner: flexible CG in
+// one CUDA graph.
+//
+// The DCT preconditioner runs on the tensor cores as four GEMM launches, so
+// this solve is not a single persistent kernel: each phase of an iteration is
+// its own kernel and the loop is a graph WHILE node whose condition the
+// device clears when the map stops (converged, l_max or breakdown), so the
+// host never waits inside the solve.  The BF16 GEMMs make M^-1 slightly
+// inexact and not exactly symmetric, so beta is the flexible (Polak-Ribiere)
+// one, beta = r_{k+1}^T (s_{k+1} - s_k) / r_k^T s_k; the term r_{k+1}^T s_k is
+// accumulated in phase B, before the GEMMs overwrite s.  All vectors, alpha,
+// beta and the stop tests are FP64, as in the other FP64 solvers.
+//
+// Per iteration:  A: d = s + beta d, q = A d, d^T q -> alpha
+//                 B: phi += alpha d, r -= alpha q (not on refresh iterations), r^T s_k
+//                 R: on refresh iterations r = b - A phi, r^T s_k
+//                 DCT: s = Pi L^+ r (pack + 4 tcgen05 GEMMs)
+//                 D: r^T s, r^T r -> beta, stop test, WHILE condition
+#include "ulp_engine.cuh"
+#include "ulp_host.h"
+
+namespace ulp {
+
+__global__ void k_set_args(PcgArgs a, PcgArgs* dst) { *dst = a; }
+
+// one warp per tile (grid-stride), the single map of the plan
+#define FCG_TILE_LOOP(a)                                               \
+  const int lane = threadIdx.x & 31;                                   \
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  \
+  const int NW = gridDim.x * (blockDim.x >> 5);                        \
+  const MapDesc& M = a.maps[0];                                        \
+  MapState* S = a.st;                                                  \
+  for (int t = gw; t < a.ntiles; t += NW)
+
+// The WHILE loop's own guard (one thread), run after the start phase and at the
+// head of every body execution: a map that has stopped -- or was never active in
+// this outer pass, so no finisher will run -- clears the condition, and so does
+// a loop that has run past l_max (reported as a time-out).  The rest of that body
+// execution then finds the map stopped and returns at once.
+__global__ void k_f_guard(const PcgArgs* pa, int count) {
+  const PcgArgs a = *pa;
+  MapState* S = a.st;
+  const MapDesc& M = a.maps[0];
+  const long long lmax = a.lmax > 0 ? a.lmax : 2LL * M.H * M.W;
+  const long long loops = count ? ++S->loops : S->loops;
+  if (*(volatile int*)&S->done) {
+    cudaGraphSetConditional(a.cond, 0);
+  } else if (loops > lmax + 2) {
+    S->status = -4;
+    S->done = 1;
+    atomicSub(a.n_active, 1);
+    __threadfence();
+    cudaGraphSetConditional(a.cond, 0);
+  }
+}
+
+// r = b - A phi (start, or refresh iterations only); on refresh iterations also r^T s_k.
+__global__ void __launch_bounds__(kThreads) k_f_res(const PcgArgs* pa, int refresh_only) {
+  const PcgArgs a = *pa;
+  FCG_TILE_LOOP(a) {
+    if (*(volatile int*)&S->done) return;
+    const long long it = *(volatile long long*)&S->iter;
+    if (refresh_only && (it % M.refresh) != 0) return;
+    const TileGeo g = tile_geo(M, t, a.R);
+    XPlane x{M.f.phi, (size_t)M.pitch};
+    double rsp = 0.0;
+    auto epi = [&](size_t off, double2, double2 ax) {
+      const double2 bv = ld2(M.f.b, off);
+      const double2 r = make_double2(bv.x - ax.x, bv.y - ax.y);
+      st2(M.f.r, off, r);
+      if (refresh_only) {
+        const double2 sv = ld2(M.f.s, off);
+        rsp = fma(r.x, sv.x, rsp);
+        rsp = fma(r.y, sv.y, rsp);
+      }
+    };
+    stencil_tile(M, g.i0, g.i1, g.j0, lane, M.f.U, M.f.V, M.f.D, x, epi);
+    if (refresh_only) {
+      rsp = warp_sum(rsp);
+      if (lane == 0) __stcg(a.P2 + t, rsp);
+    }
+  }
+}
+
+// d = s + beta d_old (d = s at l = 0), q = A d, d^T q -> alpha.
+__global__ void __launch_bounds__(kThreads) k_f_a(const PcgArgs* pa) {
+  const PcgArgs a = *pa;
+  FCG_TILE_LOOP(a) {
+    if (*(volatile int*)&S->done) return;
+    a_tile<kJacobi>(a, M, S, t, lane);
+  }
+}
+
+// phi += alpha d; r -= alpha q and r^T s_k (not on refresh iterations).
+__global__ void __launch_bounds__(kThreads) k_f_b(const PcgArgs* pa) {
+  const PcgArgs a = *pa;
+  FCG_TILE_LOOP(a) {
+    if (*(volatile int*)&S->done) return;
+    const long long it = *(volatile long long*)&S->iter;
+    const bool refresh = (it % M.refresh) == 0;
+    const TileGeo g = tile_geo(M, t, a.R);
+    const size_t P = M.pitch;
+    const double* d = (it & 1) ? M.f.d0 : M.f.d1;
+    const double alpha = *(volatile double*)&S->alpha;
+    const int j = g.j0 + 2 * lane;
+    double rsp = 0.0;
+    for (int i = g.i0; i < g.i1; ++i) {
+      const size_t off = (size_t)i * P + j;
+      const double2 dv = ld2(d, off);
+      double2 ph = ld2(M.f.phi, off);
+      ph.x = fma(alpha, dv.x, ph.x);
+      ph.y = fma(alpha, dv.y, ph.y);
+      st2(M.f.phi, off, ph);
+      if (!refresh) {
+        const double2 qv = ld2(M.f.q, off), sv = ld2(M.f.s, off);
+        double2 r = ld2(M.f.r, off);
+        r.x = fma(-alpha, qv.x, r.x);
+        r.y = fma(-alpha, qv.y, r.y);
+        st2(M.f.r, off, r);
+        rsp = fma(r.x, sv.x, rsp);
+        rsp = fma(r.y, sv.y, rsp);
+      }
+    }
+    if (!refresh) {
+      rsp = warp_sum(rsp);
+      if (lane == 0) __stcg(a.P2 + t, rsp);
+    }
+  }
+}
+
+// r^T s, r^T r (and b^T b at the start) -> delta, beta, stop test.
+__global__ void __launch_bounds__(kThreads) k_f_dots(const PcgArgs* pa, int init) {
+  const PcgArgs a = *pa;
+  FCG_TILE_LOOP(a) {
+    if (*(volatile int*)&S->done) return;
+    const TileGeo g = tile_geo(M, t, a.R);
+    const size_t P = M.pitch;
+    const int j = g.j0 + 2 * lane;
+    double rs = 0.0, rr = 0.0, bb = 0.0;
+    for (int i = g.i0; i < g.i1; ++i) {
+      const size_t off = (size_t)i * P + j;
+      const double2 rv = ld2(M.f.r, off), sv = ld2(M.f.s, off);
+      rs = fma(rv.x, sv.x, rs);
+      rs = fma(rv.y, sv.y, rs);
+      rr = fma(rv.x, rv.x, rr);
+      rr = fma(rv.y, rv.y, rr);
+      if (init) {
+        const double2 bv = ld2(M.f.b, off);
+        bb = fma(bv.x, bv.x, bb);
+        bb = fma(bv.y, bv.y, bb);
+      }
+    }
+    tile_arrive(a, M, S, t, init ? kPhResInit : kPhFcg, rs, rr, bb, lane);
+  }
+}
+
+static int tile_blocks(const Plan& pl) { return (pl.ntiles + kWarps - 1) / kWarps; }
+
+// Captures the solve graph: start (r, s, delta_0) then WHILE { A, B, R, DCT, D }.
+static cudaError_t fcg_build(Plan& pl) {
+  cudaError_t e = cudaSuccess;
+  if (!pl.cap_stream) {
+    e = cudaStreamCreateWithFlags(&pl.cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  cudaStream_t st = pl.cap_stream;
+  const MapDesc& M = pl.hmaps[0];
+  const int nb = tile_blocks(pl);
+  cudaGraph_t g = nullptr;
+  if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return e;
+  }
+  pl.fcg_cond = h;
+  cudaGraphNodeParams cp = {};
+  if ((e = cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+      cudaSuccess) {
+    cudaGraphDestroy(g);
+    return e;
+  }
+  k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
+  e = dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st);
+  k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+  k_f_guard<<<1, 1, 0, st>>>(pl.dargs, 0);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+  cudaGraphNode_t cn = nullptr;
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&cn, g, deps, nullptr, ndeps, &cp);
+  }
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+  cudaGraph_t gout = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(st, &gout);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return e;
+  }
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) ==
+      cudaSuccess) {
+    k_f_guard<<<1, 1, 0, st>>>(pl.dargs, 1);
+    k_f_a<<<nb, kThreads, 0, st>>>(pl.dargs);
+    k_f_b<<<nb, kThreads, 0, st>>>(pl.dargs);
+    k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+    e = dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st);
+    k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaGraph_t bout = nullptr;
+    const cudaError_t e3 = cudaStreamEndCapture(st, &bout);
+    if (e == cudaSuccess) e = e3;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&pl.fcg_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) pl.fcg_exec = nullptr;
+  return e;
+}
+
+// Host-driven form of the same solve (options.profile = 2): every kernel is a
+// host launch, so a profiler sees each one; the host reads the stop flag after
+// every iteration.  For measurement only.
+static cudaError_t fcg_eager(Plan& pl, cudaStream_t st) {
+  const MapDesc& M = pl.hmaps[0];
+  const int nb = tile_blocks(pl);
+  k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
+  cudaError_t e = dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st);
+  if (e != cudaSuccess) return e;
+  k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+  for (long long l = 0;; ++l) {
+    int done = 0;
+    if ((e = cudaMemcpyAsync(&done, &pl.dstate->done, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    if (done || l > (1LL << 24)) break;
+    k_f_a<<<nb, kThreads, 0, st>>>(pl.dargs);
+    k_f_b<<<nb, kThreads, 0, st>>>(pl.dargs);
+    k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+    if ((e = dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st)) != cudaSuccess) return e;
+    k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fcg(Plan& pl, const PcgArgs& a_in, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+  if (!pl.dct || pl.nmaps != 1) return cudaErrorNotSupported;
+  if (pl.opt.profile == 2) {
+    PcgArgs a = a_in;
+    a.cond = 0;
+    k_set_args<<<1, 1, 0, st>>>(a, pl.dargs);
+    launch_pcg_reset(pl, st);
+    if (e0) cudaEventRecord(e0, st);
+    const cudaError_t e = fcg_eager(pl, st);
+    if (e == cudaSuccess && e1) cudaEventRecord(e1, st);
+    return e;
+  }
+  if (!pl.fcg_exec) {
+    const cudaError_t e = fcg_build(pl);
+    if (e != cudaSuccess) return e;
+  }
+  PcgArgs a = a_in;
+  a.cond = pl.fcg_cond;
+  pl.kernel_launches += 2;
+  pl.solver_launches += 1;
+  k_set_args<<<1, 1, 0, st>>>(a, pl.dargs);
+  launch_pcg_reset(pl, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (e0) cudaEventRecord(e0, st);
+  e = cudaGraphLaunch(pl.fcg_exec, st);
+  if (e == cudaSuccess && e1) e = cudaEventRecord(e1, st);
+  return e;
+}
+
+void destroy_fcg(Plan& pl) {
+  if (pl.fcg_exec) cudaGraphExecDestroy(pl.fcg_exec);
+  pl.fcg_exec = nullptr;
+}
+
+}  // namespace ulp

@@ -19,7 +19,7 @@ __global__ void k_pack(MapDesc M, MapState* S, const double* __restrict__ psi,
                        const uint8_t* __restrict__ mask, const double* __restrict__ phi0) {
   const size_t n = (size_t)M.H * M.pitch;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / M.pitch), j = (int)(t % M.pitch);
+    const int i = (int)((unsigned)t / (unsigned)M.pitch), j = (int)((unsigned)t - (unsigned)i * (unsigned)M.pitch);
     double dx = 0.0, dy = 0.0, ph = 0.0;
     uint8_t mk = 0;
     if (j < M.W) {
@@ -41,7 +41,7 @@ __global__ void k_pack(MapDesc M, MapState* S, const double* __restrict__ psi,
 __global__ void k_unpack(MapDesc M, double* __restrict__ phi) {
   const size_t n = (size_t)M.H * M.W;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(k / M.W), j = (int)(k % M.W);
+    const int i = (int)((unsigned)k / (unsigned)M.W), j = (int)((unsigned)k - (unsigned)i * (unsigned)M.W);
     phi[k] = M.f.phi[(size_t)i * M.pitch + j];
   }
 }
@@ -76,7 +76,7 @@ __global__ void k_weights(const MapDesc* __restrict__ maps, MapState* S, const d
   const size_t n = (size_t)M.H * M.pitch;
   const size_t P = M.pitch;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / P), j = (int)(t % P);
+    const int i = (int)((unsigned)t / (unsigned)P), j = (int)((unsigned)t - (unsigned)i * (unsigned)P);
     const double ph = M.f.phi[t];
     const bool mk = M.f.mask[t] != 0;
     double u = 0.0, v = 0.0;
@@ -103,7 +103,7 @@ __global__ void k_system(const MapDesc* __restrict__ maps, MapState* S) {
   const size_t n = (size_t)M.H * M.pitch;
   const size_t P = M.pitch;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / P), j = (int)(t % P);
+    const int i = (int)((unsigned)t / (unsigned)P), j = (int)((unsigned)t - (unsigned)i * (unsigned)P);
     const double uw = (j > 0) ? M.f.U[t - 1] : 0.0;
     const double ue = M.f.U[t];
     const double vn = (i > 0) ? M.f.V[t - P] : 0.0;
@@ -149,27 +149,6 @@ __device__ __forceinline__ void res_tile(const PcgArgs& a, const MapDesc& M, Map
   stencil_tile(M, g.i0, g.i1, g.j0, lane, M.f.U, M.f.V, M.f.D, x, epi);
   if (KIND == kIdentity) rs = rr;
   tile_arrive(a, M, S, t, init ? kPhResInit : kPhRes, rs, rr, bb, lane);
-}
-
-// d = s + beta d_old, q = A d, partial d^T q (Algorithm 1: q <- A d, d^T q).
-template <int KIND>
-__device__ __forceinline__ void a_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t, int lane) {
-  const TileGeo g = tile_geo(M, t, a.R);
-  const size_t P = M.pitch;
-  const long long it = *(volatile long long*)&S->iter;
-  const double* sv = (KIND == kIdentity) ? M.f.r : M.f.s;
-  const double* dold = (it & 1) ? M.f.d1 : M.f.d0;
-  double* dnew = (it & 1) ? M.f.d0 : M.f.d1;
-  XDir x{sv, dold, *(volatile double*)&S->beta, it == 0, P};
-  double dq = 0.0;
-  auto epi = [&](size_t off, double2 xc, double2 ax) {
-    st2(dnew, off, xc);
-    st2(M.f.q, off, ax);
-    dq = fma(xc.x, ax.x, dq);
-    dq = fma(xc.y, ax.y, dq);
-  };
-  stencil_tile(M, g.i0, g.i1, g.j0, lane, M.f.U, M.f.V, M.f.D, x, epi);
-  tile_arrive(a, M, S, t, kPhA, dq, 0.0, 0.0, lane);
 }
 
 // phi += alpha d; r -= alpha q; s = M^{-1} r; partials r^T s, r^T r.
@@ -538,6 +517,7 @@ __global__ void k_pcg_reset(MapState* S, int nmaps, int* n_active, Barrier* bar)
     s->done = act ? 0 : 1;
     s->stop_after = 0;
     s->arrive = 0u;
+    s->loops = 0;
     if (act) atomicAdd(&s_cnt, 1);
   }
   __syncthreads();
@@ -661,21 +641,21 @@ __global__ void k_jacobi_apply(MapDesc M, const double* __restrict__ r, double* 
 __global__ void k_to_plane(MapDesc M, const double* __restrict__ src, double* dst) {
   const size_t n = (size_t)M.H * M.pitch;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / M.pitch), j = (int)(t % M.pitch);
+    const int i = (int)((unsigned)t / (unsigned)M.pitch), j = (int)((unsigned)t - (unsigned)i * (unsigned)M.pitch);
     dst[t] = (j < M.W) ? src[(size_t)i * M.W + j] : 0.0;
   }
 }
 __global__ void k_from_plane(MapDesc M, const double* __restrict__ src, double* dst) {
   const size_t n = (size_t)M.H * M.W;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(k / M.W), j = (int)(k % M.W);
+    const int i = (int)((unsigned)k / (unsigned)M.W), j = (int)((unsigned)k - (unsigned)i * (unsigned)M.W);
     dst[k] = src[(size_t)i * M.pitch + j];
   }
 }
 __global__ void k_mask_to_plane(MapDesc M, const uint8_t* __restrict__ src) {
   const size_t n = (size_t)M.H * M.pitch;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / M.pitch), j = (int)(t % M.pitch);
+    const int i = (int)((unsigned)t / (unsigned)M.pitch), j = (int)((unsigned)t - (unsigned)i * (unsigned)M.pitch);
     M.f.mask[t] = (j < M.W && src) ? (src[(size_t)i * M.W + j] ? 1 : 0) : 0;
   }
 }

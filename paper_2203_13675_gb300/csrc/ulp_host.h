@@ -8,6 +8,8 @@
 
 namespace ulp {
 
+struct DctPlan;  // ulp_dct.cu
+
 struct Plan {
   int device = 0;
   int nsm = 0;
@@ -27,6 +29,11 @@ struct Plan {
   int* n_active = nullptr;
   int nbands = 0;
   int bps_sweep = 1;         // resident blocks per SM of the sweep solvers
+  DctPlan* dct = nullptr;    // DCT preconditioner buffers (single-map plans)
+  void* dct_mem = nullptr;
+  PcgArgs* dargs = nullptr;  // solver arguments in device memory (read by the graph-driven solve)
+  cudaGraphExec_t fcg_exec = nullptr;       // flexible-CG solve graph (DCT preconditioner)
+  unsigned long long fcg_cond = 0;          // its WHILE-node handle
   double *d_p = nullptr, *d_tau = nullptr;
   void* arena = nullptr;
   size_t arena_bytes = 0;
@@ -66,6 +73,19 @@ cudaError_t launch_pcg64(const Plan& pl, int kind, const PcgArgs& a, cudaStream_
                          cudaEvent_t e1 = nullptr);
 int pcg64_max_blocks_per_sm(int kind);
 void launch_pcg_reset(const Plan& pl, cudaStream_t st);
+
+// ulp_dct.cu
+size_t dct_bytes(int H, int W);
+DctPlan* dct_create(int H, int W, void* mem);  // builds the matrices in mem (dct_bytes); null on failure
+void dct_destroy(DctPlan* d);
+cudaError_t dct_apply(const DctPlan& d, const double* r, int pitch, const uint8_t* mask, double* s,
+                      cudaStream_t st);
+int dct_error(const DctPlan& d);  // 1 if a GEMM wait ran out since the last call (clears the flag)
+
+// ulp_fcg.cu
+cudaError_t launch_fcg(Plan& pl, const PcgArgs& a, cudaStream_t st, cudaEvent_t e0 = nullptr,
+                       cudaEvent_t e1 = nullptr);
+void destroy_fcg(Plan& pl);
 
 // ulp_mixed.cu
 cudaError_t launch_pcg32(const Plan& pl, int kind, const PcgArgs& a, cudaStream_t st, cudaEvent_t e0 = nullptr,

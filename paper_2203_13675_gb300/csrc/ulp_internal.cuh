@@ -67,7 +67,7 @@ struct MapState {
   int outer_k, err_flag;
   unsigned arrive, arrive_outer;
   double outer_err;
-  int sweep_epoch, pad;
+  long long loops;          // body executions of the graph-driven solve since its start
 };
 
 // Device-side record of one call (per map), copied to the host at the end.
@@ -100,6 +100,7 @@ struct PcgArgs {
   unsigned long long timeout_ns;
   double omega;
   int apply_only;           // sweep solvers: stop after the first s = M^-1 r (single-step entry point)
+  unsigned long long cond;  // flexible-CG graph: WHILE-node handle cleared when the map stops (0 = none)
 };
 
 // ------------------------------------------------------------------ helpers

@@ -71,7 +71,8 @@ struct XDir32 {  // d = s + beta d_old (FP32), d = s on the first iteration
 
 // FP32 sliding-window stencil (same tiling as the FP64 walker); the diagonal
 // is D = U_{i,j-1} + U_{i,j} + V_{i-1,j} + V_{i,j} from the FP32 weights, so the
-// FP32 operator keeps A 1 = 0 exactly.
+// FP32 operator keeps A 1 = 0 exactly.  FP32 rows move half the bytes of FP64
+// ones, so loads run two rows ahead of the arithmetic to keep enough in flight.
 template <class X, class Epi>
 __device__ __forceinline__ void stencil_tile32(const MapDesc& M, int i0, int i1, int j0, int lane,
                                                const float* U, const float* V, const X& x, Epi& epi) {
@@ -89,52 +90,65 @@ __device__ __forceinline__ void stencil_tile32(const MapDesc& M, int i0, int i1,
     vn = ldf2(V, (size_t)(i0 - 1) * P + j);
   }
   float2 xc = x.make(x.load(i0, j));
-  Raw rs = (i0 + 1 < M.H) ? x.load(i0 + 1, j) : X::zero();
+  // raw x of rows i+1, i+2; weights and halo of rows i, i+1
+  Raw r1 = (i0 + 1 < M.H) ? x.load(i0 + 1, j) : X::zero();
+  Raw r2 = (i0 + 2 < M.H && i0 + 1 < i1) ? x.load(i0 + 2, j) : X::zero();
   size_t off = (size_t)i0 * P + j;
-  float2 u = ldf2(U, off), v = ldf2(V, off);
-  float h = halo ? x.at(i0, hc) : 0.f;
-  float uwh = hw ? __ldcg(U + (size_t)i0 * P + hc) : 0.f;
+  float2 u0 = ldf2(U, off), v0 = ldf2(V, off), u1 = z2, v1 = z2;
+  float h0 = halo ? x.at(i0, hc) : 0.f, h1 = 0.f;
+  float w0 = hw ? __ldcg(U + off - j + hc) : 0.f, w1 = 0.f;
+  if (i0 + 1 < i1) {
+    u1 = ldf2(U, off + P);
+    v1 = ldf2(V, off + P);
+    if (halo) h1 = x.at(i0 + 1, hc);
+    if (hw) w1 = __ldcg(U + off + P - j + hc);
+  }
   for (int i = i0; i < i1; ++i) {
-    const bool more = i + 1 < i1;
-    const size_t off2 = off + P;
-    Raw rs2 = (more && i + 2 < M.H) ? x.load(i + 2, j) : X::zero();
+    // issue the loads two rows ahead
+    Raw r3 = (i + 3 < M.H && i + 2 < i1) ? x.load(i + 3, j) : X::zero();
     float2 u2 = z2, v2 = z2;
-    float h2 = 0.f, uwh2 = 0.f;
-    if (more) {
-      u2 = ldf2(U, off2);
-      v2 = ldf2(V, off2);
-      if (halo) h2 = x.at(i + 1, hc);
-      if (hw) uwh2 = __ldcg(U + (size_t)(i + 1) * P + hc);
+    float h2 = 0.f, w2 = 0.f;
+    if (i + 2 < i1) {
+      const size_t o2 = off + 2 * P;
+      u2 = ldf2(U, o2);
+      v2 = ldf2(V, o2);
+      if (halo) h2 = x.at(i + 2, hc);
+      if (hw) w2 = __ldcg(U + o2 - j + hc);
     }
-    const float2 xs = (i + 1 < M.H) ? x.make(rs) : z2;
+    const float2 xs = (i + 1 < M.H) ? x.make(r1) : z2;
     float west = __shfl_up_sync(kFull, xc.y, 1);
     float east = __shfl_down_sync(kFull, xc.x, 1);
-    float uw = __shfl_up_sync(kFull, u.y, 1);
-    if (lane == 0) { west = h; uw = uwh; }
-    if (lane == 31) east = h;
-    const float dx = __fadd_rn(__fadd_rn(__fadd_rn(uw, u.x), vn.x), v.x);
-    const float dy = __fadd_rn(__fadd_rn(__fadd_rn(u.x, u.y), vn.y), v.y);
+    float uw = __shfl_up_sync(kFull, u0.y, 1);
+    if (lane == 0) { west = h0; uw = w0; }
+    if (lane == 31) east = h0;
+    const float dx = __fadd_rn(__fadd_rn(__fadd_rn(uw, u0.x), vn.x), v0.x);
+    const float dy = __fadd_rn(__fadd_rn(__fadd_rn(u0.x, u0.y), vn.y), v0.y);
     float2 ax;
     ax.x = dx * xc.x;
-    ax.x = fmaf(-u.x, xc.y, ax.x);
+    ax.x = fmaf(-u0.x, xc.y, ax.x);
     ax.x = fmaf(-uw, west, ax.x);
-    ax.x = fmaf(-v.x, xs.x, ax.x);
+    ax.x = fmaf(-v0.x, xs.x, ax.x);
     ax.x = fmaf(-vn.x, xn.x, ax.x);
     ax.y = dy * xc.y;
-    ax.y = fmaf(-u.y, east, ax.y);
-    ax.y = fmaf(-u.x, xc.x, ax.y);
-    ax.y = fmaf(-v.y, xs.y, ax.y);
+    ax.y = fmaf(-u0.y, east, ax.y);
+    ax.y = fmaf(-u0.x, xc.x, ax.y);
+    ax.y = fmaf(-v0.y, xs.y, ax.y);
     ax.y = fmaf(-vn.y, xn.y, ax.y);
     epi(off, xc, ax);
     xn = xc;
     xc = xs;
-    vn = v;
-    rs = rs2;
-    u = u2;
-    v = v2;
-    h = h2;
-    uwh = uwh2;
-    off = off2;
+    vn = v0;
+    r1 = r2;
+    r2 = r3;
+    u0 = u1;
+    v0 = v1;
+    u1 = u2;
+    v1 = v2;
+    h0 = h1;
+    h1 = h2;
+    w0 = w1;
+    w1 = w2;
+    off += P;
   }
 }
 
@@ -212,6 +226,7 @@ __device__ __forceinline__ void a32_tile(const PcgArgs& a, const MapDesc& M, Map
 
 // x += alpha d; then either r -= alpha q, s = M^-1 r (partials) or, on a
 // refresh iteration, phi += x, x = 0 (the residual is then recomputed in FP64).
+// Loads run two rows ahead.
 template <int KIND>
 __device__ __forceinline__ void b32_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t, bool refresh,
                                          int lane) {
@@ -221,29 +236,46 @@ __device__ __forceinline__ void b32_tile(const PcgArgs& a, const MapDesc& M, Map
   const float* d = (it & 1) ? M.h.d0 : M.h.d1;
   const float alpha = (float)*(volatile double*)&S->alpha;
   const int j = g.j0 + 2 * lane;
+  const float2 z2 = make_float2(0.f, 0.f);
+  struct Row {
+    float2 d, x, q, r, di;
+  };
+  auto load = [&](int i) {
+    Row w{z2, z2, z2, z2, z2};
+    if (i < g.i1) {
+      const size_t off = (size_t)i * P + j;
+      w.d = ldf2(d, off);
+      w.x = ldf2(M.h.x, off);
+      if (!refresh) {
+        w.q = ldf2(M.h.q, off);
+        w.r = ldf2(M.h.r, off);
+        if (KIND == kJacobi) w.di = ldf2(M.h.Dinv, off);
+      }
+    }
+    return w;
+  };
   DF rs, rr;
+  Row c0 = load(g.i0), c1 = load(g.i0 + 1);
   for (int i = g.i0; i < g.i1; ++i) {
+    const Row c2 = load(i + 2);
     const size_t off = (size_t)i * P + j;
-    const float2 dv = ldf2(d, off);
-    float2 xv = ldf2(M.h.x, off);
-    xv.x = __fmaf_rn(alpha, dv.x, xv.x);
-    xv.y = __fmaf_rn(alpha, dv.y, xv.y);
+    float2 xv = c0.x;
+    xv.x = __fmaf_rn(alpha, c0.d.x, xv.x);
+    xv.y = __fmaf_rn(alpha, c0.d.y, xv.y);
     if (refresh) {
       double2 ph = ld2(M.f.phi, off);
       ph.x += (double)xv.x;
       ph.y += (double)xv.y;
       st2(M.f.phi, off, ph);
-      stf2(M.h.x, off, make_float2(0.f, 0.f));
+      stf2(M.h.x, off, z2);
     } else {
       stf2(M.h.x, off, xv);
-      const float2 qv = ldf2(M.h.q, off);
-      float2 r = ldf2(M.h.r, off);
-      r.x = __fmaf_rn(-alpha, qv.x, r.x);
-      r.y = __fmaf_rn(-alpha, qv.y, r.y);
+      float2 r = c0.r;
+      r.x = __fmaf_rn(-alpha, c0.q.x, r.x);
+      r.y = __fmaf_rn(-alpha, c0.q.y, r.y);
       stf2(M.h.r, off, r);
       if (KIND == kJacobi) {
-        const float2 di = ldf2(M.h.Dinv, off);
-        const float2 s = make_float2(di.x * r.x, di.y * r.y);
+        const float2 s = make_float2(c0.di.x * r.x, c0.di.y * r.y);
         stf2(M.h.s, off, s);
         rs.add_prod(r.x, s.x);
         rs.add_prod(r.y, s.y);
@@ -251,6 +283,8 @@ __device__ __forceinline__ void b32_tile(const PcgArgs& a, const MapDesc& M, Map
       rr.add_prod(r.x, r.x);
       rr.add_prod(r.y, r.y);
     }
+    c0 = c1;
+    c1 = c2;
   }
   if (!refresh) {
     const double vrr = rr.value();

@@ -25,7 +25,8 @@ ULP_PHI0_ZERO, ULP_PHI0_USER = 0, 1
 EXPORTED = ["ulp_options_default", "ulp_last_error", "unwrap_lp", "ulp_plan_create",
             "ulp_plan_create_batched", "ulp_plan_destroy", "ulp_unwrap", "ulp_unwrap_batched",
             "ulp_plan_last_status", "ulp_wrapped_diffs", "ulp_weights", "ulp_matvec",
-            "ulp_precond_apply", "ulp_pcg", "ulp_plan_counters", "ulp_pcg_noalloc"]
+            "ulp_precond_apply", "ulp_pcg", "ulp_plan_counters", "ulp_pcg_noalloc",
+            "ulp_autotune"]
 
 
 class UlpError(RuntimeError):
@@ -98,6 +99,8 @@ def load(path: str | None = None):
     L.ulp_pcg.argtypes = [P, P, P, I, I, I, D, I, ctypes.POINTER(ulp_options), P, V,
                           ctypes.POINTER(ulp_stats)]
     L.ulp_pcg_noalloc.argtypes = [P, P, P, I, I, I, D, I, P, V, ctypes.POINTER(ulp_stats)]
+    L.ulp_autotune.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ulp_map), I, I, I,
+                               ctypes.c_char_p, ctypes.POINTER(ulp_options)]
     _lib = L
     return L
 
@@ -225,6 +228,28 @@ class Plan:
         st = ulp_stats()
         rc = load().ulp_plan_last_status(self._h, ctypes.byref(st))
         return rc, st.as_dict()
+
+
+def _map_array(maps):
+    arr = (ulp_map * len(maps))()
+    for t, m in enumerate(maps):
+        arr[t].psi = m["psi"].data_ptr()
+        arr[t].mask = m["mask"].data_ptr() if m.get("mask") is not None else None
+        arr[t].phi = m["phi"].data_ptr()
+        arr[t].p = float(m["p"])
+        arr[t].eps = float(m.get("eps", 1e-2))
+    return arr
+
+
+def ulp_autotune(maps, precond="jacobi", precision=ULP_PRECISION_FP64, iters=40, cache_path=None):
+    """ulp_autotune(): fastest tile_rows / blocks_per_sm for these maps (returns ulp_options)."""
+    n = len(maps)
+    Ha = (ctypes.c_int * n)(*[m["psi"].shape[0] for m in maps])
+    Wa = (ctypes.c_int * n)(*[m["psi"].shape[1] for m in maps])
+    best = ulp_options()
+    _check(load().ulp_autotune(n, Ha, Wa, _map_array(maps), _precond(precond), int(precision), int(iters),
+                               cache_path.encode() if cache_path else None, ctypes.byref(best)))
+    return best
 
 
 def ulp_wrapped_diffs(psi, stream=None):

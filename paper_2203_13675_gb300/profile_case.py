@@ -21,13 +21,14 @@ def main():
     ap.add_argument("--max-inner", type=int, default=200)
     ap.add_argument("--max-outer", type=int, default=1)
     ap.add_argument("--calls", type=int, default=2)
+    ap.add_argument("--eager", action="store_true", help="host-driven DCT solve (every kernel a host launch)")
     a = ap.parse_args()
     w = synth.WORKLOADS[a.workload]
     m = synth.workload_map(a.workload)
     psi = torch.from_numpy(m.psi).cuda()
     mask = torch.from_numpy(m.mask).cuda() if m.mask is not None else None
     H, W = m.psi.shape
-    plan = native.Plan(H, W, outer_tol=0.0,
+    plan = native.Plan(H, W, outer_tol=0.0, profile=2 if a.eager else 0,
                        precision=native.ULP_PRECISION_MIXED if a.precision == "mixed" else 0)
     ms = []
     for _ in range(a.calls):

@@ -50,10 +50,33 @@ KERNEL = {("f64", "jacobi"): "k_pcg64", ("f64", "identity"): "k_pcg64", ("mixed"
           ("mixed", "identity"): "k_pcg32", ("f64", "dct"): "flexible-CG graph (k_f_*, k_gemm_nt x4)"}
 DTYPE = {"f64": "f64", "mixed": "f32+f64"}
 
+# Flexible-CG phases (DCT / learned preconditioner), algorithmic HBM bytes per pixel per
+# launch: A reads s, d_old, U, V, D and writes d, q (56); B reads d, phi, q, s, r and writes
+# phi, r and the BF16 copy of r (58); D reads r, s (16).  M is the preconditioner: for the
+# DCT the four BF16 GEMMs, 4 Hp Wp (Hp + Wp) flop per application (tensor-bound).
+FCG_BYTES = {"A": 56, "B": 58, "D": 16}
+FCG_KERNEL = {"A": "k_f_a", "B": "k_f_b", "R": "k_f_res", "D": "k_f_dots", "M": "k_gemm_nt x4 (DCT chain)"}
+
 
 def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
         int(os.environ.get("LOCAL_RANK", 0))
+
+
+def load_peaks_all():
+    """HBM GB/s and bf16 TFLOP/s (burst, sustained) from MEASURED_PEAKS.json, else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    out = {"hbm": (6800.0, "fallback"), "bf16": (1900.0, "fallback bf16 burst"),
+           "bf16_sust": (1700.0, "fallback bf16 sustained")}
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if d.get("hbm_gbs"):
+            out["hbm"] = (float(d["hbm_gbs"]), "measured")
+        if d.get("bf16_tflops"):
+            out["bf16"] = (float(d["bf16_tflops"]), "measured bf16_tflops (burst)")
+        if d.get("bf16_tflops_sustained"):
+            out["bf16_sust"] = (float(d["bf16_tflops_sustained"]), "measured bf16_tflops_sustained")
+    return out
 
 
 def load_peaks():
@@ -268,6 +291,13 @@ def run_ours(args):
     traffic = None
     if tpx is not None and cnt["timed_launches"]:
         traffic = tpx * H * W * iters / cnt["timed_launches"]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "kernel": f"{KERNEL[chosen]}<{chosen[1]}> (persistent PCG)",
+                "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_px_iter": ALG_BYTES[chosen],
+                "solver_ms_per_step": cnt["solver_ms"] / args.steps}
+    if chosen[1] in ("dct", "learned"):
+        roofline = fcg_roofline(native, H, W, psi, mask, w, chosen[1], plan)
 
     # end to end: host (pinned) buffers in, host buffer out, inside the timed region
     psi_h = torch.from_numpy(m.psi).pin_memory()
@@ -318,14 +348,7 @@ def run_ours(args):
                    "inner_iterations": st["inner"], "outer_passes": st["outer"]},
         "plain": {"value": px / (ms_plain * 1e3), "unit": UNIT, "ms_per_step": ms_plain, "precond": "jacobi",
                   "dtype": "f64", "inner_iterations": st_plain["inner"]},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": KERNEL[chosen] if chosen[1] == "dct" else f"{KERNEL[chosen]}<{chosen[1]}> (persistent PCG)",
-                     "peak_source": f"{peak_kind} hbm_gbs",
-                     "alg_bytes_per_px_iter": ALG_BYTES[chosen],
-                     "solver_ms_per_step": cnt["solver_ms"] / args.steps,
-                     "gemm_tflop_per_step": (8.0 * H * W * (H + W) * (iters + st["outer"]) / args.steps / 1e12
-                                             if chosen[1] == "dct" else 0.0)},
+        "roofline": roofline,
         "e2e": {"value": px / (ms_e2e * 1e3), "unit": UNIT, "h2d_bytes_per_step": H * W * 8 + (H * W if mask is not None else 0),
                 "d2h_bytes_per_step": H * W * 8, "ms_per_step": ms_e2e},
         "forms": {f"{k[0]}_{k[1]}": {"value": px / (v[0] * 1e3), "ms_per_step": v[0],
@@ -343,6 +366,52 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def fcg_roofline(native, H, W, psi, mask, w, precond, timed_plan):
+    """Roofline of the dominant kernel of a flexible-CG solve.  Kernels inside the
+    solve's graph cannot carry their own events, so the same solve is replayed
+    host-driven (options.profile = 2) with an event after every phase; the
+    dominant phase (largest summed time) is reported with its algorithmic bytes
+    (or, for the DCT chain, tensor flops) per launch over its mean duration."""
+    peaks = load_peaks_all()
+    eager = native.Plan(H, W, outer_tol=0.0, profile=2)
+    if precond == "learned":
+        eager.set_unet(timed_plan._unet)
+    call = dict(p=w["p"], eps=w["tau"], precond=precond, tol=w["tol"], max_outer=w["max_outer"], stats=False)
+    eager.unwrap(psi, mask, **call)
+    eager.counters(reset=True)
+    eager.unwrap(psi, mask, **call)
+    c = eager.counters(reset=True)
+    eager.close()
+    Hp, Wp = (H + 127) // 128 * 128, (W + 127) // 128 * 128
+    phases = {}
+    for ph, ms in c["phase_ms"].items():
+        n = c["phase_launches"][ph]
+        if n == 0 or ms <= 0:
+            continue
+        mean_s = ms / n / 1e3
+        ent = {"ms_total": ms, "launches": n, "us_per_launch": mean_s * 1e6, "kernel": FCG_KERNEL[ph]}
+        if ph in FCG_BYTES:
+            ent.update(bound="hbm", achieved=FCG_BYTES[ph] * H * W / mean_s / 1e9, unit="GB/s",
+                       peak=peaks["hbm"][0], peak_source=peaks["hbm"][1] + " hbm_gbs",
+                       alg_per_launch=f"{FCG_BYTES[ph]} B/px x {H}x{W}")
+        elif ph == "M" and precond == "dct":
+            fl = 4.0 * Hp * Wp * (Hp + Wp)
+            ent.update(bound="tensor", achieved=fl / mean_s / 1e12, unit="TFLOP/s",
+                       peak=peaks["bf16_sust"][0], peak_source=peaks["bf16_sust"][1],
+                       alg_per_launch=f"4 Hp Wp (Hp + Wp) = {fl:.3g} flop")
+        if "achieved" in ent:
+            ent["frac"] = ent["achieved"] / ent["peak"] if ent["peak"] else None
+        phases[ph] = ent
+    dom = max((k for k in phases if "achieved" in phases[k]), key=lambda k: phases[k]["ms_total"])
+    d = phases[dom]
+    tpx = profile_traffic(f"fcg_{precond}_{dom}_c2_2048")
+    return {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+            "frac": d["frac"], "traffic": (tpx * H * W if tpx is not None else None),
+            "kernel": f"{d['kernel']} (flexible-CG phase {dom}, dominant)", "peak_source": d["peak_source"],
+            "alg_per_launch": d["alg_per_launch"], "measured": "host-driven replay of the same solve, "
+            "CUDA events after every phase on the solve's stream", "phases": phases}
 
 
 # ------------------------------------------------------------------ batched workload

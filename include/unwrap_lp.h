@@ -43,14 +43,16 @@ extern "C" {
 
 /* Preconditioner M of Algorithm 1 ("estimate preconditioning matrix M from A").
  * The first five are the paper's list (Sec. 2, items 1-5); DCT is the
- * unweighted Neumann-Poisson pseudo-inverse applied through cosine transforms. */
+ * unweighted Neumann-Poisson pseudo-inverse applied through cosine transforms;
+ * LEARNED is a trained network (ulp_unet) applied as M^-1 inside flexible CG. */
 typedef enum {
   ULP_PRECOND_IDENTITY = 0, /* M = I: PCG becomes CG */
   ULP_PRECOND_JACOBI = 1,   /* M = diag(A) */
   ULP_PRECOND_ILU0 = 2,     /* incomplete LU, no fill, natural row-major order */
   ULP_PRECOND_IC0 = 3,      /* incomplete Cholesky, no fill (same M as ILU0 for symmetric A) */
   ULP_PRECOND_SSOR = 4,     /* symmetric SOR, relaxation options.omega */
-  ULP_PRECOND_DCT = 5       /* s = L^+ r, L the unit-weight Neumann Laplacian */
+  ULP_PRECOND_DCT = 5,      /* s = L^+ r, L the unit-weight Neumann Laplacian */
+  ULP_PRECOND_LEARNED = 6   /* s = D^-1 r + rho N(r / rho, U, V), rho = rms(r); needs ulp_plan_set_unet */
 } ulp_precond;
 
 typedef enum {
@@ -97,6 +99,10 @@ typedef struct ulp_options {
   int graph;              /* 1: ulp_unwrap / ulp_unwrap_batched capture their kernel sequence into a CUDA
                              graph on the first call and replay it while the arguments stay the same
                              (ignored when profile = 1) */
+  int stall_window;       /* ULP_PRECOND_LEARNED: an inner solve whose ||r||^2 has not dropped by 1% below
+                             its best value for this many iterations, or that meets r^T s <= 0 or
+                             d^T A d <= 0, switches to the Jacobi preconditioner for the rest of that solve;
+                             default (0) 200 (plain CG's residual norm can plateau for tens of iterations) */
 } ulp_options;
 
 /* Per-call statistics, written on the host when the call synchronises. */
@@ -108,6 +114,7 @@ typedef struct ulp_stats {
   long long inner[ULP_MAX_OUTER_STATS];       /* l at exit of each inner solve */
   double relres[ULP_MAX_OUTER_STATS];         /* ||r_l|| / ||b|| at exit of each inner solve */
   double outer_err[ULP_MAX_OUTER_STATS];      /* Algorithm 1's error after each pass (inf if ||phi^k|| = 0) */
+  int fallbacks;                              /* ULP_PRECOND_LEARNED: inner solves that switched to Jacobi */
 } ulp_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -192,6 +199,11 @@ typedef struct ulp_counters {
   long long solver_launches;  /* persistent PCG launches among them */
   double solver_ms;           /* summed duration of the timed solver launches (profile only) */
   long long timed_launches;   /* solver launches included in solver_ms */
+  /* options.profile = 2, flexible-CG solves (DCT, learned), run host-driven: summed durations and
+   * counts of each phase, [0] A (d = s + beta d, q = A d, d^T q), [1] B (phi, r update), [2] R (true
+   * residual), [3] M (s = M^-1 r: the GEMM chain or the network), [4] D (r^T s, r^T r, stop test) */
+  double phase_ms[5];
+  long long phase_launches[5];
 } ulp_counters;
 ULP_API int ulp_plan_counters(ulp_plan plan, int reset, ulp_counters* out);
 
@@ -275,6 +287,84 @@ ULP_API int ulp_pcg(const double* U, const double* V, const double* b, int H, in
 ULP_API int ulp_pcg_noalloc(const double* U, const double* V, const double* b, int H, int W,
                             int precond, double tol, int max_inner, double* phi, void* cuda_stream,
                             ulp_stats* stats);
+
+
+/* ---------------------------------------------------------------------------
+ * Learned preconditioner.  The paper compares fixed algebraic preconditioners
+ * (Sec. 2, items 1-5); this extension replaces the application s = M^-1 r of
+ * Algorithm 1 by a trained network, used inside flexible CG because it is not
+ * a fixed linear operator.  Network: a four-level U-Net on NHWC BF16
+ * activations, widths 16/32/64/128, 3x3 convolutions with ReLU, 2x2 average
+ * pooling and nearest-neighbour upsampling with skip concatenations, and a
+ * linear 1x1 head:
+ *   e0: 3->16 at HxW, e1: 16->32 at H/2, e2: 32->64 at H/4, b3: 64->128 at H/8,
+ *   d2: [e2 | up(b3)] 192->64, d1: [e1 | up(d2)] 96->32, d0: [e0 | up(d1)] 48->16,
+ *   y = w_h . d0 + b_h.
+ * Input per pixel: (r / rho, U, V) with rho = sqrt(mean(r^2)); the
+ * application is the Jacobi step plus the learned correction,
+ * s = D^-1 r + rho * y (D the diagonal of A(U,V); 0 on masked pixels).
+ * Parameters (FP32, canonical order): for e0 e1 e2 b3 d2 d1 d0 the weight
+ * [Cout][Cin][3][3] then the bias [Cout]; then the head weight [16] and bias.
+ * All device pointers; calls on one network must not overlap on the GPU (they
+ * share its workspace).
+ * ------------------------------------------------------------------------- */
+typedef struct ulp_unet_s* ulp_unet;
+
+/* number of parameters (242721) */
+ULP_API int ulp_unet_param_count(void);
+/* new network on the current device: He-uniform weights from splitmix64(seed), zero biases */
+ULP_API int ulp_unet_create(unsigned long long seed, ulp_unet* out);
+ULP_API void ulp_unet_destroy(ulp_unet net);
+/* copy the canonical parameter vector from / to host memory (set resets the optimizer state) */
+ULP_API int ulp_unet_set_params(ulp_unet net, const float* params);
+ULP_API int ulp_unet_get_params(ulp_unet net, float* params);
+/* binary parameter file: "ULPUNET1", int64 count, count FP32 values */
+ULP_API int ulp_unet_save(ulp_unet net, const char* path);
+ULP_API int ulp_unet_load(const char* path, ulp_unet* out);
+
+/* One preconditioner application on an H x W map (contiguous FP64 planes r, U,
+ * V, s; mask uint8 or NULL): s = D^-1 r + rho N(r / rho, U, V), 0 on masked
+ * pixels.  The network runs on the map zero-padded to multiples of 128. */
+ULP_API int ulp_unet_apply(ulp_unet net, const double* r, const double* U, const double* V,
+                           const uint8_t* mask, int H, int W, double* s, void* cuda_stream);
+
+/* Network output y = N(r / rho, U, V) (FP32 [B][H][W]) for B images stored one
+ * after another in r, U, V ([B][H][W] FP64); H, W multiples of 128, B <= 64. */
+ULP_API int ulp_unet_forward(ulp_unet net, int B, int H, int W, const double* r, const double* U,
+                             const double* V, float* y, void* cuda_stream);
+
+/* Training loss and its gradient with respect to the parameters (canonical
+ * order, FP32 device array of ulp_unet_param_count() values, NULL to skip).
+ * Per image, with x = r / rho, e~ = e / rho (e the error of a PCG iterate,
+ * A e = r) and the direction s~ = D^-1 x + y:
+ *   L = 1 - (s~^T x)^2 / ((s~^T A s~)(e~^T x)),
+ * the A-norm fraction of the error that one exact line search along s~ leaves;
+ * the loss is the mean over the B images.  Layout as ulp_unet_forward; loss
+ * (host, nullable) synchronises. */
+ULP_API int ulp_unet_loss_grad(ulp_unet net, int B, int H, int W, const double* r, const double* U,
+                               const double* V, const double* e, double* loss, float* grad,
+                               void* cuda_stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the loss
+ * of B training pairs: pair b is r + pair_idx[b]*H*W, e + pair_idx[b]*H*W with
+ * the weights U + sys_idx[b]*H*W, V + sys_idx[b]*H*W (host index arrays).
+ * loss (host, nullable) receives the batch loss before the step and synchronises. */
+ULP_API int ulp_unet_train_step(ulp_unet net, int B, const long long* pair_idx, const int* sys_idx,
+                                int H, int W, const double* r, const double* e, const double* U,
+                                const double* V, float lr, double* loss, void* cuda_stream);
+
+/* Training pairs from the inner PCG of Algorithm 1 on A(U,V) phi = b: phi* is
+ * the PCG solution to relative residual tol_star (from 0), and for each
+ * k < n, phi_l is the PCG iterate after iters[k] iterations from 0; writes
+ * r_out[k] = b - A phi_l and e_out[k] = phi* - phi_l ([n][H][W] FP64).
+ * precond: identity or Jacobi.  Synchronises. */
+ULP_API int ulp_unet_harvest(const double* U, const double* V, const double* b, int H, int W, int precond,
+                             double tol_star, int n, const int* iters, double* r_out, double* e_out,
+                             void* cuda_stream);
+
+/* Network used by ULP_PRECOND_LEARNED on a single-map FP64 plan (NULL detaches).
+ * The plan does not own it: keep it alive while the plan may use it. */
+ULP_API int ulp_plan_set_unet(ulp_plan plan, ulp_unet net);
 
 #ifdef __cplusplus
 }

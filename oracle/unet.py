@@ -21,17 +21,25 @@ step):
                   H/4, d1: [a1, up(d2)] 96->32 at H/2, d0: [a0, up(d1)] 48->16 at
                   H x W (up = nearest-neighbour 2x); every conv followed by ReLU
   head            y = w_h . d0 + b_h  (1x1, 16 -> 1, linear)
-  application     s = rho * y, and s = 0 on masked pixels
-  training loss   L = mean over pixels of (y - t)^2, t = (e - mean e) / rms(e - mean e)
-                  per image, e the error phi* - phi_l of a PCG iterate.
+  application     s = D^-1 r + rho * y (the Jacobi step plus the learned correction),
+                  D the diagonal of A(U, V), D^-1 = 0 where D = 0; s = 0 on masked pixels
+  training loss   per image, with x = r / rho and s~ = D^-1 x + y (the direction in
+                  units of rho), the A-norm quality of s~ as a conjugate-gradient
+                  search direction for the error e~ = e / rho (A e = r):
+                      L = 1 - (s~^T x)^2 / ((s~^T A s~) (e~^T x))
+                  i.e. 1 - cos^2 of the A-angle between s~ and e~, the fraction of
+                  the error's energy norm that one exact line search along s~ leaves;
+                  the batch loss is the mean over images.
 
 Canonical parameter vector (FP32 on the device, FP64 here): for each conv in
 the order e0 e1 e2 b3 d2 d1 d0 the weight [Cout][Cin][3][3] then the bias
 [Cout]; then the head weight [16] and the head bias [1].
 
 Parity status: conv3x3 and its adjoints are pinned by brute-force loops,
-scipy.signal.correlate2d and the adjoint identities; the gradient by central
-finite differences; the whole network by a hand-built exact identity network
+scipy.signal.correlate2d and the adjoint identities; the stencil by the CSR
+matrix of the main oracle; the loss by its closed form on a direction
+parallel to e (L = 0) and its bounds; the gradient by central finite
+differences; the whole network by a hand-built exact identity network
 (tests/test_oracle_unet.py).
 """
 from __future__ import annotations
@@ -170,6 +178,31 @@ def backward(theta, c, dy):
 
 
 # ---------------------------------------------------------------- preconditioner use
+def diag(U, V):
+    """D of Eq. (Axb): U_{i,j-1} + U_{i,j} + V_{i-1,j} + V_{i,j} (U, V [...,H,W])."""
+    U, V = np.asarray(U, np.float64), np.asarray(V, np.float64)
+    D = U + V
+    D[..., :, 1:] += U[..., :, :-1]
+    D[..., 1:, :] += V[..., :-1, :]
+    return D
+
+
+def stencil(U, V, x):
+    """(A x)_{ij} = D x_{ij} - U_{ij} x_{i,j+1} - U_{i,j-1} x_{i,j-1} - V_{ij} x_{i+1,j} - V_{i-1,j} x_{i-1,j}."""
+    U, V, x = (np.asarray(a, np.float64) for a in (U, V, x))
+    y = diag(U, V) * x
+    y[..., :, :-1] -= U[..., :, :-1] * x[..., :, 1:]
+    y[..., :, 1:] -= U[..., :, :-1] * x[..., :, :-1]
+    y[..., :-1, :] -= V[..., :-1, :] * x[..., 1:, :]
+    y[..., 1:, :] -= V[..., :-1, :] * x[..., :-1, :]
+    return y
+
+
+def jacobi(U, V, x):
+    D = diag(U, V)
+    return np.where(D > 0, x / np.where(D > 0, D, 1.0), 0.0)
+
+
 def network_input(r, U, V):
     """r, U, V [B,H,W] -> (x [B,H,W,3], rho [B]) with x = (r / rho, U, V)."""
     r = np.asarray(r, np.float64)
@@ -181,36 +214,52 @@ def network_input(r, U, V):
     return x, rho
 
 
-def target(e):
-    """Mean-removed, RMS-normalised error per image."""
-    e = np.asarray(e, np.float64)
-    if e.ndim == 2:
-        e = e[None]
-    z = e - e.mean(axis=(1, 2), keepdims=True)
-    s = np.sqrt(np.mean(z * z, axis=(1, 2), keepdims=True))
-    return np.where(s > 0, z / np.where(s > 0, s, 1.0), 0.0)
-
-
-def apply(theta, r, U, V, mask=None):
-    """One preconditioner application s = rho * N_theta(r / rho, U, V) (0 on masked pixels)."""
+def apply(theta, r, U, V, mask=None, pad=128):
+    """One preconditioner application s = D^-1 r + rho * N_theta(r / rho, U, V)
+    (0 on masked pixels).  rho is the RMS over the map itself; the network runs
+    on the input zero-padded to multiples of ``pad`` rows and columns, and its
+    output is cropped back."""
     x, rho = network_input(r, U, V)
-    y, _ = forward(theta, x)
-    s = rho[:, None, None] * y
+    B, H, W, _ = x.shape
+    Hn, Wn = -(-H // pad) * pad, -(-W // pad) * pad
+    xp = np.zeros((B, Hn, Wn, 3))
+    xp[:, :H, :W, :] = x
+    y, _ = forward(theta, xp)
+    s = jacobi(x[..., 1], x[..., 2], np.asarray(r, np.float64).reshape(B, H, W)) + rho[:, None, None] * y[:, :H, :W]
     if mask is not None:
         s = np.where(np.asarray(mask, bool), 0.0, s)
     return s[0] if np.ndim(r) == 2 else s
 
 
+def direction_loss(x, U, V, e_scaled, y):
+    """Per-image loss 1 - (s^T x)^2 / ((s^T A s)(e^T x)) with s = D^-1 x + y, and dL/dy."""
+    s = jacobi(U, V, x) + y
+    As = stencil(U, V, s)
+    a = np.sum(s * x, axis=(1, 2))
+    b = np.sum(s * As, axis=(1, 2))
+    g = np.sum(e_scaled * x, axis=(1, 2))
+    L = 1.0 - a * a / (b * g)
+    # dL/ds = -(2 a / (b g)) x + (2 a^2 / (b^2 g)) A s  (A symmetric)
+    dy = (-(2 * a / (b * g)))[:, None, None] * x + (2 * a * a / (b * b * g))[:, None, None] * As
+    return L, dy
+
+
 def loss_grad(theta, r, U, V, e):
-    """Training loss mean((y - t)^2) on the pairs (r, U, V) -> e, and its gradient."""
-    x, _ = network_input(r, U, V)
-    t = target(e)
+    """Training loss (mean over the batch of the direction loss) and its gradient."""
+    x, rho = network_input(r, U, V)
+    U = np.asarray(U, np.float64).reshape(x.shape[:3])
+    V = np.asarray(V, np.float64).reshape(x.shape[:3])
+    e = np.asarray(e, np.float64).reshape(x.shape[:3])
+    es = e / rho[:, None, None]
     y, c = forward(theta, x)
-    n = y.size
-    loss = float(np.sum((y - t) ** 2) / n)
-    return loss, backward(theta, c, 2.0 * (y - t) / n)
+    L, dy = direction_loss(x[..., 0], U, V, es, y)
+    B = x.shape[0]
+    return float(np.mean(L)), backward(theta, c, dy / B)
 
 
+def zero_params():
+    """N = 0: the application is the Jacobi step."""
+    return np.zeros(param_count())
 def identity_params():
     """Parameters for which N(x) = x_r exactly: e0 splits r into relu(r) and
     relu(-r), d0 passes both through, the head takes their difference."""

@@ -69,6 +69,8 @@ static void destroy_plan(Plan& pl) {
   pl.cap_stream = nullptr;
   for (cudaEvent_t e : pl.ev_pool) cudaEventDestroy(e);
   pl.ev_pool.clear();
+  for (cudaEvent_t e : pl.ph_pool) cudaEventDestroy(e);
+  pl.ph_pool.clear();
   if (pl.arena) cudaFree(pl.arena);
   pl.arena = nullptr;
 }
@@ -86,6 +88,18 @@ static void next_events(Plan& pl, cudaEvent_t* e0, cudaEvent_t* e1) {
   *e0 = pl.ev_pool[pl.ev_used];
   *e1 = pl.ev_pool[pl.ev_used + 1];
   pl.ev_used += 2;
+}
+
+void ulp::phase_mark(Plan& pl, cudaStream_t st, int tag) {
+  if (pl.ph_pool.size() < pl.ph_used + 1) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    pl.ph_pool.push_back(e);
+    pl.ph_tag.push_back(-1);
+  }
+  pl.ph_tag[pl.ph_used] = tag;
+  cudaEventRecord(pl.ph_pool[pl.ph_used], st);
+  pl.ph_used += 1;
 }
 
 // Rows per warp tile: about one tile per resident warp of the persistent
@@ -280,7 +294,7 @@ __global__ void k_set_pt(PT pt, double* p, double* tau, int first, int n) {
 }
 
 static int check_solver_args(int precond, double tol, int max_outer) {
-  if (precond < ULP_PRECOND_IDENTITY || precond > ULP_PRECOND_DCT)
+  if (precond < ULP_PRECOND_IDENTITY || precond > ULP_PRECOND_LEARNED)
     return fail(ULP_ERR_INVALID, "unknown preconditioner %d", precond);
 
   if (!(tol > 0.0)) return fail(ULP_ERR_INVALID, "tol must be > 0");
@@ -298,6 +312,7 @@ static void fill_stats(const MapStats& d, ulp_stats* s) {
     s->relres[k] = d.relres[k];
     s->outer_err[k] = d.outer_err[k];
   }
+  s->fallbacks = d.fallbacks;
 }
 
 static PcgArgs pcg_args(const Plan& pl, double tol, int max_inner) {
@@ -318,6 +333,7 @@ static PcgArgs pcg_args(const Plan& pl, double tol, int max_inner) {
   a.lmax = max_inner;
   a.timeout_ns = (unsigned long long)(pl.opt.spin_timeout_s * 1e9);
   a.omega = pl.opt.omega;
+  a.stall_window = pl.opt.stall_window > 0 ? pl.opt.stall_window : 200;
   return a;
 }
 
@@ -367,7 +383,7 @@ static int enqueue_call(Plan& pl, const ulp_map* maps, int precond, double tol, 
     ULP_CU(launch_system(pl, pl.d_p, pl.d_tau, st));
     cudaEvent_t e0, e1;
     next_events(pl, &e0, &e1);
-    if (precond == ULP_PRECOND_DCT) ULP_CU(launch_fcg(pl, a, st, e0, e1));
+    if (precond == ULP_PRECOND_DCT || precond == ULP_PRECOND_LEARNED) ULP_CU(launch_fcg(pl, precond, a, st, e0, e1));
     else if (mixed) ULP_CU(launch_pcg32(pl, precond, a, st, e0, e1));
     else ULP_CU(launch_pcg64(pl, precond, a, st, e0, e1));
     ULP_CU(launch_outer_error(pl, pl.opt.outer_tol, max_outer, st));
@@ -430,6 +446,8 @@ extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precon
     return fail(ULP_ERR_UNSUPPORTED, "mixed precision supports the identity and Jacobi preconditioners");
   if (precond == ULP_PRECOND_DCT && (pl.nmaps != 1 || !pl.dct))
     return fail(ULP_ERR_UNSUPPORTED, "the DCT preconditioner is available on single-map plans");
+  if (precond == ULP_PRECOND_LEARNED && (pl.nmaps != 1 || !pl.unet))
+    return fail(ULP_ERR_UNSUPPORTED, "the learned preconditioner needs a single-map plan and ulp_plan_set_unet");
   for (int m = 0; m < pl.nmaps; ++m) {
     if (!maps[m].psi || !maps[m].phi) return fail(ULP_ERR_INVALID, "map %d: null psi or phi", m);
     if (!(maps[m].p >= 0.0 && maps[m].p <= 2.0)) return fail(ULP_ERR_INVALID, "map %d: p outside [0, 2]", m);
@@ -438,8 +456,8 @@ extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precon
   ULP_CU(cudaSetDevice(pl.device));
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   pl.last_stream = st;
-  // the DCT solve is itself a graph with a WHILE node, which cannot be nested: it runs eagerly
-  if (pl.opt.graph && !pl.opt.profile && precond != ULP_PRECOND_DCT)
+  // the DCT and learned solves are themselves graphs with a WHILE node, which cannot be nested: they run eagerly
+  if (pl.opt.graph && !pl.opt.profile && precond != ULP_PRECOND_DCT && precond != ULP_PRECOND_LEARNED)
     rc = graph_call(pl, maps, precond, tol, max_outer, max_inner, st, mixed);
   else rc = enqueue_call(pl, maps, precond, tol, max_outer, max_inner, st, mixed);
   if (rc != ULP_OK) return rc;
@@ -471,11 +489,39 @@ extern "C" int ulp_plan_counters(ulp_plan plan, int reset, ulp_counters* out) {
     ULP_CU(cudaEventElapsedTime(&ms, pl.ev_pool[k], pl.ev_pool[k + 1]));
     out->solver_ms += ms;
   }
+  for (int k = 0; k < 5; ++k) {
+    out->phase_ms[k] = 0.0;
+    out->phase_launches[k] = 0;
+  }
+  for (size_t k = 1; k < pl.ph_used; ++k) {
+    const int t = pl.ph_tag[k];
+    if (t < 0 || t > 4) continue;
+    ULP_CU(cudaEventSynchronize(pl.ph_pool[k]));
+    float ms = 0.f;
+    ULP_CU(cudaEventElapsedTime(&ms, pl.ph_pool[k - 1], pl.ph_pool[k]));
+    out->phase_ms[t] += ms;
+    out->phase_launches[t] += 1;
+  }
   if (reset) {
     pl.kernel_launches = 0;
     pl.solver_launches = 0;
     pl.ev_used = 0;
+    pl.ph_used = 0;
   }
+  return ULP_OK;
+}
+
+extern "C" int ulp_plan_set_unet(ulp_plan plan, ulp_unet net) {
+  if (!plan) return fail(ULP_ERR_INVALID, "null plan");
+  Plan& pl = plan->p;
+  if (net && (pl.nmaps != 1 || pl.opt.precision != ULP_PRECISION_FP64))
+    return fail(ULP_ERR_UNSUPPORTED, "the learned preconditioner needs a single-map FP64 plan");
+  Unet* u = net ? ulp_unet_impl(net) : nullptr;
+  if (u != pl.unet && pl.fcg_kind == ULP_PRECOND_LEARNED) {
+    ULP_CU(cudaSetDevice(pl.device));
+    destroy_fcg(pl);  // the captured solve refers to the old network's buffers
+  }
+  pl.unet = u;
   return ULP_OK;
 }
 
@@ -634,7 +680,9 @@ extern "C" int ulp_precond_apply(int precond, const double* U, const double* V, 
   const MapDesc& M = pl.hmaps[0];
   rc = load_weights(pl, U, V, tp.st);
   if (rc != ULP_OK) return rc;
-  if (precond == ULP_PRECOND_IDENTITY || precond == ULP_PRECOND_JACOBI) {
+  if (precond == ULP_PRECOND_LEARNED) {
+    return fail(ULP_ERR_UNSUPPORTED, "ulp_precond_apply: use ulp_unet_apply for the learned preconditioner");
+  } else if (precond == ULP_PRECOND_IDENTITY || precond == ULP_PRECOND_JACOBI) {
     ULP_CU(launch_to_plane(pl, r, M.f.r, tp.st));
     ULP_CU(launch_jacobi_apply(pl, precond, M.f.r, M.f.s, tp.st));
   } else if (precond == ULP_PRECOND_DCT) {
@@ -670,7 +718,8 @@ extern "C" int ulp_pcg(const double* U, const double* V, const double* b, int H,
   if (rc != ULP_OK) return rc;
   ULP_CU(launch_to_plane(pl, b, M.f.b, tp.st));
   ULP_CU(launch_to_plane(pl, phi, M.f.phi, tp.st));
-  if (precond == ULP_PRECOND_DCT) ULP_CU(launch_fcg(pl, pcg_args(pl, tol, max_inner), tp.st));
+  if (precond == ULP_PRECOND_LEARNED) return fail(ULP_ERR_UNSUPPORTED, "ulp_pcg: the learned preconditioner needs a plan");
+  if (precond == ULP_PRECOND_DCT) ULP_CU(launch_fcg(pl, precond, pcg_args(pl, tol, max_inner), tp.st));
   else ULP_CU(launch_pcg64(pl, precond, pcg_args(pl, tol, max_inner), tp.st, nullptr, nullptr));
   ULP_CU(launch_outer_error(pl, 0.0, 1, tp.st));
   ULP_CU(launch_from_plane(pl, M.f.phi, phi, tp.st));

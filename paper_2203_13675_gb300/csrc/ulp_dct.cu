@@ -29,94 +29,27 @@
 #include <vector>
 
 #include "ulp_host.h"
+#include "ulp_tc.cuh"
 
 namespace ulp {
 
 constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 3;
 constexpr int kTileBytes = kBM * kBK * 2;                 // 16 KB per operand tile
 constexpr int kStageBytes = 2 * kTileBytes;               // A + B
-constexpr int kGemmSmem = kStages * kStageBytes + 1024 + 256;  // + alignment + barriers
+constexpr int kGemmSmem = kStages * kStageBytes + 1024 + 256 + 512;  // + alignment + barriers + 1/Lambda rows
 
 enum Epi { kEpiBf16T = 0, kEpiBf16TScale = 1, kEpiF64TMask = 2 };
 
 struct GemmOut {
   void* out;           // Epi 0/1: bf16 [N][ldo]; Epi 2: double plane [*][ldo]
   int ldo;
-  const float* scale;  // Epi 1: [N][ldo] multiplier
-  const uint8_t* mask; // Epi 2: [*][ldo] (1 = zero the output), may be null
+  const float* lh;     // Epi 1: eigenvalues 2 - 2 cos(pi a / H) by output row n (+inf on padding)
+  const float* lw;     // Epi 1: eigenvalues 2 - 2 cos(pi b / W) by output column m (+inf on padding)
+  const unsigned* mbits; // Epi 2: mask bits, bit (n & 31) of word [n >> 5][m] (1 = zero the output), or null
+  int ldb;               // Epi 2: row stride of mbits in words
   int rows, cols;      // Epi 2: only n < rows and m < cols are written
   int* err;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait on an mbarrier phase; false (and the error flag set) after 2 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*(volatile int*)err || globaltimer() - t0 > 2000000000ull) {
-      atomicExch(err, 1);
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, uint64_t* bar, int c0, int c1) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
-      : "memory");
-}
-__device__ __forceinline__ uint64_t sw128_desc(const void* p) {
-  // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
-  // 1024 bytes (stride byte offset), descriptor version 1
-  const uint64_t a = (smem_u32(p) & 0x3FFFFu) >> 4;
-  return a | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
-}
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
@@ -135,6 +68,20 @@ __global__ void __launch_bounds__(128, 1) k_gemm_nt(const __grid_constant__ CUte
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
   const int nkb = K / kBK;
+  float* s_lh = reinterpret_cast<float*>(base + kStages * kStageBytes + 256);
+  const int m = m0 + warp * 32 + lane;  // this thread's accumulator row in the epilogue
+  float lwm = 0.f;
+  uint32_t zbits[kBN / 32] = {};        // Epi 2: mask bits of this thread's 128 outputs
+  if (EPI == kEpiBf16TScale) {
+    s_lh[threadIdx.x] = o.lh[n0 + threadIdx.x];
+    lwm = o.lw[m];
+  } else if (EPI == kEpiF64TMask) {
+    // four coalesced words, issued before the main loop so they overlap the MMAs
+    if (o.mbits) {
+#pragma unroll
+      for (int w = 0; w < kBN / 32; ++w) zbits[w] = __ldg(o.mbits + (size_t)((n0 >> 5) + w) * o.ldb + m);
+    }
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -190,7 +137,6 @@ __global__ void __launch_bounds__(128, 1) k_gemm_nt(const __grid_constant__ CUte
   const bool ready = __all_sync(0xffffffffu, mbar_wait(done, 0, o.err));
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ready) {
-    const int m = m0 + warp * 32 + lane;
 #pragma unroll 1
     for (int c = 0; c < kBN / 16; ++c) {
       float v[16];
@@ -202,10 +148,13 @@ __global__ void __launch_bounds__(128, 1) k_gemm_nt(const __grid_constant__ CUte
         if (EPI == kEpiBf16T) {
           reinterpret_cast<__nv_bfloat16*>(o.out)[off] = __float2bfloat16_rn(v[q]);
         } else if (EPI == kEpiBf16TScale) {
-          reinterpret_cast<__nv_bfloat16*>(o.out)[off] = __float2bfloat16_rn(v[q] * o.scale[off]);
+          // 1/Lambda(a, b) with a = n, b = m; the zero mode and the padding give 0
+          const float sc = (n | m) ? 1.f / (s_lh[c * 16 + q] + lwm) : 0.f;
+          reinterpret_cast<__nv_bfloat16*>(o.out)[off] = __float2bfloat16_rn(v[q] * sc);
         } else {
           if (n < o.rows && m < o.cols) {
-            const bool z = o.mask && o.mask[off];
+            const int nn = c * 16 + q;
+            const bool z = (zbits[nn >> 5] >> (nn & 31)) & 1u;
             reinterpret_cast<double*>(o.out)[off] = z ? 0.0 : (double)v[q];
           }
         }
@@ -227,24 +176,24 @@ __global__ void k_pack_bf16(const double* __restrict__ r, int H, int W, int pitc
   }
 }
 
-// ------------------------------------------------------------------ host side
-using PFN_encodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                     const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
-                                     CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
-                                     CUtensorMapFloatOOBfill);
-
-static PFN_encodeTiled encode_fn() {
-  static PFN_encodeTiled fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_encodeTiled>(p);
+// mask (uint8 plane, pitch) -> bits[(i >> 5)][j], bit (i & 31); rows >= H and columns >= W are 0
+__global__ void k_mask_bits(const uint8_t* __restrict__ mask, int H, int W, int pitch, unsigned* bits, int Hp,
+                            int Wp) {
+  const int nw = Hp / 32;
+  const size_t n = (size_t)nw * Wp;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const int w = (int)(t / Wp), j = (int)(t % Wp);
+    unsigned v = 0;
+    if (j < W)
+      for (int b = 0; b < 32; ++b) {
+        const int i = 32 * w + b;
+        if (i < H && mask[(size_t)i * pitch + j]) v |= 1u << b;
+      }
+    bits[t] = v;
   }
-  return fn;
 }
 
+// ------------------------------------------------------------------ host side
 // 2-D BF16 tensor [rows][cols] (cols contiguous), box 64 x 128, 128-byte swizzle.
 static bool make_map(CUtensorMap* tm, const void* ptr, int rows, int cols) {
   PFN_encodeTiled fn = encode_fn();
@@ -294,14 +243,15 @@ struct DctPlan {
   int H = 0, W = 0, Hp = 0, Wp = 0;
   __nv_bfloat16 *CH = nullptr, *CHT = nullptr, *CW = nullptr, *CWT = nullptr;
   __nv_bfloat16 *R = nullptr, *X = nullptr, *Y = nullptr;  // R, X^T / S^, Y^T
-  float* lam_inv = nullptr;                                  // [Hp][Wp]
+  float *lh = nullptr, *lw = nullptr;                        // [Hp], [Wp] eigenvalue factors
+  unsigned* mbits = nullptr;                                 // [Hp / 32][Wp] mask bits
   int* err = nullptr;
   void* mem = nullptr;
 };
 
 size_t dct_bytes(int H, int W) {
   const size_t Hp = (H + 127) / 128 * 128, Wp = (W + 127) / 128 * 128;
-  return 2 * (Hp * Hp + Wp * Wp) * 2 + 3 * Hp * Wp * 2 + Hp * Wp * 4 + 4096;
+  return 2 * (Hp * Hp + Wp * Wp) * 2 + 3 * Hp * Wp * 2 + (Hp + Wp) * 4 + Hp / 32 * Wp * 4 + 4096;
 }
 
 // Builds the matrices into mem (dct_bytes(H, W) bytes of device memory).
@@ -325,7 +275,9 @@ int dct_setup(DctPlan& d, int H, int W, void* mem) {
   d.R = static_cast<__nv_bfloat16*>(take(Hp * Wp * 2));
   d.X = static_cast<__nv_bfloat16*>(take(Hp * Wp * 2));
   d.Y = static_cast<__nv_bfloat16*>(take(Hp * Wp * 2));
-  d.lam_inv = static_cast<float*>(take(Hp * Wp * 4));
+  d.lh = static_cast<float*>(take(Hp * 4));
+  d.lw = static_cast<float*>(take(Wp * 4));
+  d.mbits = static_cast<unsigned*>(take(Hp / 32 * Wp * 4));
   d.err = static_cast<int*>(take(256));
   std::vector<__nv_bfloat16> C, CT;
   dct_matrix(H, d.Hp, C, CT);
@@ -334,15 +286,13 @@ int dct_setup(DctPlan& d, int H, int W, void* mem) {
   dct_matrix(W, d.Wp, C, CT);
   if (cudaMemcpy(d.CW, C.data(), C.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return -2;
   if (cudaMemcpy(d.CWT, CT.data(), CT.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return -2;
-  std::vector<float> li(Hp * Wp, 0.f);
+  // Lambda(a, b) = lh[a] + lw[b]; padded indices get +inf so that 1/Lambda = 0 there
   const double pi = 3.14159265358979323846;
-  for (int a = 0; a < H; ++a)
-    for (int b = 0; b < W; ++b) {
-      if (a == 0 && b == 0) continue;
-      const double lam = (2.0 - 2.0 * std::cos(pi * a / H)) + (2.0 - 2.0 * std::cos(pi * b / W));
-      li[(size_t)a * Wp + b] = (float)(1.0 / lam);
-    }
-  if (cudaMemcpy(d.lam_inv, li.data(), li.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return -2;
+  std::vector<float> lh(Hp, INFINITY), lw(Wp, INFINITY);
+  for (int a = 0; a < H; ++a) lh[a] = (float)(2.0 - 2.0 * std::cos(pi * a / H));
+  for (int b = 0; b < W; ++b) lw[b] = (float)(2.0 - 2.0 * std::cos(pi * b / W));
+  if (cudaMemcpy(d.lh, lh.data(), Hp * 4, cudaMemcpyHostToDevice) != cudaSuccess) return -2;
+  if (cudaMemcpy(d.lw, lw.data(), Wp * 4, cudaMemcpyHostToDevice) != cudaSuccess) return -2;
   if (cudaMemset(d.err, 0, 256) != cudaSuccess) return -2;
   return 0;
 }
@@ -366,11 +316,27 @@ int dct_error(const DctPlan& d) {
 }
 
 // s = Pi L^+ r: r, s are FP64 planes with the given pitch; mask a uint8 plane or null.
+unsigned* dct_input(const DctPlan& d, int* ld_pairs) {
+  *ld_pairs = d.Wp / 2;
+  return reinterpret_cast<unsigned*>(d.R);
+}
+
+static int elem_blocks(size_t n) { return (int)((n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048); }
+
+cudaError_t dct_prepare_mask(const DctPlan& d, const uint8_t* mask, int pitch, cudaStream_t st) {
+  if (mask)
+    k_mask_bits<<<elem_blocks((size_t)d.Hp / 32 * d.Wp), 256, 0, st>>>(mask, d.H, d.W, pitch, d.mbits, d.Hp, d.Wp);
+  return cudaGetLastError();
+}
+
 cudaError_t dct_apply(const DctPlan& d, const double* r, int pitch, const uint8_t* mask, double* s,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool packed) {
   const int Hp = d.Hp, Wp = d.Wp;
-  k_pack_bf16<<<(Hp * Wp + 255) / 256 < 2048 ? (Hp * Wp + 255) / 256 : 2048, 256, 0, st>>>(r, d.H, d.W, pitch,
-                                                                                         d.R, Hp, Wp);
+  if (!packed) {
+    k_pack_bf16<<<elem_blocks((size_t)Hp * Wp), 256, 0, st>>>(r, d.H, d.W, pitch, d.R, Hp, Wp);
+    const cudaError_t e = dct_prepare_mask(d, mask, pitch, st);
+    if (e != cudaSuccess) return e;
+  }
   GemmOut o{};
   o.err = d.err;
   // G1: X^T[b][i] = sum_j R[i][j] C_W[b][j]
@@ -381,19 +347,21 @@ cudaError_t dct_apply(const DctPlan& d, const double* r, int pitch, const uint8_
   // G2: S^[a][b] = (sum_i X^T[b][i] C_H[a][i]) / Lambda[a][b]
   o.out = d.Y;
   o.ldo = Wp;
-  o.scale = d.lam_inv;
+  o.lh = d.lh;
+  o.lw = d.lw;
   e = gemm<kEpiBf16TScale>(d.X, Wp, d.CH, Hp, Hp, o, st);
   if (e != cudaSuccess) return e;
   // G3: Y^T[j][a] = sum_b S^[a][b] C_W^T[j][b]
   o.out = d.X;
   o.ldo = Hp;
-  o.scale = nullptr;
+  o.lh = o.lw = nullptr;
   e = gemm<kEpiBf16T>(d.Y, Hp, d.CWT, Wp, Wp, o, st);
   if (e != cudaSuccess) return e;
   // G4: S[i][j] = sum_a Y^T[j][a] C_H^T[i][a], masked, into the FP64 plane
   o.out = s;
   o.ldo = pitch;
-  o.mask = mask;
+  o.mbits = mask ? d.mbits : nullptr;
+  o.ldb = Wp;
   o.rows = d.H;
   o.cols = d.W;
   return gemm<kEpiF64TMask>(d.X, Wp, d.CHT, Hp, Hp, o, st);

@@ -144,15 +144,20 @@ enum Phase { kPhResInit = 0, kPhA = 1, kPhB = 2, kPhRes = 3, kPhFcg = 4 };
 __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, MapState* Sp, int ph, int lane) {
   volatile MapState* S = Sp;
   const int base = M.tile_base, n = M.ntiles;
-  const double v0 = warp_sum_partials(a.P0 + base, n, lane);
-  double v1 = 0.0, v2 = 0.0;
-  if (ph != kPhA) v1 = warp_sum_partials(a.P1 + base, n, lane);
-  if (ph == kPhResInit || ph == kPhFcg) v2 = warp_sum_partials(a.P2 + base, n, lane);
+  const int cnt = (ph == kPhA) ? 1 : (ph == kPhResInit || ph == kPhFcg) ? 3 : 2;
+  double v0, v1, v2;
+  warp_sum_partials3(a.P0 + base, a.P1 + base, a.P2 + base, cnt, n, lane, v0, v1, v2);
   if (lane == 0) {
     bool done = false;
     if (ph == kPhA) {
       S->dq = v0;
-      if (!(v0 > 0.0) || !isfinite(v0)) {  // breakdown: stop after this iteration
+      if ((!(v0 > 0.0) || !isfinite(v0)) && a.learned && !S->fallback) {
+        // the network gave a direction that is not a descent direction: no step,
+        // Jacobi from now on, and the next direction restarts (beta = 0)
+        S->alpha = 0.0;
+        S->fallback = 1;
+        S->restart = 1;
+      } else if (!(v0 > 0.0) || !isfinite(v0)) {  // breakdown: stop after this iteration
         S->status = -3;
         S->alpha = 0.0;
         S->stop_after = 1;
@@ -166,13 +171,25 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
         S->rr = v1;
         S->bb = v2;
         S->iter = 0;
+        S->rr_best = v1;
+        S->stall = 0;
       } else if (ph == kPhFcg) {
         // flexible CG (Polak-Ribiere): beta = r_{k+1}^T (s_{k+1} - s_k) / (r_k^T s_k), v2 = r_{k+1}^T s_k
         const double dold = S->delta;
         S->delta = v0;
         S->rr = v1;
-        S->beta = (v0 - v2) / dold;
+        S->beta = S->restart ? 0.0 : (v0 - v2) / dold;
+        S->restart = 0;
         S->iter += 1;
+        if (a.learned && !S->fallback) {
+          if (v1 < 0.99 * S->rr_best) {
+            S->rr_best = v1;
+            S->stall = 0;
+          } else if (++S->stall >= a.stall_window || !(v0 > 0.0)) {
+            S->fallback = 1;  // the next s is D^-1 r and the direction restarts from it
+            S->restart = 1;
+          }
+        }
       } else {
         const double dold = S->delta;
         S->delta = v0;

@@ -14,9 +14,12 @@
 // Per iteration:  A: d = s + beta d, q = A d, d^T q -> alpha
 //                 B: phi += alpha d, r -= alpha q (not on refresh iterations), r^T s_k
 //                 R: on refresh iterations r = b - A phi, r^T s_k
-//                 DCT: s = Pi L^+ r (pack + 4 tcgen05 GEMMs)
+//                 DCT: s = Pi L^+ r (4 tcgen05 GEMMs on the BF16 copy of r that B and R write)
 //                 D: r^T s, r^T r -> beta, stop test, WHILE condition
+#include <cuda_bf16.h>
+
 #include "ulp_engine.cuh"
+
 #include "ulp_host.h"
 
 namespace ulp {
@@ -31,6 +34,14 @@ __global__ void k_set_args(PcgArgs a, PcgArgs* dst) { *dst = a; }
   const MapDesc& M = a.maps[0];                                        \
   MapState* S = a.st;                                                  \
   for (int t = gw; t < a.ntiles; t += NW)
+
+// BF16 copy of r at (i, j), (i, j+1) for the DCT's first GEMM (zero beyond column W-1)
+__device__ __forceinline__ void put_rbf(const PcgArgs& a, const MapDesc& M, int i, int j, double2 r) {
+  if (a.rbf && j < M.W) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn((float)r.x, j + 1 < M.W ? (float)r.y : 0.f);
+    a.rbf[(size_t)i * a.rbf_ld + (j >> 1)] = *reinterpret_cast<const unsigned*>(&v);
+  }
+}
 
 // The WHILE loop's own guard (one thread), run after the start phase and at the
 // head of every body execution: a map that has stopped -- or was never active in
@@ -55,7 +66,7 @@ __global__ void k_f_guard(const PcgArgs* pa, int count) {
 }
 
 // r = b - A phi (start, or refresh iterations only); on refresh iterations also r^T s_k.
-__global__ void __launch_bounds__(kThreads) k_f_res(const PcgArgs* pa, int refresh_only) {
+__global__ void __launch_bounds__(kThreads, 2) k_f_res(const PcgArgs* pa, int refresh_only) {
   const PcgArgs a = *pa;
   FCG_TILE_LOOP(a) {
     if (*(volatile int*)&S->done) return;
@@ -64,10 +75,13 @@ __global__ void __launch_bounds__(kThreads) k_f_res(const PcgArgs* pa, int refre
     const TileGeo g = tile_geo(M, t, a.R);
     XPlane x{M.f.phi, (size_t)M.pitch};
     double rsp = 0.0;
+    const int j = g.j0 + 2 * lane;
+    int ir = g.i0;  // the walker calls epi once per row, in order
     auto epi = [&](size_t off, double2, double2 ax) {
       const double2 bv = ld2(M.f.b, off);
       const double2 r = make_double2(bv.x - ax.x, bv.y - ax.y);
       st2(M.f.r, off, r);
+      put_rbf(a, M, ir++, j, r);
       if (refresh_only) {
         const double2 sv = ld2(M.f.s, off);
         rsp = fma(r.x, sv.x, rsp);
@@ -100,25 +114,47 @@ __global__ void __launch_bounds__(kThreads) k_f_b(const PcgArgs* pa) {
     const bool refresh = (it % M.refresh) == 0;
     const TileGeo g = tile_geo(M, t, a.R);
     const size_t P = M.pitch;
-    const double* d = (it & 1) ? M.f.d0 : M.f.d1;
+    const double* __restrict__ d = (it & 1) ? M.f.d0 : M.f.d1;
+    double* __restrict__ phi = M.f.phi;
+    double* __restrict__ rp = M.f.r;
+    const double* __restrict__ qp = M.f.q;
+    const double* __restrict__ sp = M.f.s;
     const double alpha = *(volatile double*)&S->alpha;
     const int j = g.j0 + 2 * lane;
     double rsp = 0.0;
-    for (int i = g.i0; i < g.i1; ++i) {
-      const size_t off = (size_t)i * P + j;
-      const double2 dv = ld2(d, off);
-      double2 ph = ld2(M.f.phi, off);
-      ph.x = fma(alpha, dv.x, ph.x);
-      ph.y = fma(alpha, dv.y, ph.y);
-      st2(M.f.phi, off, ph);
-      if (!refresh) {
-        const double2 qv = ld2(M.f.q, off), sv = ld2(M.f.s, off);
-        double2 r = ld2(M.f.r, off);
-        r.x = fma(-alpha, qv.x, r.x);
-        r.y = fma(-alpha, qv.y, r.y);
-        st2(M.f.r, off, r);
-        rsp = fma(r.x, sv.x, rsp);
-        rsp = fma(r.y, sv.y, rsp);
+    // rows in groups of four, all loads of a group issued before its stores
+    for (int i = g.i0; i < g.i1; i += 4) {
+      double2 dv[4], ph[4], qv[4], sv[4], rv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (i + k < g.i1) {
+          const size_t off = (size_t)(i + k) * P + j;
+          dv[k] = ld2(d, off);
+          ph[k] = ld2(phi, off);
+          if (!refresh) {
+            qv[k] = ld2(qp, off);
+            sv[k] = ld2(sp, off);
+            rv[k] = ld2(rp, off);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (i + k < g.i1) {
+          const size_t off = (size_t)(i + k) * P + j;
+          ph[k].x = fma(alpha, dv[k].x, ph[k].x);
+          ph[k].y = fma(alpha, dv[k].y, ph[k].y);
+          st2(phi, off, ph[k]);
+          if (!refresh) {
+            double2 r = rv[k];
+            r.x = fma(-alpha, qv[k].x, r.x);
+            r.y = fma(-alpha, qv[k].y, r.y);
+            st2(rp, off, r);
+            put_rbf(a, M, i + k, j, r);
+            rsp = fma(r.x, sv[k].x, rsp);
+            rsp = fma(r.y, sv[k].y, rsp);
+          }
+        }
       }
     }
     if (!refresh) {
@@ -129,43 +165,112 @@ __global__ void __launch_bounds__(kThreads) k_f_b(const PcgArgs* pa) {
 }
 
 // r^T s, r^T r (and b^T b at the start) -> delta, beta, stop test.
-__global__ void __launch_bounds__(kThreads) k_f_dots(const PcgArgs* pa, int init) {
+__global__ void __launch_bounds__(kThreads, 2) k_f_dots(const PcgArgs* pa, int init) {
   const PcgArgs a = *pa;
   FCG_TILE_LOOP(a) {
     if (*(volatile int*)&S->done) return;
     const TileGeo g = tile_geo(M, t, a.R);
     const size_t P = M.pitch;
     const int j = g.j0 + 2 * lane;
+    const double* __restrict__ rp = M.f.r;
+    const double* __restrict__ sp = M.f.s;
+    const double* __restrict__ bp = M.f.b;
     double rs = 0.0, rr = 0.0, bb = 0.0;
-    for (int i = g.i0; i < g.i1; ++i) {
-      const size_t off = (size_t)i * P + j;
-      const double2 rv = ld2(M.f.r, off), sv = ld2(M.f.s, off);
-      rs = fma(rv.x, sv.x, rs);
-      rs = fma(rv.y, sv.y, rs);
-      rr = fma(rv.x, rv.x, rr);
-      rr = fma(rv.y, rv.y, rr);
-      if (init) {
-        const double2 bv = ld2(M.f.b, off);
-        bb = fma(bv.x, bv.x, bb);
-        bb = fma(bv.y, bv.y, bb);
+    for (int i = g.i0; i < g.i1; i += 4) {
+      double2 rv[4], sv[4], bv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (i + k < g.i1) {
+          const size_t off = (size_t)(i + k) * P + j;
+          rv[k] = ld2(rp, off);
+          sv[k] = ld2(sp, off);
+          if (init) bv[k] = ld2(bp, off);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (i + k < g.i1) {
+          rs = fma(rv[k].x, sv[k].x, rs);
+          rs = fma(rv[k].y, sv[k].y, rs);
+          rr = fma(rv[k].x, rv[k].x, rr);
+          rr = fma(rv[k].y, rv[k].y, rr);
+          if (init) {
+            bb = fma(bv[k].x, bv[k].x, bb);
+            bb = fma(bv[k].y, bv[k].y, bb);
+          }
+        }
       }
     }
     tile_arrive(a, M, S, t, init ? kPhResInit : kPhFcg, rs, rr, bb, lane);
   }
 }
 
+// Learned preconditioner's fallback: s = D^-1 r once the map's fallback flag is
+// set (the network kernels skip themselves from then on).
+__global__ void __launch_bounds__(kThreads) k_f_jacobi(const PcgArgs* pa) {
+  const PcgArgs a = *pa;
+  FCG_TILE_LOOP(a) {
+    if (*(volatile int*)&S->done || !*(volatile int*)&S->fallback) return;
+    const TileGeo g = tile_geo(M, t, a.R);
+    const size_t P = M.pitch;
+    const int j = g.j0 + 2 * lane;
+    const double* __restrict__ rp = M.f.r;
+    const double* __restrict__ dp = M.f.Dinv;
+    double* __restrict__ sp = M.f.s;
+    for (int i = g.i0; i < g.i1; ++i) {
+      const size_t off = (size_t)i * P + j;
+      const double2 rv = ld2(rp, off), di = ld2(dp, off);
+      st2(sp, off, make_double2(di.x * rv.x, di.y * rv.y));
+    }
+  }
+}
+
 static int tile_blocks(const Plan& pl) { return (pl.ntiles + kWarps - 1) / kWarps; }
 
-// Captures the solve graph: start (r, s, delta_0) then WHILE { A, B, R, DCT, D }.
-static cudaError_t fcg_build(Plan& pl) {
+// s = M^-1 r of the flexible solve: the DCT chain, or the network followed by its
+// Jacobi fallback (only one of the two does work in any iteration).
+static cudaError_t fcg_precond(Plan& pl, int kind, cudaStream_t st) {
+  const MapDesc& M = pl.hmaps[0];
+  if (kind == ULP_PRECOND_DCT) return dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st, true);
+  const cudaError_t e = unet_apply_plane(*pl.unet, M.f.r, M.f.U, M.f.V, M.f.mask, M.H, M.W, M.pitch, M.f.s,
+                                         &pl.dstate[0].fallback, st);
+  if (e != cudaSuccess) return e;
+  k_f_jacobi<<<tile_blocks(pl), kThreads, 0, st>>>(pl.dargs);
+  return cudaGetLastError();
+}
+
+// Start of a solve: r = b - A phi (and its BF16 copy), the mask bits, s = M^-1 r, delta_0.
+static cudaError_t fcg_start(Plan& pl, int kind, cudaStream_t st) {
+  const MapDesc& M = pl.hmaps[0];
+  const int nb = tile_blocks(pl);
+  k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && kind == ULP_PRECOND_DCT) e = dct_prepare_mask(*pl.dct, M.f.mask, M.pitch, st);
+  if (e == cudaSuccess) e = fcg_precond(pl, kind, st);
+  k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+// One iteration: A, B, R, s = M^-1 r, D.
+static cudaError_t fcg_iteration(Plan& pl, int kind, cudaStream_t st) {
+  const int nb = tile_blocks(pl);
+  k_f_a<<<nb, kThreads, 0, st>>>(pl.dargs);
+  k_f_b<<<nb, kThreads, 0, st>>>(pl.dargs);
+  k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = fcg_precond(pl, kind, st);
+  k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+// Captures the solve graph: start, then WHILE { guard, iteration }.
+static cudaError_t fcg_build(Plan& pl, int kind) {
   cudaError_t e = cudaSuccess;
   if (!pl.cap_stream) {
     e = cudaStreamCreateWithFlags(&pl.cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
   }
   cudaStream_t st = pl.cap_stream;
-  const MapDesc& M = pl.hmaps[0];
-  const int nb = tile_blocks(pl);
   cudaGraph_t g = nullptr;
   if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
   cudaGraphConditionalHandle h;
@@ -180,9 +285,7 @@ static cudaError_t fcg_build(Plan& pl) {
     cudaGraphDestroy(g);
     return e;
   }
-  k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
-  e = dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st);
-  k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+  e = fcg_start(pl, kind, st);
   k_f_guard<<<1, 1, 0, st>>>(pl.dargs, 0);
   if (e == cudaSuccess) e = cudaGetLastError();
   cudaStreamCaptureStatus cs;
@@ -209,12 +312,7 @@ static cudaError_t fcg_build(Plan& pl) {
   if ((e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) ==
       cudaSuccess) {
     k_f_guard<<<1, 1, 0, st>>>(pl.dargs, 1);
-    k_f_a<<<nb, kThreads, 0, st>>>(pl.dargs);
-    k_f_b<<<nb, kThreads, 0, st>>>(pl.dargs);
-    k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
-    e = dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st);
-    k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
-    if (e == cudaSuccess) e = cudaGetLastError();
+    e = fcg_iteration(pl, kind, st);
     cudaGraph_t bout = nullptr;
     const cudaError_t e3 = cudaStreamEndCapture(st, &bout);
     if (e == cudaSuccess) e = e3;
@@ -222,50 +320,78 @@ static cudaError_t fcg_build(Plan& pl) {
   if (e == cudaSuccess) e = cudaGraphInstantiate(&pl.fcg_exec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) pl.fcg_exec = nullptr;
+  else {
+    pl.fcg_kind = kind;
+    if (kind == ULP_PRECOND_LEARNED) pl.fcg_gen = unet_ws_gen(*pl.unet);
+  }
   return e;
 }
 
 // Host-driven form of the same solve (options.profile = 2): every kernel is a
 // host launch, so a profiler sees each one; the host reads the stop flag after
 // every iteration.  For measurement only.
-static cudaError_t fcg_eager(Plan& pl, cudaStream_t st) {
+static cudaError_t fcg_eager(Plan& pl, int kind, cudaStream_t st) {
   const MapDesc& M = pl.hmaps[0];
   const int nb = tile_blocks(pl);
+  cudaError_t e = cudaSuccess;
+  phase_mark(pl, st, -1);
   k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
-  cudaError_t e = dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st);
+  phase_mark(pl, st, 2);
+  if (kind == ULP_PRECOND_DCT) e = dct_prepare_mask(*pl.dct, M.f.mask, M.pitch, st);
+  if (e == cudaSuccess) e = fcg_precond(pl, kind, st);
   if (e != cudaSuccess) return e;
+  phase_mark(pl, st, 3);
   k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+  phase_mark(pl, st, 4);
   for (long long l = 0;; ++l) {
     int done = 0;
     if ((e = cudaMemcpyAsync(&done, &pl.dstate->done, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     if (done || l > (1LL << 24)) break;
+    phase_mark(pl, st, -1);
     k_f_a<<<nb, kThreads, 0, st>>>(pl.dargs);
+    phase_mark(pl, st, 0);
     k_f_b<<<nb, kThreads, 0, st>>>(pl.dargs);
+    phase_mark(pl, st, 1);
     k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
-    if ((e = dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st)) != cudaSuccess) return e;
+    phase_mark(pl, st, 2);
+    if ((e = fcg_precond(pl, kind, st)) != cudaSuccess) return e;
+    phase_mark(pl, st, 3);
     k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
+    phase_mark(pl, st, 4);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_fcg(Plan& pl, const PcgArgs& a_in, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
-  if (!pl.dct || pl.nmaps != 1) return cudaErrorNotSupported;
+cudaError_t launch_fcg(Plan& pl, int kind, const PcgArgs& a_in, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+  if (pl.nmaps != 1) return cudaErrorNotSupported;
+  if (kind == ULP_PRECOND_DCT && !pl.dct) return cudaErrorNotSupported;
+  if (kind == ULP_PRECOND_LEARNED) {
+    if (!pl.unet) return cudaErrorNotSupported;
+    const MapDesc& M = pl.hmaps[0];
+    const int rc = unet_prepare(*pl.unet, 1, (M.H + 127) / 128 * 128, (M.W + 127) / 128 * 128);
+    if (rc) return rc == -5 ? cudaErrorMemoryAllocation : cudaErrorUnknown;
+  }
+  PcgArgs a = a_in;
+  a.rbf = nullptr;
+  a.rbf_ld = 0;
+  if (kind == ULP_PRECOND_DCT) a.rbf = dct_input(*pl.dct, &a.rbf_ld);
+  a.learned = kind == ULP_PRECOND_LEARNED;
   if (pl.opt.profile == 2) {
-    PcgArgs a = a_in;
     a.cond = 0;
     k_set_args<<<1, 1, 0, st>>>(a, pl.dargs);
     launch_pcg_reset(pl, st);
     if (e0) cudaEventRecord(e0, st);
-    const cudaError_t e = fcg_eager(pl, st);
+    const cudaError_t e = fcg_eager(pl, kind, st);
     if (e == cudaSuccess && e1) cudaEventRecord(e1, st);
     return e;
   }
+  if (pl.fcg_exec && (pl.fcg_kind != kind || (kind == ULP_PRECOND_LEARNED && pl.fcg_gen != unet_ws_gen(*pl.unet))))
+    destroy_fcg(pl);
   if (!pl.fcg_exec) {
-    const cudaError_t e = fcg_build(pl);
+    const cudaError_t e = fcg_build(pl, kind);
     if (e != cudaSuccess) return e;
   }
-  PcgArgs a = a_in;
   a.cond = pl.fcg_cond;
   pl.kernel_launches += 2;
   pl.solver_launches += 1;
@@ -282,6 +408,7 @@ cudaError_t launch_fcg(Plan& pl, const PcgArgs& a_in, cudaStream_t st, cudaEvent
 void destroy_fcg(Plan& pl) {
   if (pl.fcg_exec) cudaGraphExecDestroy(pl.fcg_exec);
   pl.fcg_exec = nullptr;
+  pl.fcg_kind = -1;
 }
 
 }  // namespace ulp

@@ -518,6 +518,10 @@ __global__ void k_pcg_reset(MapState* S, int nmaps, int* n_active, Barrier* bar)
     s->stop_after = 0;
     s->arrive = 0u;
     s->loops = 0;
+    s->fallback = 0;
+    s->restart = 0;
+    s->stall = 0;
+    s->rr_best = 0.0;
     if (act) atomicAdd(&s_cnt, 1);
   }
   __syncthreads();
@@ -580,6 +584,7 @@ __global__ void k_outer_error(const MapDesc* __restrict__ maps, MapState* S, Map
     st->outer_err[k] = err;
   }
   st->inner_total += s->iter;
+  st->fallbacks += s->fallback;
   int status = s->status;
   if (*(volatile int*)bar_err) status = -4;
   if (status < 0) st->status = status;
@@ -600,6 +605,7 @@ __global__ void k_begin(MapState* S, MapStats* stats, int nmaps) {
     st->status = 0;
     st->outer = 0;
     st->inner_total = 0;
+    st->fallbacks = 0;
     for (int k = 0; k < 64; ++k) { st->inner[k] = 0; st->relres[k] = 0.0; st->outer_err[k] = 0.0; }
     s->outer_k = 0;
     s->arrive_outer = 0u;

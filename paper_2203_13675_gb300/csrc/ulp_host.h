@@ -9,6 +9,7 @@
 namespace ulp {
 
 struct DctPlan;  // ulp_dct.cu
+struct Unet;     // ulp_unet.cu
 
 struct Plan {
   int device = 0;
@@ -34,6 +35,9 @@ struct Plan {
   PcgArgs* dargs = nullptr;  // solver arguments in device memory (read by the graph-driven solve)
   cudaGraphExec_t fcg_exec = nullptr;       // flexible-CG solve graph (DCT preconditioner)
   unsigned long long fcg_cond = 0;          // its WHILE-node handle
+  int fcg_kind = -1;                        // preconditioner the flexible-CG graph was built for
+  Unet* unet = nullptr;                     // learned preconditioner (not owned)
+  long long fcg_gen = 0;                    // its workspace generation captured in fcg_exec
   double *d_p = nullptr, *d_tau = nullptr;
   void* arena = nullptr;
   size_t arena_bytes = 0;
@@ -44,6 +48,11 @@ struct Plan {
   mutable long long solver_launches = 0;
   std::vector<cudaEvent_t> ev_pool;      // pairs (start, stop) recorded around solver launches
   size_t ev_used = 0;
+  // host-driven flexible CG (options.profile = 2): an event after every phase; ph_tag[k] is
+  // the phase (0 A, 1 B, 2 R, 3 M, 4 D) of the interval that ends at event k, -1 for a start
+  std::vector<cudaEvent_t> ph_pool;
+  std::vector<int> ph_tag;
+  size_t ph_used = 0;
   // captured call (options.graph): the executable graph, the arguments it was captured with
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -78,12 +87,32 @@ void launch_pcg_reset(const Plan& pl, cudaStream_t st);
 size_t dct_bytes(int H, int W);
 DctPlan* dct_create(int H, int W, void* mem);  // builds the matrices in mem (dct_bytes); null on failure
 void dct_destroy(DctPlan* d);
+unsigned* dct_input(const DctPlan& d, int* ld_pairs);
+// the mask's bit plane used by dct_apply(..., packed = true)
+cudaError_t dct_prepare_mask(const DctPlan& d, const uint8_t* mask, int pitch, cudaStream_t st);
+// packed: the BF16 copy of r (dct_input) and the mask bits (dct_prepare_mask) are
+// already written, skip those passes
 cudaError_t dct_apply(const DctPlan& d, const double* r, int pitch, const uint8_t* mask, double* s,
-                      cudaStream_t st);
+                      cudaStream_t st, bool packed = false);
 int dct_error(const DctPlan& d);  // 1 if a GEMM wait ran out since the last call (clears the flag)
 
 // ulp_fcg.cu
-cudaError_t launch_fcg(Plan& pl, const PcgArgs& a, cudaStream_t st, cudaEvent_t e0 = nullptr,
+// ulp_unet.cu: workspace for B images of Hn x Wn (multiples of 128); 0, -5 (no memory) or -2
+int unet_prepare(Unet& u, int B, int Hn, int Wn);
+// s = rho N(r / rho, U, V) on one map; every kernel returns at once while *skip != 0
+cudaError_t unet_apply_plane(Unet& u, const double* r, const double* U, const double* V, const uint8_t* mask, int H,
+                             int W, int pitch, double* s, const int* skip, cudaStream_t st);
+int unet_error(Unet& u);  // 1 if a tensor-core wait ran out since the last call (clears the flag)
+long long unet_ws_gen(const Unet& u);  // changes whenever the workspace is reallocated
+}  // namespace ulp
+ulp::Unet* ulp_unet_impl(ulp_unet net);  // the network behind a C handle
+namespace ulp {
+
+// ulp_api.cu: records the event that ends a phase interval of the host-driven flexible CG
+void phase_mark(Plan& pl, cudaStream_t st, int tag);
+
+// ulp_fcg.cu: the flexible-CG solve with the DCT (kind ULP_PRECOND_DCT) or learned preconditioner
+cudaError_t launch_fcg(Plan& pl, int kind, const PcgArgs& a, cudaStream_t st, cudaEvent_t e0 = nullptr,
                        cudaEvent_t e1 = nullptr);
 void destroy_fcg(Plan& pl);
 

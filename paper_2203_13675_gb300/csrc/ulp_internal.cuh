@@ -68,6 +68,12 @@ struct MapState {
   unsigned arrive, arrive_outer;
   double outer_err;
   long long loops;          // body executions of the graph-driven solve since its start
+  // learned preconditioner: switch to Jacobi after a stall or a breakdown
+  int fallback;             // 1: s = D^-1 r from now on in this solve
+  int restart;              // 1: the next beta is 0
+  int stall;                // iterations since rr last fell below 0.99 rr_best
+  int pad_;
+  double rr_best;
 };
 
 // Device-side record of one call (per map), copied to the host at the end.
@@ -77,6 +83,7 @@ struct MapStats {
   long long inner[64];
   double relres[64];
   double outer_err[64];
+  int fallbacks;
 };
 
 struct Barrier {
@@ -101,6 +108,10 @@ struct PcgArgs {
   double omega;
   int apply_only;           // sweep solvers: stop after the first s = M^-1 r (single-step entry point)
   unsigned long long cond;  // flexible-CG graph: WHILE-node handle cleared when the map stops (0 = none)
+  unsigned* rbf;            // flexible-CG graph: BF16 copy of r as column pairs (the DCT input), or null
+  int rbf_ld;               // its row stride in pairs
+  int learned;              // flexible CG with the learned preconditioner: stall / breakdown fall back to Jacobi
+  int stall_window;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -183,6 +194,44 @@ __device__ __forceinline__ double warp_sum_partials(const double* P, int n, int 
   if (k + 32 < n) a1 += __ldcg(P + k + 32);
   if (k + 64 < n) a2 += __ldcg(P + k + 64);
   return warp_sum((a0 + a1) + (a2 + a3));
+}
+
+// Fixed-order sums of n partials of up to three arrays at once (cnt = 1, 2, 3):
+// lane l adds P[l + 32 (8 j + u)] into accumulator u, the 8 cnt loads of a round
+// issued together, then a fixed tree over u and over the lanes.  Latency: one
+// L2 round trip per 256 partials instead of one per 128 partials and array.
+__device__ __forceinline__ void warp_sum_partials3(const double* P0, const double* P1, const double* P2, int cnt,
+                                                   int n, int lane, double& v0, double& v1, double& v2) {
+  double a0[8], a1[8], a2[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) a0[u] = a1[u] = a2[u] = 0.0;
+  int k = lane;
+  for (; k + 32 * 7 < n; k += 256) {
+    double t0[8], t1[8], t2[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      t0[u] = __ldcg(P0 + k + 32 * u);
+      t1[u] = cnt > 1 ? __ldcg(P1 + k + 32 * u) : 0.0;
+      t2[u] = cnt > 2 ? __ldcg(P2 + k + 32 * u) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      a0[u] += t0[u];
+      a1[u] += t1[u];
+      a2[u] += t2[u];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    if (k + 32 * u < n) {
+      a0[u] += __ldcg(P0 + k + 32 * u);
+      if (cnt > 1) a1[u] += __ldcg(P1 + k + 32 * u);
+      if (cnt > 2) a2[u] += __ldcg(P2 + k + 32 * u);
+    }
+  }
+  v0 = warp_sum(((a0[0] + a0[1]) + (a0[2] + a0[3])) + ((a0[4] + a0[5]) + (a0[6] + a0[7])));
+  v1 = cnt > 1 ? warp_sum(((a1[0] + a1[1]) + (a1[2] + a1[3])) + ((a1[4] + a1[5]) + (a1[6] + a1[7]))) : 0.0;
+  v2 = cnt > 2 ? warp_sum(((a2[0] + a2[1]) + (a2[2] + a2[3])) + ((a2[4] + a2[5]) + (a2[6] + a2[7]))) : 0.0;
 }
 
 __device__ __forceinline__ int find_map(const int* base, int nmaps, int t) {

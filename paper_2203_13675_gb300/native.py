@@ -14,7 +14,7 @@ import torch
 
 from . import build as _build
 
-PRECOND = {"identity": 0, "jacobi": 1, "ilu0": 2, "ic0": 3, "ssor": 4, "dct": 5}
+PRECOND = {"identity": 0, "jacobi": 1, "ilu0": 2, "ic0": 3, "ssor": 4, "dct": 5, "learned": 6}
 ULP_OK, ULP_WARN_MAXITER = 0, 1
 ULP_ERR_INVALID, ULP_ERR_CUDA, ULP_ERR_BREAKDOWN, ULP_ERR_TIMEOUT, ULP_ERR_NOMEM, ULP_ERR_UNSUPPORTED = \
     -1, -2, -3, -4, -5, -6
@@ -26,7 +26,10 @@ EXPORTED = ["ulp_options_default", "ulp_last_error", "unwrap_lp", "ulp_plan_crea
             "ulp_plan_create_batched", "ulp_plan_destroy", "ulp_unwrap", "ulp_unwrap_batched",
             "ulp_plan_last_status", "ulp_wrapped_diffs", "ulp_weights", "ulp_matvec",
             "ulp_precond_apply", "ulp_pcg", "ulp_plan_counters", "ulp_pcg_noalloc",
-            "ulp_autotune"]
+            "ulp_autotune", "ulp_unet_param_count", "ulp_unet_create", "ulp_unet_destroy",
+            "ulp_unet_set_params", "ulp_unet_get_params", "ulp_unet_save", "ulp_unet_load",
+            "ulp_unet_apply", "ulp_unet_forward", "ulp_unet_loss_grad", "ulp_unet_train_step",
+            "ulp_unet_harvest", "ulp_plan_set_unet"]
 
 
 class UlpError(RuntimeError):
@@ -40,24 +43,26 @@ class ulp_options(ctypes.Structure):
                 ("refresh", ctypes.c_longlong), ("omega", ctypes.c_double),
                 ("precision", ctypes.c_int), ("phi0_mode", ctypes.c_int),
                 ("tile_rows", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("spin_timeout_s", ctypes.c_double), ("profile", ctypes.c_int), ("graph", ctypes.c_int)]
+                ("spin_timeout_s", ctypes.c_double), ("profile", ctypes.c_int), ("graph", ctypes.c_int),
+                ("stall_window", ctypes.c_int)]
 
 
 class ulp_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("outer", ctypes.c_int), ("inner_total", ctypes.c_longlong),
                 ("inner", ctypes.c_longlong * 64), ("relres", ctypes.c_double * 64),
-                ("outer_err", ctypes.c_double * 64)]
+                ("outer_err", ctypes.c_double * 64), ("fallbacks", ctypes.c_int)]
 
     def as_dict(self):
         k = min(self.outer, 64)
         return {"status": self.status, "outer": self.outer, "inner_total": self.inner_total,
                 "inner": list(self.inner[:k]), "relres": list(self.relres[:k]),
-                "outer_err": list(self.outer_err[:k])}
+                "outer_err": list(self.outer_err[:k]), "fallbacks": self.fallbacks}
 
 
 class ulp_counters(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("solver_launches", ctypes.c_longlong),
-                ("solver_ms", ctypes.c_double), ("timed_launches", ctypes.c_longlong)]
+                ("solver_ms", ctypes.c_double), ("timed_launches", ctypes.c_longlong),
+                ("phase_ms", ctypes.c_double * 5), ("phase_launches", ctypes.c_longlong * 5)]
 
 
 class ulp_map(ctypes.Structure):
@@ -101,6 +106,22 @@ def load(path: str | None = None):
     L.ulp_pcg_noalloc.argtypes = [P, P, P, I, I, I, D, I, P, V, ctypes.POINTER(ulp_stats)]
     L.ulp_autotune.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ulp_map), I, I, I,
                                ctypes.c_char_p, ctypes.POINTER(ulp_options)]
+    LL = ctypes.c_ulonglong
+    L.ulp_unet_param_count.argtypes = []
+    L.ulp_unet_create.argtypes = [LL, ctypes.POINTER(V)]
+    L.ulp_unet_destroy.argtypes = [V]
+    L.ulp_unet_destroy.restype = None
+    L.ulp_unet_set_params.argtypes = [V, P]
+    L.ulp_unet_get_params.argtypes = [V, P]
+    L.ulp_unet_save.argtypes = [V, ctypes.c_char_p]
+    L.ulp_unet_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(V)]
+    L.ulp_unet_apply.argtypes = [V, P, P, P, P, I, I, P, V]
+    L.ulp_unet_forward.argtypes = [V, I, I, I, P, P, P, P, V]
+    L.ulp_unet_loss_grad.argtypes = [V, I, I, I, P, P, P, P, ctypes.POINTER(D), P, V]
+    L.ulp_unet_train_step.argtypes = [V, I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(I), I, I,
+                                      P, P, P, P, ctypes.c_float, ctypes.POINTER(D), V]
+    L.ulp_unet_harvest.argtypes = [P, P, P, I, I, I, D, I, ctypes.POINTER(I), P, P, V]
+    L.ulp_plan_set_unet.argtypes = [V, V]
     _lib = L
     return L
 
@@ -217,12 +238,21 @@ class Plan:
         _check(rc)
         return rc, ([s.as_dict() for s in st] if st is not None else None)
 
+    def set_unet(self, net):
+        """ulp_plan_set_unet(): the network used by precond="learned" (None detaches)."""
+        _check(load().ulp_plan_set_unet(self._h, net._h if net is not None else None))
+        self._unet = net  # keep it alive while the plan may use it
+
     def counters(self, reset=False):
-        """ulp_plan_counters(): kernel launches, solver launches and (profile=1) solver ms."""
+        """ulp_plan_counters(): kernel launches, solver launches, (profile=1) solver ms and
+        (profile=2, flexible CG) per-phase ms and counts keyed A, B, R, M, D."""
         c = ulp_counters()
         _check(load().ulp_plan_counters(self._h, int(bool(reset)), ctypes.byref(c)))
+        names = ("A", "B", "R", "M", "D")
         return {"kernel_launches": c.kernel_launches, "solver_launches": c.solver_launches,
-                "solver_ms": c.solver_ms, "timed_launches": c.timed_launches}
+                "solver_ms": c.solver_ms, "timed_launches": c.timed_launches,
+                "phase_ms": {n: c.phase_ms[k] for k, n in enumerate(names)},
+                "phase_launches": {n: c.phase_launches[k] for k, n in enumerate(names)}}
 
     def last_status(self):
         st = ulp_stats()
@@ -261,11 +291,12 @@ def ulp_wrapped_diffs(psi, stream=None):
     return dx, dy
 
 
-def ulp_weights(phi, dx, dy, mask=None, p=1.0, eps=1e-2, stream=None):
+def ulp_weights(phi, dx, dy, mask=None, p=1.0, eps=1e-2, stream=None, U=None, V=None, b=None):
+    """U, V, b: optional contiguous output tensors (views into larger buffers allowed)."""
     H, W = phi.shape
-    U = torch.empty_like(phi)
-    V = torch.empty_like(phi)
-    b = torch.empty_like(phi)
+    U = torch.empty_like(phi) if U is None else _dev(U)
+    V = torch.empty_like(phi) if V is None else _dev(V)
+    b = torch.empty_like(phi) if b is None else _dev(b)
     _check(load().ulp_weights(_ptr(_dev(phi)), _ptr(_dev(dx)), _ptr(_dev(dy)),
                               _ptr(mask), H, W, float(p), float(eps), _ptr(U), _ptr(V), _ptr(b),
                               _stream(stream)))
@@ -305,3 +336,97 @@ def ulp_pcg_noalloc(U, V, b, phi, precond="jacobi", tol=1e-6, max_inner=0, strea
                                 float(tol), int(max_inner), _ptr(_dev(phi)), _stream(stream), ctypes.byref(st))
     _check(rc)
     return phi, st.as_dict()
+
+
+# ---------------------------------------------------------------- learned preconditioner
+class Unet:
+    """Owns a ulp_unet (the learned preconditioner's parameters and workspace)."""
+
+    def __init__(self, seed=0, path=None):
+        L = load()
+        h = ctypes.c_void_p()
+        if path is not None:
+            _check(L.ulp_unet_load(os.fsencode(path), ctypes.byref(h)))
+        else:
+            _check(L.ulp_unet_create(int(seed), ctypes.byref(h)))
+        self._h = h
+
+    @staticmethod
+    def param_count() -> int:
+        return load().ulp_unet_param_count()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ulp_unet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        """params: host float32 array-like of param_count() values (canonical order)."""
+        t = torch.as_tensor(params, dtype=torch.float32).contiguous().cpu()
+        assert t.numel() == self.param_count()
+        _check(load().ulp_unet_set_params(self._h, ctypes.c_void_p(t.data_ptr())))
+
+    def get_params(self):
+        t = torch.empty(self.param_count(), dtype=torch.float32)
+        _check(load().ulp_unet_get_params(self._h, ctypes.c_void_p(t.data_ptr())))
+        return t
+
+    def save(self, path):
+        _check(load().ulp_unet_save(self._h, os.fsencode(path)))
+
+    def apply(self, r, U, V, mask=None, s=None, stream=None):
+        H, W = r.shape
+        if s is None:
+            s = torch.empty_like(r)
+        _check(load().ulp_unet_apply(self._h, _ptr(_dev(r)), _ptr(_dev(U)), _ptr(_dev(V)),
+                                     _ptr(mask) if mask is not None else None, H, W, _ptr(_dev(s)),
+                                     _stream(stream)))
+        return s
+
+    def forward(self, r, U, V, stream=None):
+        B, H, W = r.shape
+        y = torch.empty((B, H, W), dtype=torch.float32, device=r.device)
+        _check(load().ulp_unet_forward(self._h, B, H, W, _ptr(_dev(r)), _ptr(_dev(U)), _ptr(_dev(V)),
+                                       _ptr(y), _stream(stream)))
+        return y
+
+    def loss_grad(self, r, U, V, e, stream=None):
+        B, H, W = r.shape
+        g = torch.empty(self.param_count(), dtype=torch.float32, device=r.device)
+        loss = ctypes.c_double()
+        _check(load().ulp_unet_loss_grad(self._h, B, H, W, _ptr(_dev(r)), _ptr(_dev(U)), _ptr(_dev(V)),
+                                         _ptr(_dev(e)), ctypes.byref(loss), _ptr(g), _stream(stream)))
+        return loss.value, g
+
+    def train_step(self, pair_idx, sys_idx, r, e, U, V, lr=1e-3, stream=None):
+        """One Adam step on pairs r[pair_idx] -> e[pair_idx] with weights U[sys_idx], V[sys_idx]."""
+        _, H, W = r.shape
+        B = len(pair_idx)
+        pi = (ctypes.c_longlong * B)(*[int(x) for x in pair_idx])
+        si = (ctypes.c_int * B)(*[int(x) for x in sys_idx])
+        loss = ctypes.c_double()
+        _check(load().ulp_unet_train_step(self._h, B, pi, si, H, W, _ptr(_dev(r)), _ptr(_dev(e)),
+                                          _ptr(_dev(U)), _ptr(_dev(V)), float(lr), ctypes.byref(loss),
+                                          _stream(stream)))
+        return loss.value
+
+
+def ulp_unet_harvest(U, V, b, iters, precond="jacobi", tol_star=1e-10, r_out=None, e_out=None, stream=None):
+    """Training pairs (b - A phi_l, phi* - phi_l) for PCG iterates phi_l after iters[k] iterations."""
+    H, W = b.shape
+    n = len(iters)
+    if r_out is None:
+        r_out = torch.empty((n, H, W), dtype=torch.float64, device=b.device)
+    if e_out is None:
+        e_out = torch.empty((n, H, W), dtype=torch.float64, device=b.device)
+    it = (ctypes.c_int * n)(*[int(x) for x in iters])
+    _check(load().ulp_unet_harvest(_ptr(_dev(U)), _ptr(_dev(V)), _ptr(_dev(b)), H, W, _precond(precond),
+                                   float(tol_star), n, it, _ptr(_dev(r_out)), _ptr(_dev(e_out)),
+                                   _stream(stream)))
+    return r_out, e_out

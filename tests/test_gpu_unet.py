@@ -1,0 +1,239 @@
+"""Learned preconditioner (U-Net on tcgen05 implicit-GEMM convolutions, BF16
+activations, FP32 accumulation) against the FP64 oracle of oracle/unet.py.
+
+Parameters are rounded to BF16-representable values first, so the remaining
+difference is the BF16 rounding of the activations after every layer (2^-9
+relative each): the forward bar is 1e-2 relative in the 2-norm, the gradient
+bar 3e-2 per layer (the backward pass rounds the propagated gradients to BF16
+as well).  Training pairs are consistent (r = A e), as the harvested ones are.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import unet as ounet
+from paper_2203_13675_gb300 import native, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _cuda(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _bf16_exact(x):
+    return torch.from_numpy(np.asarray(x, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _params(seed):
+    rng = np.random.default_rng(seed)
+    p = {}
+    for name, ci, co in ounet.LAYERS:
+        p[name] = (rng.standard_normal((co, ci, 3, 3)) * np.sqrt(2.0 / (9 * ci)), rng.standard_normal(co) * 0.05)
+    p["head"] = (rng.standard_normal(16) * 0.3, 0.02)
+    theta = ounet.flatten(p)
+    # conv weights as the tensor cores see them; biases and head stay FP32
+    offs = 0
+    for name, ci, co in ounet.LAYERS:
+        n = co * ci * 9
+        theta[offs:offs + n] = _bf16_exact(theta[offs:offs + n])
+        offs += n + co
+    return np.asarray(theta, np.float32).astype(np.float64)
+
+
+def _inputs(B, H, W, seed):
+    rng = np.random.default_rng(seed)
+    r = np.stack([synth.smooth_map(H, W, seed + b).phi_true + 0.3 * rng.standard_normal((H, W)) for b in range(B)])
+    U = rng.uniform(0.05, 1.0, (B, H, W))
+    V = rng.uniform(0.05, 1.0, (B, H, W))
+    return r, U, V
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def test_param_count_matches_oracle():
+    assert native.Unet.param_count() == ounet.param_count()
+
+
+@pytest.mark.parametrize("B,H,W", [(1, 128, 128), (2, 128, 256), (1, 256, 128)])
+def test_forward_vs_oracle(B, H, W):
+    theta = _params(1)
+    net = native.Unet()
+    net.set_params(theta)
+    r, U, V = _inputs(B, H, W, 3)
+    y = net.forward(_cuda(r), _cuda(U), _cuda(V)).cpu().numpy().astype(np.float64)
+    x, _ = ounet.network_input(r, U, V)
+    ref, _ = ounet.forward(theta, x)
+    err = _rel(y, ref)
+    assert err < 1e-2, err
+
+
+@pytest.mark.parametrize("H,W,mask_frac", [(100, 150, 0.05), (128, 128, 0.0), (130, 64, 0.0)])
+def test_apply_vs_oracle(H, W, mask_frac):
+    theta = _params(2)
+    net = native.Unet()
+    net.set_params(theta)
+    m = synth.phase_map(H, W, 5, mask_frac=mask_frac)
+    r, U, V = _inputs(1, H, W, 7)
+    mask = m.mask
+    s = net.apply(_cuda(r[0]), _cuda(U[0]), _cuda(V[0]),
+                  mask=_cuda(mask, torch.uint8) if mask is not None else None).cpu().numpy()
+    ref = ounet.apply(theta, r[0], U[0], V[0], mask)
+    assert _rel(s, ref) < 1e-2
+    if mask is not None:
+        assert np.all(s[mask == 1] == 0.0)
+
+
+def test_identity_network_returns_jacobi_plus_r():
+    net = native.Unet()
+    net.set_params(ounet.identity_params())
+    r, U, V = _inputs(1, 96, 200, 11)
+    s = net.apply(_cuda(r[0]), _cuda(U[0]), _cuda(V[0])).cpu().numpy()
+    # exact up to the BF16 rounding of r / rho
+    ref = ounet.jacobi(U[0], V[0], r[0]) + r[0]
+    assert np.max(np.abs(s - ref)) <= 2.0 ** -8 * np.max(np.abs(r[0]))
+
+
+def _pairs(B, H, W, seed):
+    r, U, V = _inputs(B, H, W, seed)
+    U[..., :, -1] = 0.0
+    V[..., -1, :] = 0.0
+    e = np.stack([synth.smooth_map(H, W, seed + 40 + b).phi_true for b in range(B)])
+    e = e + 0.05 * np.random.default_rng(seed).standard_normal(e.shape)
+    return ounet.stencil(U, V, e), U, V, e
+
+
+def test_loss_and_gradient_vs_oracle():
+    theta = _params(4)
+    net = native.Unet()
+    net.set_params(theta)
+    r, U, V, e = _pairs(2, 128, 128, 13)
+    loss, g = net.loss_grad(_cuda(r), _cuda(U), _cuda(V), _cuda(e))
+    rloss, rg = ounet.loss_grad(theta, r, U, V, e)
+    assert abs(loss - rloss) <= 1e-2 * rloss, (loss, rloss)
+    g = g.cpu().numpy().astype(np.float64)
+    k = 0
+    for name, ci, co in ounet.LAYERS:
+        n = co * ci * 9
+        assert _rel(g[k:k + n], rg[k:k + n]) < 3e-2, (name, _rel(g[k:k + n], rg[k:k + n]))
+        assert _rel(g[k + n:k + n + co], rg[k + n:k + n + co]) < 3e-2, (name, "bias")
+        k += n + co
+    assert _rel(g[k:], rg[k:]) < 1e-2
+
+
+def test_train_step_reduces_loss_and_is_deterministic():
+    B = 4
+    r, U, V, e = _pairs(B, 128, 128, 17)
+    rc, ec, Uc, Vc = _cuda(r), _cuda(e), _cuda(U), _cuda(V)
+    losses = []
+    for rep in range(2):
+        net = native.Unet(seed=5)
+        ls = [net.train_step(range(B), range(B), rc, ec, Uc, Vc, lr=1e-3) for _ in range(30)]
+        losses.append(ls)
+        params = net.get_params().numpy()
+        if rep == 0:
+            first = params
+    assert losses[0] == losses[1], "training must be deterministic"
+    assert np.array_equal(first, params)
+    assert all(0.0 <= x <= 1.0 for x in losses[0])
+    assert np.mean(losses[0][-5:]) < np.mean(losses[0][:5]) - 0.01, losses[0][::5]
+
+
+def test_save_load_roundtrip():
+    net = native.Unet(seed=9)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "net.bin")
+        net.save(path)
+        net2 = native.Unet(path=path)
+        assert torch.equal(net.get_params(), net2.get_params())
+
+
+def test_harvest_pairs_satisfy_their_definition():
+    H, W = 128, 128
+    m = synth.phase_map(H, W, 8, noise=0.4)
+    dx, dy = oracle.wrapped_diffs(m.psi)
+    U, V = oracle.weights(np.zeros((H, W)), dx, dy, None, 0.5, 0.01)
+    A = oracle.assemble(U, V, dx, dy)
+    Uc, Vc, bc = _cuda(U), _cuda(V), _cuda(A.b)
+    iters = [0, 1, 5, 20]
+    r, e = native.ulp_unet_harvest(Uc, Vc, bc, iters, precond="jacobi", tol_star=1e-12)
+    r, e = r.cpu().numpy(), e.cpu().numpy()
+    # pair 0 is phi_l = 0: r = b, e = phi*
+    np.testing.assert_allclose(r[0], A.b, rtol=0, atol=1e-12)
+    for k in range(len(iters)):
+        # A e = A phi* - A phi_l = b - A phi_l = r, up to phi*'s own residual
+        Ae = A.matvec(e[k])
+        assert np.linalg.norm(Ae - r[k]) <= 1e-9 * np.linalg.norm(A.b), k
+    # more iterations, smaller error in the A-norm
+    anorm = [float(np.sum(e[k] * r[k])) for k in range(len(iters))]
+    assert all(a > b for a, b in zip(anorm, anorm[1:])), anorm
+
+
+def _rms(a, b, keep=None):
+    d = a - b
+    if keep is not None:
+        d = d[keep]
+    d = d - d.mean()
+    return float(np.sqrt(np.mean(d ** 2)))
+
+
+def test_fcg_with_zero_network_is_jacobi_pcg():
+    """Flexible CG whose network is zero applies exactly the Jacobi step: the
+    same solution and the same iteration counts (within 2) as the oracle's
+    Jacobi PCG."""
+    H, W = 128, 160
+    m = synth.phase_map(H, W, 21, ramp=0.02, n_bumps=12, noise=0.5, mask_frac=0.05, sigma_range=(5.0, 20.0))
+    net = native.Unet()
+    net.set_params(ounet.zero_params())
+    plan = native.Plan(H, W, outer_tol=0.0)
+    plan.set_unet(net)
+    mk = _cuda(m.mask, torch.uint8)
+    phi, st = plan.unwrap(_cuda(m.psi), mk, p=1.0, precond="learned", tol=1e-6, max_outer=3, max_inner=5000)
+    ref, rst = oracle.unwrap(m.psi, m.mask, p=1.0, kind=oracle.M_JACOBI, tol=1e-6, max_outer=3)
+    assert st["status"] == 0 and st["fallbacks"] == 0, st
+    assert _rms(phi.cpu().numpy(), ref, m.mask == 0) < 1e-4
+    for a, b in zip(st["inner"], rst["inner"]):
+        assert abs(a - b) <= 2, (st["inner"], rst["inner"])
+
+
+def test_bad_network_falls_back_to_jacobi():
+    """A correction of -1000 r makes s point away from r (r^T s < 0 at the
+    first iteration: every D^-1 on this map is far below 1000): each solve
+    must switch to Jacobi, converge, and report it."""
+    H, W = 128, 128
+    m = synth.phase_map(H, W, 22, noise=0.4)
+    theta = ounet.identity_params()
+    k = ounet.param_count() - 17
+    theta[k], theta[k + 1] = -1000.0, 1000.0  # head weights: y = -1000 x_r
+    net = native.Unet()
+    net.set_params(theta)
+    plan = native.Plan(H, W, outer_tol=0.0)
+    plan.set_unet(net)
+    phi, st = plan.unwrap(_cuda(m.psi), None, p=1.0, precond="learned", tol=1e-6, max_outer=2, max_inner=5000)
+    ref, rst = oracle.unwrap(m.psi, None, p=1.0, kind=oracle.M_JACOBI, tol=1e-6, max_outer=2)
+    assert st["status"] == 0, st
+    assert st["fallbacks"] == 2, st
+    assert _rms(phi.cpu().numpy(), ref) < 1e-4
+
+
+def test_trained_network_gains_over_jacobi():
+    """The network trained by the library's own kernels on pairs the plain
+    solver generated cuts the inner iterations of Algorithm 1 against the same
+    solve with the Jacobi preconditioner, on a map it was not trained on, and
+    reaches the same solution."""
+    from paper_2203_13675_gb300 import learned
+    data = learned.harvest(12, size=256, passes=(0, 2))
+    net = native.Unet(seed=1)
+    losses = learned.train(net, data, epochs=3, batch=8, lr=1e-3, seed=1)
+    assert np.mean(losses[-10:]) < 0.5 * np.mean(losses[:10]), (losses[:10], losses[-10:])
+    res = learned.evaluate(net, size=256, seed=5, max_outer=3, preconds=("jacobi", "learned"), reps=1)
+    jac, lrn = res["jacobi"], res["learned"]
+    assert jac["status"] == 0 and lrn["status"] == 0, res
+    assert lrn["inner_total"] < 0.5 * jac["inner_total"], res
+    assert lrn["rms_vs_first"] < 1e-4, res

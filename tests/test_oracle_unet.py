@@ -79,12 +79,16 @@ def test_identity_network_is_exact():
     r = rng.standard_normal((16, 24))
     U = rng.uniform(0, 1, (16, 24))
     V = rng.uniform(0, 1, (16, 24))
+    x, rho = unet.network_input(r, U, V)
+    y, _ = unet.forward(unet.identity_params(), x)
+    np.testing.assert_allclose(y[0] * rho[0], r, rtol=1e-14, atol=1e-14)
+    # the application adds the Jacobi step; masked pixels are zero
     s = unet.apply(unet.identity_params(), r, U, V)
-    np.testing.assert_allclose(s, r, rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(s, unet.jacobi(U, V, r) + r, rtol=1e-13, atol=1e-13)
     mask = np.zeros((16, 24), bool)
     mask[3:5, 7:9] = True
     s = unet.apply(unet.identity_params(), r, U, V, mask)
-    assert np.all(s[mask] == 0) and np.allclose(s[~mask], r[~mask])
+    assert np.all(s[mask] == 0)
 
 
 def test_zero_residual_gives_zero_input():
@@ -92,12 +96,63 @@ def test_zero_residual_gives_zero_input():
     assert rho[0] == 0 and np.all(x[..., 0] == 0) and np.all(x[..., 1] == 1)
 
 
-def test_target_normalisation():
-    rng = _rng(6)
-    e = rng.standard_normal((2, 8, 16)) * 5 + 3
-    t = unet.target(e)
-    np.testing.assert_allclose(t.mean(axis=(1, 2)), 0, atol=1e-14)
-    np.testing.assert_allclose(np.sqrt((t ** 2).mean(axis=(1, 2))), 1, rtol=1e-14)
+def test_zero_network_is_jacobi():
+    rng = _rng(15)
+    r = rng.standard_normal((20, 12))
+    U = rng.uniform(0, 1, (20, 12))
+    V = rng.uniform(0, 1, (20, 12))
+    np.testing.assert_allclose(unet.apply(unet.zero_params(), r, U, V), unet.jacobi(U, V, r), rtol=0, atol=0)
+
+
+def test_stencil_and_diag_match_the_csr_matrix():
+    """The U-Net oracle's matrix-free A is the main oracle's CSR A of Eq. (Axb)."""
+    import oracle
+    rng = _rng(16)
+    H, W = 7, 9
+    U = rng.uniform(0, 1, (H, W))
+    V = rng.uniform(0, 1, (H, W))
+    U[:, -1] = 0.0
+    V[-1, :] = 0.0
+    z = np.zeros((H, W))
+    A = oracle.assemble(U, V, z, z)
+    x = rng.standard_normal((H, W))
+    np.testing.assert_allclose(unet.stencil(U, V, x), A.matvec(x), rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(unet.diag(U, V).ravel(), np.diag(A.dense()), rtol=1e-14)
+
+
+def _consistent_pair(B, H, W, seed):
+    rng = _rng(seed)
+    U = rng.uniform(0.1, 1, (B, H, W))
+    V = rng.uniform(0.1, 1, (B, H, W))
+    U[..., :, -1] = 0.0
+    V[..., -1, :] = 0.0
+    e = rng.standard_normal((B, H, W))
+    r = unet.stencil(U, V, e)
+    return r, U, V, e
+
+
+def test_direction_loss_closed_forms():
+    r, U, V, e = _consistent_pair(2, 16, 16, 17)
+    x, rho = unet.network_input(r, U, V)
+    es = e / rho[:, None, None]
+    # s parallel to the error: one line search is exact, L = 0
+    y = 3.0 * es - unet.jacobi(U, V, x[..., 0])
+    L, _ = unet.direction_loss(x[..., 0], U, V, es, y)
+    np.testing.assert_allclose(L, 0.0, atol=1e-12)
+    # any direction: 0 <= L <= 1 (Cauchy-Schwarz in the A inner product)
+    rng = _rng(18)
+    for _ in range(5):
+        L, _ = unet.direction_loss(x[..., 0], U, V, es, rng.standard_normal(es.shape))
+        assert np.all(L >= -1e-12) and np.all(L <= 1 + 1e-12)
+    # a direction A-orthogonal to the error gives L = 1
+    s0 = rng.standard_normal(es.shape)
+    for b in range(2):
+        As0 = unet.stencil(U[b], V[b], s0[b])
+        s0[b] -= np.sum(s0[b] * x[b, ..., 0]) / np.sum(es[b] * x[b, ..., 0]) * es[b]
+        assert abs(np.sum(s0[b] * x[b, ..., 0])) < 1e-9 * np.linalg.norm(As0)
+    y = s0 - unet.jacobi(U, V, x[..., 0])
+    L, _ = unet.direction_loss(x[..., 0], U, V, es, y)
+    np.testing.assert_allclose(L, 1.0, atol=1e-9)
 
 
 def _random_theta(seed, scale=1.0):
@@ -114,12 +169,9 @@ def test_gradient_central_differences():
     """Every layer's weight and bias gradient against central differences of the loss."""
     rng = _rng(7)
     theta = _random_theta(8)
-    r = rng.standard_normal((2, 16, 16))
-    U = rng.uniform(0.1, 1, (2, 16, 16))
-    V = rng.uniform(0.1, 1, (2, 16, 16))
-    e = rng.standard_normal((2, 16, 16))
+    r, U, V, e = _consistent_pair(2, 16, 16, 19)
     loss, g = unet.loss_grad(theta, r, U, V, e)
-    assert loss > 0
+    assert 0 < loss < 1
     offsets, k = {}, 0
     for name, ci, co in unet.LAYERS:
         offsets[name] = (k, k + co * ci * 9)  # first weight, first bias
@@ -142,12 +194,8 @@ def test_gradient_central_differences():
 def test_gradient_planted_mistake_is_caught(monkeypatch):
     """A wrong bias gradient planted in the conv backward must fail the
     central-difference pin."""
-    rng = _rng(9)
     theta = _random_theta(10)
-    r = rng.standard_normal((1, 16, 16))
-    U = rng.uniform(0.1, 1, (1, 16, 16))
-    V = rng.uniform(0.1, 1, (1, 16, 16))
-    e = rng.standard_normal((1, 16, 16))
+    r, U, V, e = _consistent_pair(1, 16, 16, 20)
     k = sum(co * ci * 9 + co for _, ci, co in unet.LAYERS[:-1]) + 16 * 48 * 9  # first bias of d0
     h = 1e-6
     tp, tm = theta.copy(), theta.copy()

@@ -13,7 +13,9 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   weights                   -- special cases p = 0, 1, 2, hand-worked grids
   assemble                  -- Table 1 nnz, A1 = 0, sum b = 0, symmetry, edge-energy identity
   precond_apply             -- ILU(0) = IC(0), SSOR(1) = symmetric Gauss-Seidel,
-                               Jacobi closed form, DCT apply vs a dense Neumann Laplacian
+                               Jacobi closed form, DCT apply vs a dense Neumann Laplacian,
+                               multigrid: Galerkin coarse operator = P^T A P (dense),
+                               symmetric cycle, two-grid limit against a dense solve
   pcg                       -- dense direct solve (<= 16x16), closed-form DCT solve (p = 2),
                                one-iteration convergence with the DCT M at p = 2, finite termination
   unwrap                    -- exact recovery of noiseless phase, M-independence
@@ -37,6 +39,7 @@ _lock = threading.Lock()
 _lib = None
 
 M_IDENTITY, M_JACOBI, M_ILU0, M_IC0, M_SSOR, M_DCT = range(6)
+M_MG = 7
 STOP_RELRES, STOP_PAPER = 0, 1
 OK, MAXITER, INVALID, BREAKDOWN = 0, 1, -1, -3
 
@@ -101,6 +104,7 @@ def lib():
             L.orc_quality_q.argtypes = [_D, _D, ctypes.c_long]
             L.orc_functional.restype = ctypes.c_double
             L.orc_functional.argtypes = [_D, _D, _D, _U8, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+            L.orc_mg_coarsen.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, _D, _D]
             _lib = L
     return _lib
 
@@ -188,6 +192,16 @@ def assemble(U, V, dx, dy):
     nnz = lib().orc_assemble(_d(U), _d(V), _d(dx), _d(dy), H, W, indptr.ctypes.data_as(_L),
                              indices.ctypes.data_as(_I), _d(data), _d(b))
     return Csr(H, W, indptr, indices[:nnz].copy(), data[:nnz].copy(), b)
+
+
+def mg_coarsen(U, V):
+    """Galerkin 2x2-aggregation coarsening of the weighted 5-point Laplacian (multigrid M)."""
+    U, V = _f64(U), _f64(V)
+    H, W = U.shape
+    Uc = np.empty(((H + 1) // 2, (W + 1) // 2))
+    Vc = np.empty_like(Uc)
+    lib().orc_mg_coarsen(_d(U), _d(V), H, W, _d(Uc), _d(Vc))
+    return Uc, Vc
 
 
 def precond_apply(kind, A: Csr, r, omega=1.0, mask=None):

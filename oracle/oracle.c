@@ -144,6 +144,14 @@ typedef struct {
   double* lam;      /* DCT: eigenvalues, H x W */
   double* tmp;      /* DCT scratch, H x W */
   double* tmp2;
+  int mg_levels;    /* MG: number of grids, level 0 = the fine grid */
+  int mg_h[32], mg_w[32];
+  double* mg_u[32]; /* MG: edge weights and diagonal per level */
+  double* mg_v[32];
+  double* mg_d[32];
+  double* mg_x[32]; /* MG: work vectors per level (iterate, right-hand side, scratch) */
+  double* mg_b[32];
+  double* mg_t[32];
 } orc_precond;
 
 /* Position of column c in CSR row r, or -1 if (r,c) is not in the pattern. */
@@ -300,6 +308,145 @@ static void orc_dct_apply(const orc_precond* P, const double* r, double* s) {
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Multigrid (Sec. 1 names multigrid with the Fourier methods as the fast    */
+/* solvers of this system): one V-cycle of aggregation multigrid as a fixed  */
+/* SPD-in-practice M.  Grids: 2x2 aggregates, Galerkin coarse operators      */
+/* A_{l+1} = P^T A_l P (again 5-point weighted Laplacians, orc_mg_coarsen),   */
+/* down to at most ORC_MG_COARSE_MAX unknowns.  Smoother: damped Jacobi,      */
+/* weight ORC_MG_OMEGA, ORC_MG_NU sweeps before and after the coarse          */
+/* correction (the same count, so the cycle is symmetric); the correction is */
+/* scaled by ORC_MG_CC (over-correction for piecewise-constant P); the        */
+/* coarsest grid gets ORC_MG_COARSE_SWEEPS sweeps from zero.                  */
+/* ------------------------------------------------------------------------ */
+void orc_mg_coarsen(const double* U, const double* V, int H, int W, double* Uc, double* Vc) {
+  int Hc = (H + 1) / 2, Wc = (W + 1) / 2;
+  for (int I = 0; I < Hc; ++I)
+    for (int J = 0; J < Wc; ++J) {
+      double u = 0.0, v = 0.0;
+      /* edge between aggregates (I,J) and (I,J+1): the fine edges (i, 2J+1)-(i, 2J+2) */
+      if (2 * J + 2 < W)
+        for (int i = 2 * I; i <= 2 * I + 1 && i < H; ++i) u += U[(long)i * W + 2 * J + 1];
+      /* edge between aggregates (I,J) and (I+1,J): the fine edges (2I+1, j)-(2I+2, j) */
+      if (2 * I + 2 < H)
+        for (int j = 2 * J; j <= 2 * J + 1 && j < W; ++j) v += V[(long)(2 * I + 1) * W + j];
+      Uc[(long)I * Wc + J] = u;
+      Vc[(long)I * Wc + J] = v;
+    }
+}
+
+/* y = A x on a grid given by its edge weights (Eq. Axb's operator). */
+static void orc_grid_matvec(const double* U, const double* V, const double* D, int H, int W,
+                            const double* x, double* y) {
+  for (int i = 0; i < H; ++i)
+    for (int j = 0; j < W; ++j) {
+      long k = (long)i * W + j;
+      double acc = D[k] * x[k];
+      if (j + 1 < W) acc -= U[k] * x[k + 1];
+      if (j > 0) acc -= U[k - 1] * x[k - 1];
+      if (i + 1 < H) acc -= V[k] * x[k + W];
+      if (i > 0) acc -= V[k - W] * x[k - W];
+      y[k] = acc;
+    }
+}
+
+/* nu damped-Jacobi sweeps x <- x + omega D^-1 (b - A x) (D = 0: no update). */
+static void orc_mg_smooth(const orc_precond* P, int l, const double* b, double* x, int nu) {
+  int H = P->mg_h[l], W = P->mg_w[l];
+  long n = (long)H * W;
+  double* Ax = P->mg_t[l];
+  for (int s = 0; s < nu; ++s) {
+    orc_grid_matvec(P->mg_u[l], P->mg_v[l], P->mg_d[l], H, W, x, Ax);
+    for (long k = 0; k < n; ++k)
+      if (P->mg_d[l][k] > 0.0) x[k] += ORC_MG_OMEGA * (b[k] - Ax[k]) / P->mg_d[l][k];
+  }
+}
+
+/* x = V-cycle(l) applied to b (x starts at 0). */
+static void orc_mg_vcycle(const orc_precond* P, int l, const double* b, double* x) {
+  int H = P->mg_h[l], W = P->mg_w[l];
+  long n = (long)H * W;
+  for (long k = 0; k < n; ++k) x[k] = 0.0;
+  if (l == P->mg_levels - 1) {
+    orc_mg_smooth(P, l, b, x, ORC_MG_COARSE_SWEEPS);
+    return;
+  }
+  orc_mg_smooth(P, l, b, x, ORC_MG_NU);
+  /* restrict the residual: b_c = P^T (b - A x), the sum over each aggregate */
+  double* r = P->mg_t[l];
+  orc_grid_matvec(P->mg_u[l], P->mg_v[l], P->mg_d[l], H, W, x, r);
+  int Hc = P->mg_h[l + 1], Wc = P->mg_w[l + 1];
+  double* bc = P->mg_b[l + 1];
+  for (long k = 0; k < (long)Hc * Wc; ++k) bc[k] = 0.0;
+  for (int i = 0; i < H; ++i)
+    for (int j = 0; j < W; ++j) {
+      long k = (long)i * W + j;
+      bc[(long)(i / 2) * Wc + j / 2] += b[k] - r[k];
+    }
+  double* xc = P->mg_x[l + 1];
+  orc_mg_vcycle(P, l + 1, bc, xc);
+  /* prolong and correct: x += cc P x_c */
+  for (int i = 0; i < H; ++i)
+    for (int j = 0; j < W; ++j) x[(long)i * W + j] += ORC_MG_CC * xc[(long)(i / 2) * Wc + j / 2];
+  orc_mg_smooth(P, l, b, x, ORC_MG_NU);
+}
+
+static int orc_mg_setup(orc_precond* P) {
+  int H = P->H, W = P->W;
+  long n = (long)H * W;
+  /* level 0 weights from the CSR matrix: U_k = -A[k][k+1], V_k = -A[k][k+W] */
+  P->mg_levels = 1;
+  P->mg_h[0] = H;
+  P->mg_w[0] = W;
+  P->mg_u[0] = (double*)calloc(n, sizeof(double));
+  P->mg_v[0] = (double*)calloc(n, sizeof(double));
+  if (!P->mg_u[0] || !P->mg_v[0]) return ORC_INVALID;
+  for (int i = 0; i < H; ++i)
+    for (int j = 0; j < W; ++j) {
+      long k = (long)i * W + j;
+      long t;
+      if (j + 1 < W && (t = orc_find(P, (int)k, (int)(k + 1))) >= 0) P->mg_u[0][k] = -P->data[t];
+      if (i + 1 < H && (t = orc_find(P, (int)k, (int)(k + W))) >= 0) P->mg_v[0][k] = -P->data[t];
+    }
+  while ((long)P->mg_h[P->mg_levels - 1] * P->mg_w[P->mg_levels - 1] > ORC_MG_COARSE_MAX && P->mg_levels < 32) {
+    int l = P->mg_levels - 1;
+    int Hc = (P->mg_h[l] + 1) / 2, Wc = (P->mg_w[l] + 1) / 2;
+    P->mg_u[l + 1] = (double*)calloc((long)Hc * Wc, sizeof(double));
+    P->mg_v[l + 1] = (double*)calloc((long)Hc * Wc, sizeof(double));
+    if (!P->mg_u[l + 1] || !P->mg_v[l + 1]) return ORC_INVALID;
+    orc_mg_coarsen(P->mg_u[l], P->mg_v[l], P->mg_h[l], P->mg_w[l], P->mg_u[l + 1], P->mg_v[l + 1]);
+    P->mg_h[l + 1] = Hc;
+    P->mg_w[l + 1] = Wc;
+    P->mg_levels += 1;
+  }
+  for (int l = 0; l < P->mg_levels; ++l) {
+    int h = P->mg_h[l], w = P->mg_w[l];
+    long m = (long)h * w;
+    P->mg_d[l] = (double*)calloc(m, sizeof(double));
+    P->mg_x[l] = (double*)calloc(m, sizeof(double));
+    P->mg_b[l] = (double*)calloc(m, sizeof(double));
+    P->mg_t[l] = (double*)calloc(m, sizeof(double));
+    if (!P->mg_d[l] || !P->mg_x[l] || !P->mg_b[l] || !P->mg_t[l]) return ORC_INVALID;
+    /* the diagonal of the grid's Laplacian: the sum of its incident edge weights */
+    for (int i = 0; i < h; ++i)
+      for (int j = 0; j < w; ++j) {
+        long k = (long)i * w + j;
+        double d = P->mg_u[l][k] + P->mg_v[l][k];
+        if (j > 0) d += P->mg_u[l][k - 1];
+        if (i > 0) d += P->mg_v[l][k - w];
+        P->mg_d[l][k] = d;
+      }
+  }
+  return ORC_OK;
+}
+
+static void orc_mg_apply(const orc_precond* P, const double* r, double* s) {
+  orc_mg_vcycle(P, 0, r, s);
+  if (P->mask)
+    for (int k = 0; k < P->n; ++k)
+      if (P->mask[k]) s[k] = 0.0;
+}
+
 static int orc_precond_setup(orc_precond* P, int kind, int H, int W,
                              const long* indptr, const int* indices,
                              const double* data, double omega,
@@ -348,6 +495,8 @@ static int orc_precond_setup(orc_precond* P, int kind, int H, int W,
         for (int l = 0; l < W; ++l)
           P->lam[(long)k * W + l] = (2.0 - 2.0 * cos(ORC_PI * k / H)) + (2.0 - 2.0 * cos(ORC_PI * l / W));
       break;
+    case ORC_M_MG:
+      return orc_mg_setup(P);
     default:
       return ORC_INVALID;
   }
@@ -357,6 +506,10 @@ static int orc_precond_setup(orc_precond* P, int kind, int H, int W,
 static void orc_precond_free(orc_precond* P) {
   free(P->dpos); free(P->diag); free(P->fact);
   free(P->ch); free(P->cw); free(P->lam); free(P->tmp); free(P->tmp2);
+  for (int l = 0; l < P->mg_levels; ++l) {
+    free(P->mg_u[l]); free(P->mg_v[l]); free(P->mg_d[l]);
+    free(P->mg_x[l]); free(P->mg_b[l]); free(P->mg_t[l]);
+  }
 }
 
 static void orc_precond_solve(const orc_precond* P, const double* r, double* s) {
@@ -373,6 +526,7 @@ static void orc_precond_solve(const orc_precond* P, const double* r, double* s) 
     case ORC_M_IC0: orc_ic0_apply(P, r, s); break;
     case ORC_M_SSOR: orc_ssor_apply(P, r, s); break;
     case ORC_M_DCT: orc_dct_apply(P, r, s); break;
+    case ORC_M_MG: orc_mg_apply(P, r, s); break;
   }
 }
 

@@ -24,8 +24,24 @@ enum {
   ORC_M_ILU0 = 2,     /* ILU(0), item 3 */
   ORC_M_IC0 = 3,      /* IC(0), item 4 */
   ORC_M_SSOR = 4,     /* "SOR factorization", item 5, read as SSOR(omega) */
-  ORC_M_DCT = 5       /* unweighted Neumann-Poisson pseudo-inverse (Fourier basis, Sec. 1) */
+  ORC_M_DCT = 5,      /* unweighted Neumann-Poisson pseudo-inverse (Fourier basis, Sec. 1) */
+  ORC_M_MG = 7        /* one symmetric aggregation-multigrid V-cycle (multigrid, Sec. 1) */
 };
+
+/* Multigrid parameters (the method's definition, see orc_mg_*): damped-Jacobi
+ * weight, sweeps before and after the coarse correction, the coarse-correction
+ * scale, the sweeps on the coarsest grid and its size bound. */
+#define ORC_MG_OMEGA (2.0 / 3.0)
+#define ORC_MG_NU 2
+#define ORC_MG_CC 1.5
+#define ORC_MG_COARSE_SWEEPS 30
+#define ORC_MG_COARSE_MAX 16
+
+/* Galerkin coarsening of the 5-point weighted Laplacian by 2x2 aggregation:
+ * the coarse edge weights of P^T A P, P the piecewise-constant prolongation
+ * (aggregate (I,J) = fine rows 2I, 2I+1 and columns 2J, 2J+1, clipped at the
+ * border).  Uc, Vc are ((H+1)/2) x ((W+1)/2). */
+void orc_mg_coarsen(const double* U, const double* V, int H, int W, double* Uc, double* Vc);
 
 enum { ORC_STOP_RELRES = 0, ORC_STOP_PAPER = 1 };
 

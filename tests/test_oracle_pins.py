@@ -302,7 +302,7 @@ def _neumann_eigs(H, W):
     return (2 - 2 * np.cos(PI * k / H)) + (2 - 2 * np.cos(PI * l / W))
 
 
-@pytest.mark.parametrize("kind", [oracle.M_IDENTITY, oracle.M_JACOBI, oracle.M_ILU0])
+@pytest.mark.parametrize("kind", [oracle.M_IDENTITY, oracle.M_JACOBI, oracle.M_ILU0, oracle.M_MG])
 def test_p2_pcg_equals_closed_form_dct_solution(kind):
     # p = 2: U = V = tau / (1 + tau) everywhere, A = c L; the least-squares phase is
     # the Fourier/DCT Poisson solution (Ghiglia-Romero), here through scipy's DCT

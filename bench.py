@@ -46,8 +46,28 @@ UNIT = "Mpixel/s"
 # GEMM operands (about 8 B/px); the GEMMs do 8 H W (H + W) flop per application.
 ALG_BYTES = {("f64", "jacobi"): 112, ("f64", "identity"): 96, ("mixed", "jacobi"): 56, ("mixed", "identity"): 48,
              ("f64", "dct"): 146}
+ALG_BYTES[("f64", "learned")] = 146
+ALG_BYTES[("f64", "mg")] = 146
 KERNEL = {("f64", "jacobi"): "k_pcg64", ("f64", "identity"): "k_pcg64", ("mixed", "jacobi"): "k_pcg32",
-          ("mixed", "identity"): "k_pcg32", ("f64", "dct"): "flexible-CG graph (k_f_*, k_gemm_nt x4)"}
+          ("mixed", "identity"): "k_pcg32", ("f64", "dct"): "flexible-CG graph (k_f_*, k_gemm_nt x4)",
+          ("f64", "learned"): "flexible-CG graph (k_f_*, U-Net)",
+          ("f64", "mg"): "flexible-CG graph (k_f_*, multigrid V-cycle)"}
+# Multigrid V-cycle (FP32 grids) HBM bytes per pixel of the map: on the map's grid, r in FP64 to
+# the FP32 right-hand side (12), the fused pre-smoother reads b, D^-1, U, V and writes x (20), the
+# residual/restriction reads x, b, U, V (16 + 1), the first post-smoother reads x, b, U, V, D^-1 and
+# writes t (24 + 1 for the coarse x), the second reads t, b, U, V, D^-1 and writes s in FP64 (28):
+# 102 B/px; the coarser grids (FP32 throughout, 86 B per pixel of each) add a third of 86.
+MG_BYTES_PER_PX = 102.0 + 86.0 / 3.0
+# forms compared on each workload: the first is the plain form (the paper's method as written);
+# CHOSEN is the form the workload's configuration is about and that `value` reports
+FORMS = {"c5_2048": [("f64", "jacobi"), ("f64", "dct"), ("f64", "mg"), ("f64", "learned")],
+         "c3_4096": [("f64", "jacobi"), ("mixed", "jacobi"), ("f64", "mg")]}
+DEFAULT_FORMS = [("f64", "jacobi"), ("mixed", "jacobi"), ("f64", "dct"), ("f64", "mg")]
+CHOSEN = {"c5_2048": ("f64", "learned"), "c3_4096": ("mixed", "jacobi")}
+DEFAULT_CHOSEN = ("f64", "mg")
+ORACLE_KIND = {"jacobi": "jacobi", "identity": "identity", "mg": "mg", "dct": "dct", "learned": "jacobi"}
+# U-Net forward flop per pixel of the padded map: 2 x 9 x sum over layers of Cin Cout / 4^level
+UNET_FLOP_PER_PX = 18 * (16 * 16 + 16 * 32 / 4 + 32 * 64 / 16 + 64 * 128 / 64 + 192 * 64 / 16 + 96 * 32 / 4 + 48 * 16)
 DTYPE = {"f64": "f64", "mixed": "f32+f64"}
 
 # Flexible-CG phases (DCT / learned preconditioner), algorithmic HBM bytes per pixel per
@@ -175,8 +195,19 @@ def oracle_sample(wl_name, p, kind, gpu_iters, budget_s=20.0):
     from paper_2203_13675_gb300 import synth
     w = synth.WORKLOADS[wl_name]
     m = synth.workload_map(wl_name)
-    kinds = {"identity": oracle.M_IDENTITY, "jacobi": oracle.M_JACOBI}
+    kinds = {"identity": oracle.M_IDENTITY, "jacobi": oracle.M_JACOBI, "mg": oracle.M_MG, "dct": oracle.M_DCT}
     oracle.build()
+    H, W = m.psi.shape
+    if kind == "mg":
+        # the multigrid oracle finishes the whole call within the budget: time it, no extrapolation
+        t0 = time.perf_counter()
+        _, ost = oracle.unwrap(m.psi, m.mask, p=p, tau=w["tau"], kind=kinds[kind], tol=w["tol"],
+                               max_outer=w["max_outer"], outer_tol=0.0)
+        est = time.perf_counter() - t0
+        return {"value": H * W / est / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": (f"{wl_name} {H}x{W} p={p:g} {kind}: the whole oracle unwrap ({w['max_outer']} passes, "
+                           f"inner iterations {ost['inner']}), {est:.1f} s on one core, not extrapolated"),
+                "est_full_run_s": est}
     t0 = time.perf_counter()
     oracle.unwrap(m.psi, m.mask, p=p, tau=w["tau"], kind=kinds[kind], tol=w["tol"], max_outer=1, max_inner=2)
     t_small = time.perf_counter() - t0
@@ -202,7 +233,6 @@ def oracle_sample(wl_name, p, kind, gpu_iters, budget_s=20.0):
             iters = d[key]["stats"]["inner"]
             src = "oracle's own full run (tests/golden/oracle_runs.json)"
     est = len(iters) * setup + sum(iters) * per_it
-    H, W = m.psi.shape
     return {"value": H * W / est / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": (f"{wl_name} {H}x{W} p={p:g} {kind}: oracle unwrap, 1 outer pass capped at {n1} and "
                        f"{n2} PCG iterations ({t_small + t12 + t2:.1f} s CPU); full run extrapolated as "
@@ -266,17 +296,24 @@ def run_ours(args):
 
     # plain form: FP64 Jacobi PCG (the paper's method as written); chosen form: the
     # fastest of the forms below that reaches the same tolerance
-    forms = [("f64", "jacobi"), ("mixed", "jacobi"), ("f64", "dct")]
+    forms = FORMS.get(wl_name, DEFAULT_FORMS)
+    net, train_rep = None, None
+    if any(pc == "learned" for _, pc in forms):
+        net, train_rep = learned_net(native, args)
     res = {}
     plans = {}
+    sols = {}
     with ClockSampler(uuid) as clk:
         for prec, pc in forms:
             if prec not in plans:
                 plans[prec] = native.Plan(H, W, outer_tol=0.0, profile=1,
                                           precision=native.ULP_PRECISION_MIXED if prec == "mixed" else 0)
+                if net is not None and prec == "f64":
+                    plans[prec].set_unet(net)
             res[(prec, pc)] = run_form(plans[prec], psi, mask, phi, w, pc, args.steps, args.warmup, dist)
+            sols[(prec, pc)] = phi.cpu().numpy()
     ms_plain, st_plain, cnt_plain = res[("f64", "jacobi")]
-    chosen = min(res, key=lambda k: res[k][0])
+    chosen = CHOSEN.get(wl_name, DEFAULT_CHOSEN)
     ms, st, cnt = res[chosen]
     plan = plans[chosen[0]]
 
@@ -296,7 +333,7 @@ def run_ours(args):
                 "kernel": f"{KERNEL[chosen]}<{chosen[1]}> (persistent PCG)",
                 "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_px_iter": ALG_BYTES[chosen],
                 "solver_ms_per_step": cnt["solver_ms"] / args.steps}
-    if chosen[1] in ("dct", "learned"):
+    if chosen[1] in ("dct", "learned", "mg"):
         roofline = fcg_roofline(native, H, W, psi, mask, w, chosen[1], plan)
 
     # end to end: host (pinned) buffers in, host buffer out, inside the timed region
@@ -353,19 +390,61 @@ def run_ours(args):
                 "d2h_bytes_per_step": H * W * 8, "ms_per_step": ms_e2e},
         "forms": {f"{k[0]}_{k[1]}": {"value": px / (v[0] * 1e3), "ms_per_step": v[0],
                                      "inner_iterations": v[1]["inner"],
+                                     "fallbacks": v[1].get("fallbacks", 0),
+                                     "rms_vs_plain_rad": rms_diff(sols[k], sols[forms[0]], m.mask),
                                      "solver_ms_per_step": v[2]["solver_ms"] / args.steps}
                   for k, v in res.items()},
-        "gpu_launches": cnt["kernel_launches"],
+        "gpu_launches": gpu_launches(cnt, st, chosen, args.steps),
         "clocks": clk.summary(),
     }
+    if train_rep is not None:
+        line["config"]["learned_training"] = train_rep
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # the oracle's plain FP64 Jacobi PCG on one core (its DCT form applies explicit cosine
-        # matrices, O(N^1.5) per application: tens of seconds per iteration at 2048^2)
-        line["cpu_baseline"] = oracle_sample(wl_name, w["p"], "jacobi", st_plain["inner"])
+        # the oracle on one core, with the chosen form's preconditioner (FP64; the oracle has no
+        # mixed precision and no network: those configurations compare against its Jacobi PCG)
+        kind = ORACLE_KIND[chosen[1]]
+        line["cpu_baseline"] = oracle_sample(wl_name, w["p"], kind, st["inner"] if kind == chosen[1] else st_plain["inner"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def gpu_launches(cnt, st, chosen, steps):
+    """Kernels of the library that ran in the timed region: the host launches, plus, for a
+    flexible-CG form, the kernels its graph ran (start + inner iterations x body per pass)."""
+    n = cnt["kernel_launches"]
+    if chosen[1] in ("dct", "learned", "mg"):
+        n += steps * sum(cnt["graph_start_kernels"] + it * cnt["graph_body_kernels"] for it in st["inner"])
+    return n
+
+
+def rms_diff(a, b, mask):
+    """RMS of a - b after removing the mean, over unmasked pixels (solutions are defined up to a constant)."""
+    import numpy as np
+    d = a - b
+    if mask is not None:
+        d = d[mask == 0]
+    d = d - d.mean()
+    return float(np.sqrt(np.mean(d * d)))
+
+
+def learned_net(native, args):
+    """The learned preconditioner: loaded from --unet, else trained here by the
+    library's own kernels (harvest from plain PCG on 64 maps of 512^2, Adam)."""
+    if args.unet:
+        return native.Unet(path=args.unet), {"source": args.unet}
+    from paper_2203_13675_gb300 import learned
+    t0 = time.perf_counter()
+    data = learned.harvest(64, 512)
+    t1 = time.perf_counter()
+    net = native.Unet(seed=0)
+    losses = learned.train(net, data, epochs=6, batch=8, lr=1e-3, seed=0)
+    t2 = time.perf_counter()
+    del data
+    return net, {"source": "trained in this run", "pairs": 64 * 3 * len(learned.ITERS), "map_size": 512,
+                 "harvest_s": t1 - t0, "train_s": t2 - t1, "steps": len(losses),
+                 "loss_first": losses[0], "loss_last": sum(losses[-20:]) / 20}
 
 
 def fcg_roofline(native, H, W, psi, mask, w, precond, timed_plan):
@@ -391,7 +470,12 @@ def fcg_roofline(native, H, W, psi, mask, w, precond, timed_plan):
         if n == 0 or ms <= 0:
             continue
         mean_s = ms / n / 1e3
-        ent = {"ms_total": ms, "launches": n, "us_per_launch": mean_s * 1e6, "kernel": FCG_KERNEL[ph]}
+        kname = FCG_KERNEL[ph]
+        if ph == "M" and precond == "learned":
+            kname = "k_conv3x3 x7 + U-Net glue"
+        elif ph == "M" and precond == "mg":
+            kname = "k_mg_pre/res/post1/post2 per grid + k_mg_coarsest"
+        ent = {"ms_total": ms, "launches": n, "us_per_launch": mean_s * 1e6, "kernel": kname}
         if ph in FCG_BYTES:
             ent.update(bound="hbm", achieved=FCG_BYTES[ph] * H * W / mean_s / 1e9, unit="GB/s",
                        peak=peaks["hbm"][0], peak_source=peaks["hbm"][1] + " hbm_gbs",
@@ -401,6 +485,15 @@ def fcg_roofline(native, H, W, psi, mask, w, precond, timed_plan):
             ent.update(bound="tensor", achieved=fl / mean_s / 1e12, unit="TFLOP/s",
                        peak=peaks["bf16_sust"][0], peak_source=peaks["bf16_sust"][1],
                        alg_per_launch=f"4 Hp Wp (Hp + Wp) = {fl:.3g} flop")
+        elif ph == "M" and precond == "mg":
+            ent.update(bound="hbm", achieved=MG_BYTES_PER_PX * H * W / mean_s / 1e9, unit="GB/s",
+                       peak=peaks["hbm"][0], peak_source=peaks["hbm"][1] + " hbm_gbs",
+                       alg_per_launch=f"{MG_BYTES_PER_PX:.0f} B/px x {H}x{W} (V-cycle, all grids)")
+        elif ph == "M" and precond == "learned":
+            fl = UNET_FLOP_PER_PX * Hp * Wp
+            ent.update(bound="tensor", achieved=fl / mean_s / 1e12, unit="TFLOP/s",
+                       peak=peaks["bf16_sust"][0], peak_source=peaks["bf16_sust"][1],
+                       alg_per_launch=f"U-Net forward {UNET_FLOP_PER_PX:.0f} flop/px x {Hp}x{Wp} = {fl:.3g} flop")
         if "achieved" in ent:
             ent["frac"] = ent["achieved"] / ent["peak"] if ent["peak"] else None
         phases[ph] = ent
@@ -471,8 +564,10 @@ def run_reference(args):
     vals = []
     sample = None
     t_all = time.perf_counter()
+    chosen = CHOSEN.get(wl_name, DEFAULT_CHOSEN)
+    kind = ORACLE_KIND[chosen[1]]
     for s in range(args.warmup + args.steps):
-        r = oracle_sample(wl_name, w["p"], "jacobi", [w["max_outer"]] * 1, budget_s=8.0)
+        r = oracle_sample(wl_name, w["p"], kind, [w["max_outer"]] * 1, budget_s=8.0)
         if s >= args.warmup:
             vals.append(r)
             sample = r["sample"]
@@ -482,7 +577,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{wl_name}_p{w['p']:g}_jacobi", "H": H, "W": W, "precond": "jacobi"},
+            "config": {"workload": f"{wl_name}_p{w['p']:g}_{chosen[1]}", "H": H, "W": W, "precond": chosen[1],
+                       "oracle_precond": kind},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                              "host_cores_available": nproc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -498,6 +594,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2_2048")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--unet", default=None, help="parameter file of the learned preconditioner (c5_2048)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

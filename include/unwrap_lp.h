@@ -44,7 +44,10 @@ extern "C" {
 /* Preconditioner M of Algorithm 1 ("estimate preconditioning matrix M from A").
  * The first five are the paper's list (Sec. 2, items 1-5); DCT is the
  * unweighted Neumann-Poisson pseudo-inverse applied through cosine transforms;
- * LEARNED is a trained network (ulp_unet) applied as M^-1 inside flexible CG. */
+ * LEARNED is a trained network (ulp_unet) applied as M^-1 inside flexible CG;
+ * MG is a multigrid cycle (the paper names multigrid among the fast solvers of
+ * this system, Sec. 1).  DCT, LEARNED and MG run in flexible CG on single-map
+ * FP64 plans. */
 typedef enum {
   ULP_PRECOND_IDENTITY = 0, /* M = I: PCG becomes CG */
   ULP_PRECOND_JACOBI = 1,   /* M = diag(A) */
@@ -52,7 +55,9 @@ typedef enum {
   ULP_PRECOND_IC0 = 3,      /* incomplete Cholesky, no fill (same M as ILU0 for symmetric A) */
   ULP_PRECOND_SSOR = 4,     /* symmetric SOR, relaxation options.omega */
   ULP_PRECOND_DCT = 5,      /* s = L^+ r, L the unit-weight Neumann Laplacian */
-  ULP_PRECOND_LEARNED = 6   /* s = D^-1 r + rho N(r / rho, U, V), rho = rms(r); needs ulp_plan_set_unet */
+  ULP_PRECOND_LEARNED = 6,  /* s = D^-1 r + rho N(r / rho, U, V), rho = rms(r); needs ulp_plan_set_unet */
+  ULP_PRECOND_MG = 7        /* one symmetric V-cycle of aggregation multigrid: 2x2 aggregates, Galerkin
+                               coarse operators, 2 + 2 damped-Jacobi sweeps (omega 2/3), correction x 1.5 */
 } ulp_precond;
 
 typedef enum {
@@ -99,10 +104,11 @@ typedef struct ulp_options {
   int graph;              /* 1: ulp_unwrap / ulp_unwrap_batched capture their kernel sequence into a CUDA
                              graph on the first call and replay it while the arguments stay the same
                              (ignored when profile = 1) */
-  int stall_window;       /* ULP_PRECOND_LEARNED: an inner solve whose ||r||^2 has not dropped by 1% below
-                             its best value for this many iterations, or that meets r^T s <= 0 or
+  int stall_window;       /* ULP_PRECOND_LEARNED: an inner solve whose ||r|| has not halved within this many
+                             iterations (counted from the last time it did), or that meets r^T s <= 0 or
                              d^T A d <= 0, switches to the Jacobi preconditioner for the rest of that solve;
-                             default (0) 200 (plain CG's residual norm can plateau for tens of iterations) */
+                             default (0) 200 (plain CG and Jacobi PCG on 2^14..2^22-pixel maps halve ||r||
+                             every 40-450 iterations) */
 } ulp_options;
 
 /* Per-call statistics, written on the host when the call synchronises. */
@@ -204,6 +210,11 @@ typedef struct ulp_counters {
    * residual), [3] M (s = M^-1 r: the GEMM chain or the network), [4] D (r^T s, r^T r, stop test) */
   double phase_ms[5];
   long long phase_launches[5];
+  /* flexible-CG solves run as a graph whose WHILE body executes once per inner iteration:
+   * the kernels of its start and of one body (the body's kernels are not in kernel_launches;
+   * an outer pass with l inner iterations runs start + l x body of them) */
+  long long graph_start_kernels;
+  long long graph_body_kernels;
 } ulp_counters;
 ULP_API int ulp_plan_counters(ulp_plan plan, int reset, ulp_counters* out);
 

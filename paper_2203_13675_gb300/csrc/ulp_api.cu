@@ -63,6 +63,10 @@ static void destroy_plan(Plan& pl) {
   if (pl.dct_mem) cudaFree(pl.dct_mem);
   pl.dct = nullptr;
   pl.dct_mem = nullptr;
+  if (pl.mg) mg_destroy(pl.mg);
+  if (pl.mg_mem) cudaFree(pl.mg_mem);
+  pl.mg = nullptr;
+  pl.mg_mem = nullptr;
   if (pl.graph_exec) cudaGraphExecDestroy(pl.graph_exec);
   if (pl.cap_stream) cudaStreamDestroy(pl.cap_stream);
   pl.graph_exec = nullptr;
@@ -250,6 +254,13 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
     }
     pl.dct = dct_create(H[0], W[0], pl.dct_mem);
     if (!pl.dct) return fail(ULP_ERR_CUDA, "DCT preconditioner set-up failed");
+    e = cudaMalloc(&pl.mg_mem, mg_bytes(H[0], W[0]));
+    if (e != cudaSuccess) {
+      pl.mg_mem = nullptr;
+      cudaGetLastError();
+      return fail(ULP_ERR_NOMEM, "cudaMalloc(multigrid levels): %s", cudaGetErrorString(e));
+    }
+    pl.mg = mg_create(pl.hmaps[0], pl.mg_mem, pl.nsm);
   }
   ULP_CU(cudaDeviceSynchronize());  // workspace zeroed before any stream may use it
   return ULP_OK;
@@ -294,7 +305,7 @@ __global__ void k_set_pt(PT pt, double* p, double* tau, int first, int n) {
 }
 
 static int check_solver_args(int precond, double tol, int max_outer) {
-  if (precond < ULP_PRECOND_IDENTITY || precond > ULP_PRECOND_LEARNED)
+  if (precond < ULP_PRECOND_IDENTITY || precond > ULP_PRECOND_MG)
     return fail(ULP_ERR_INVALID, "unknown preconditioner %d", precond);
 
   if (!(tol > 0.0)) return fail(ULP_ERR_INVALID, "tol must be > 0");
@@ -383,7 +394,8 @@ static int enqueue_call(Plan& pl, const ulp_map* maps, int precond, double tol, 
     ULP_CU(launch_system(pl, pl.d_p, pl.d_tau, st));
     cudaEvent_t e0, e1;
     next_events(pl, &e0, &e1);
-    if (precond == ULP_PRECOND_DCT || precond == ULP_PRECOND_LEARNED) ULP_CU(launch_fcg(pl, precond, a, st, e0, e1));
+    if (precond == ULP_PRECOND_DCT || precond == ULP_PRECOND_LEARNED || precond == ULP_PRECOND_MG)
+      ULP_CU(launch_fcg(pl, precond, a, st, e0, e1));
     else if (mixed) ULP_CU(launch_pcg32(pl, precond, a, st, e0, e1));
     else ULP_CU(launch_pcg64(pl, precond, a, st, e0, e1));
     ULP_CU(launch_outer_error(pl, pl.opt.outer_tol, max_outer, st));
@@ -446,6 +458,8 @@ extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precon
     return fail(ULP_ERR_UNSUPPORTED, "mixed precision supports the identity and Jacobi preconditioners");
   if (precond == ULP_PRECOND_DCT && (pl.nmaps != 1 || !pl.dct))
     return fail(ULP_ERR_UNSUPPORTED, "the DCT preconditioner is available on single-map plans");
+  if (precond == ULP_PRECOND_MG && (pl.nmaps != 1 || !pl.mg))
+    return fail(ULP_ERR_UNSUPPORTED, "the multigrid preconditioner is available on single-map plans");
   if (precond == ULP_PRECOND_LEARNED && (pl.nmaps != 1 || !pl.unet))
     return fail(ULP_ERR_UNSUPPORTED, "the learned preconditioner needs a single-map plan and ulp_plan_set_unet");
   for (int m = 0; m < pl.nmaps; ++m) {
@@ -456,8 +470,10 @@ extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precon
   ULP_CU(cudaSetDevice(pl.device));
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   pl.last_stream = st;
-  // the DCT and learned solves are themselves graphs with a WHILE node, which cannot be nested: they run eagerly
-  if (pl.opt.graph && !pl.opt.profile && precond != ULP_PRECOND_DCT && precond != ULP_PRECOND_LEARNED)
+  // the DCT, learned and multigrid solves are themselves graphs with a WHILE node, which cannot be
+  // nested: they run eagerly
+  if (pl.opt.graph && !pl.opt.profile && precond != ULP_PRECOND_DCT && precond != ULP_PRECOND_LEARNED &&
+      precond != ULP_PRECOND_MG)
     rc = graph_call(pl, maps, precond, tol, max_outer, max_inner, st, mixed);
   else rc = enqueue_call(pl, maps, precond, tol, max_outer, max_inner, st, mixed);
   if (rc != ULP_OK) return rc;
@@ -493,6 +509,8 @@ extern "C" int ulp_plan_counters(ulp_plan plan, int reset, ulp_counters* out) {
     out->phase_ms[k] = 0.0;
     out->phase_launches[k] = 0;
   }
+  out->graph_start_kernels = pl.fcg_start_kernels;
+  out->graph_body_kernels = pl.fcg_body_kernels;
   for (size_t k = 1; k < pl.ph_used; ++k) {
     const int t = pl.ph_tag[k];
     if (t < 0 || t > 4) continue;
@@ -529,7 +547,10 @@ extern "C" int ulp_plan_last_status(ulp_plan plan, ulp_stats* stats) {
   if (!plan) return fail(ULP_ERR_INVALID, "null plan");
   Plan& pl = plan->p;
   ULP_CU(cudaSetDevice(pl.device));
-  return collect(pl, pl.last_stream, stats);
+  std::vector<ulp_stats> all(pl.nmaps);  // collect() writes one record per map; the caller gets the first
+  const int rc = collect(pl, pl.last_stream, all.data());
+  if (stats) *stats = all[0];
+  return rc;
 }
 
 static bool is_device_ptr(const void* p) {
@@ -685,6 +706,11 @@ extern "C" int ulp_precond_apply(int precond, const double* U, const double* V, 
   } else if (precond == ULP_PRECOND_IDENTITY || precond == ULP_PRECOND_JACOBI) {
     ULP_CU(launch_to_plane(pl, r, M.f.r, tp.st));
     ULP_CU(launch_jacobi_apply(pl, precond, M.f.r, M.f.s, tp.st));
+  } else if (precond == ULP_PRECOND_MG) {
+    ULP_CU(launch_to_plane(pl, r, M.f.r, tp.st));
+    if (mask) ULP_CU(launch_mask_to_plane(pl, mask, tp.st));
+    ULP_CU(mg_setup(*pl.mg, nullptr, tp.st));
+    ULP_CU(mg_apply(*pl.mg, mask ? M.f.mask : nullptr, nullptr, tp.st));
   } else if (precond == ULP_PRECOND_DCT) {
     ULP_CU(launch_to_plane(pl, r, M.f.r, tp.st));
     if (mask) ULP_CU(launch_mask_to_plane(pl, mask, tp.st));
@@ -719,7 +745,8 @@ extern "C" int ulp_pcg(const double* U, const double* V, const double* b, int H,
   ULP_CU(launch_to_plane(pl, b, M.f.b, tp.st));
   ULP_CU(launch_to_plane(pl, phi, M.f.phi, tp.st));
   if (precond == ULP_PRECOND_LEARNED) return fail(ULP_ERR_UNSUPPORTED, "ulp_pcg: the learned preconditioner needs a plan");
-  if (precond == ULP_PRECOND_DCT) ULP_CU(launch_fcg(pl, precond, pcg_args(pl, tol, max_inner), tp.st));
+  if (precond == ULP_PRECOND_DCT || precond == ULP_PRECOND_MG)
+    ULP_CU(launch_fcg(pl, precond, pcg_args(pl, tol, max_inner), tp.st));
   else ULP_CU(launch_pcg64(pl, precond, pcg_args(pl, tol, max_inner), tp.st, nullptr, nullptr));
   ULP_CU(launch_outer_error(pl, 0.0, 1, tp.st));
   ULP_CU(launch_from_plane(pl, M.f.phi, phi, tp.st));

@@ -182,7 +182,9 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
         S->restart = 0;
         S->iter += 1;
         if (a.learned && !S->fallback) {
-          if (v1 < 0.99 * S->rr_best) {
+          // progress test: ||r|| must halve (||r||^2 quarter) within every stall_window
+          // iterations, measured from the last point where it did
+          if (v1 < 0.25 * S->rr_best) {
             S->rr_best = v1;
             S->stall = 0;
           } else if (++S->stall >= a.stall_window || !(v0 > 0.0)) {
@@ -211,6 +213,8 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
       }
     }
     S->arrive = 0u;
+#pragma unroll 1
+    for (int g = 0; g < kArriveGroups; ++g) S->arrive_grp[g] = 0u;
     if (done) {
       S->done = 1;
       __threadfence();
@@ -223,22 +227,34 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
 }
 
 // Publishes this warp's tile partials and runs the map's finisher if this was
-// the last tile of the map in this phase.
+// the last tile of the map in this phase.  Arrival is counted in two levels so
+// that no counter takes more than about ntiles / 32 atomics: tile t counts into
+// group g = (t - tile_base) mod 32, and the last tile of each group counts into
+// the map's counter (thousands of warps finishing together on one address
+// otherwise serialise into a tail of tens of microseconds).  Fence before each
+// count, fence after observing the last one, as before.
 __device__ __forceinline__ void tile_arrive(const PcgArgs& a, const MapDesc& M, MapState* S, int t,
                                             int ph, double v0, double v1, double v2, int lane) {
   v0 = warp_sum(v0);
   if (ph != kPhA) v1 = warp_sum(v1);
   if (ph == kPhResInit) v2 = warp_sum(v2);
-  unsigned old = 0;
+  int last = 0;
   if (lane == 0) {
     __stcg(a.P0 + t, v0);
     if (ph != kPhA) __stcg(a.P1 + t, v1);
     if (ph == kPhResInit) __stcg(a.P2 + t, v2);  // kPhFcg: P2 holds r_{k+1}^T s_k from phase B
     __threadfence();
-    old = atomicAdd(&S->arrive, 1u);
+    const int n = M.ntiles;
+    const int ng = n < kArriveGroups ? n : kArriveGroups;
+    const int g = (t - M.tile_base) % kArriveGroups;
+    const unsigned gsize = (unsigned)((n - g + kArriveGroups - 1) / kArriveGroups);
+    if (atomicAdd(&S->arrive_grp[g], 1u) == gsize - 1u) {
+      __threadfence();
+      last = atomicAdd(&S->arrive, 1u) == (unsigned)ng - 1u;
+    }
   }
-  old = __shfl_sync(kFull, old, 0);
-  if (old == (unsigned)M.ntiles - 1u) {
+  last = __shfl_sync(kFull, last, 0);
+  if (last) {
     __threadfence();
     finish_map(a, M, S, ph, lane);
   }

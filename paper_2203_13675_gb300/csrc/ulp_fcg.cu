@@ -232,6 +232,7 @@ static int tile_blocks(const Plan& pl) { return (pl.ntiles + kWarps - 1) / kWarp
 static cudaError_t fcg_precond(Plan& pl, int kind, cudaStream_t st) {
   const MapDesc& M = pl.hmaps[0];
   if (kind == ULP_PRECOND_DCT) return dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st, true);
+  if (kind == ULP_PRECOND_MG) return mg_apply(*pl.mg, M.f.mask, pl.dstate, st);
   const cudaError_t e = unet_apply_plane(*pl.unet, M.f.r, M.f.U, M.f.V, M.f.mask, M.H, M.W, M.pitch, M.f.s,
                                          &pl.dstate[0].fallback, st);
   if (e != cudaSuccess) return e;
@@ -246,6 +247,7 @@ static cudaError_t fcg_start(Plan& pl, int kind, cudaStream_t st) {
   k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && kind == ULP_PRECOND_DCT) e = dct_prepare_mask(*pl.dct, M.f.mask, M.pitch, st);
+  if (e == cudaSuccess && kind == ULP_PRECOND_MG) e = mg_setup(*pl.mg, pl.dstate, st);
   if (e == cudaSuccess) e = fcg_precond(pl, kind, st);
   k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
   return e == cudaSuccess ? cudaGetLastError() : e;
@@ -317,6 +319,13 @@ static cudaError_t fcg_build(Plan& pl, int kind) {
     const cudaError_t e3 = cudaStreamEndCapture(st, &bout);
     if (e == cudaSuccess) e = e3;
   }
+  // kernel counts of the start and of one loop body (every captured node is a kernel,
+  // except the conditional node itself)
+  size_t n_all = 0, n_body = 0;
+  if (e == cudaSuccess) e = cudaGraphGetNodes(g, nullptr, &n_all);
+  if (e == cudaSuccess) e = cudaGraphGetNodes(body, nullptr, &n_body);
+  pl.fcg_start_kernels = (long long)n_all - 1;
+  pl.fcg_body_kernels = (long long)n_body;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&pl.fcg_exec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) pl.fcg_exec = nullptr;
@@ -338,6 +347,7 @@ static cudaError_t fcg_eager(Plan& pl, int kind, cudaStream_t st) {
   k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
   phase_mark(pl, st, 2);
   if (kind == ULP_PRECOND_DCT) e = dct_prepare_mask(*pl.dct, M.f.mask, M.pitch, st);
+  if (e == cudaSuccess && kind == ULP_PRECOND_MG) e = mg_setup(*pl.mg, pl.dstate, st);
   if (e == cudaSuccess) e = fcg_precond(pl, kind, st);
   if (e != cudaSuccess) return e;
   phase_mark(pl, st, 3);
@@ -366,6 +376,7 @@ static cudaError_t fcg_eager(Plan& pl, int kind, cudaStream_t st) {
 cudaError_t launch_fcg(Plan& pl, int kind, const PcgArgs& a_in, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
   if (pl.nmaps != 1) return cudaErrorNotSupported;
   if (kind == ULP_PRECOND_DCT && !pl.dct) return cudaErrorNotSupported;
+  if (kind == ULP_PRECOND_MG && !pl.mg) return cudaErrorNotSupported;
   if (kind == ULP_PRECOND_LEARNED) {
     if (!pl.unet) return cudaErrorNotSupported;
     const MapDesc& M = pl.hmaps[0];

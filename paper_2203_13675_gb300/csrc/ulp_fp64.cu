@@ -517,6 +517,7 @@ __global__ void k_pcg_reset(MapState* S, int nmaps, int* n_active, Barrier* bar)
     s->done = act ? 0 : 1;
     s->stop_after = 0;
     s->arrive = 0u;
+    for (int g = 0; g < kArriveGroups; ++g) s->arrive_grp[g] = 0u;
     s->loops = 0;
     s->fallback = 0;
     s->restart = 0;

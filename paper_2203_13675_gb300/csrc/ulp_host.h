@@ -10,6 +10,7 @@ namespace ulp {
 
 struct DctPlan;  // ulp_dct.cu
 struct Unet;     // ulp_unet.cu
+struct MgPlan;   // ulp_mg.cu
 
 struct Plan {
   int device = 0;
@@ -36,7 +37,11 @@ struct Plan {
   cudaGraphExec_t fcg_exec = nullptr;       // flexible-CG solve graph (DCT preconditioner)
   unsigned long long fcg_cond = 0;          // its WHILE-node handle
   int fcg_kind = -1;                        // preconditioner the flexible-CG graph was built for
+  long long fcg_start_kernels = 0;          // kernels of its start and of one WHILE-body execution
+  long long fcg_body_kernels = 0;
   Unet* unet = nullptr;                     // learned preconditioner (not owned)
+  MgPlan* mg = nullptr;                     // multigrid hierarchy (single-map plans)
+  void* mg_mem = nullptr;
   long long fcg_gen = 0;                    // its workspace generation captured in fcg_exec
   double *d_p = nullptr, *d_tau = nullptr;
   void* arena = nullptr;
@@ -97,6 +102,14 @@ cudaError_t dct_apply(const DctPlan& d, const double* r, int pitch, const uint8_
 int dct_error(const DctPlan& d);  // 1 if a GEMM wait ran out since the last call (clears the flag)
 
 // ulp_fcg.cu
+// ulp_mg.cu: aggregation multigrid on the map's planes (U, V, D^-1; r -> s, y as scratch)
+size_t mg_bytes(int H, int W);
+MgPlan* mg_create(const MapDesc& M, void* mem, int nsm);
+void mg_destroy(MgPlan* p);
+cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st);  // coarse grids, once per solve
+cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st);
+int mg_levels(const MgPlan& p);
+
 // ulp_unet.cu: workspace for B images of Hn x Wn (multiples of 128); 0, -5 (no memory) or -2
 int unet_prepare(Unet& u, int B, int Hn, int Wn);
 // s = rho N(r / rho, U, V) on one map; every kernel returns at once while *skip != 0
@@ -111,7 +124,7 @@ namespace ulp {
 // ulp_api.cu: records the event that ends a phase interval of the host-driven flexible CG
 void phase_mark(Plan& pl, cudaStream_t st, int tag);
 
-// ulp_fcg.cu: the flexible-CG solve with the DCT (kind ULP_PRECOND_DCT) or learned preconditioner
+// ulp_fcg.cu: the flexible-CG solve with the DCT, multigrid or learned preconditioner
 cudaError_t launch_fcg(Plan& pl, int kind, const PcgArgs& a, cudaStream_t st, cudaEvent_t e0 = nullptr,
                        cudaEvent_t e1 = nullptr);
 void destroy_fcg(Plan& pl);

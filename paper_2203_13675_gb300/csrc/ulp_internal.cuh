@@ -60,6 +60,8 @@ struct MapDesc {
 };
 
 // Mutable per-map solver state (device).
+constexpr int kArriveGroups = 32;
+
 struct MapState {
   double delta, delta0, rr, bb, dq, alpha, beta, relres;
   long long iter;
@@ -68,6 +70,7 @@ struct MapState {
   unsigned arrive, arrive_outer;
   double outer_err;
   long long loops;          // body executions of the graph-driven solve since its start
+  unsigned arrive_grp[kArriveGroups];  // two-level tile arrival: tile t counts into group (t - tile_base) % 32
   // learned preconditioner: switch to Jacobi after a stall or a breakdown
   int fallback;             // 1: s = D^-1 r from now on in this solve
   int restart;              // 1: the next beta is 0

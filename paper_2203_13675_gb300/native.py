@@ -14,7 +14,7 @@ import torch
 
 from . import build as _build
 
-PRECOND = {"identity": 0, "jacobi": 1, "ilu0": 2, "ic0": 3, "ssor": 4, "dct": 5, "learned": 6}
+PRECOND = {"identity": 0, "jacobi": 1, "ilu0": 2, "ic0": 3, "ssor": 4, "dct": 5, "learned": 6, "mg": 7}
 ULP_OK, ULP_WARN_MAXITER = 0, 1
 ULP_ERR_INVALID, ULP_ERR_CUDA, ULP_ERR_BREAKDOWN, ULP_ERR_TIMEOUT, ULP_ERR_NOMEM, ULP_ERR_UNSUPPORTED = \
     -1, -2, -3, -4, -5, -6
@@ -62,7 +62,8 @@ class ulp_stats(ctypes.Structure):
 class ulp_counters(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("solver_launches", ctypes.c_longlong),
                 ("solver_ms", ctypes.c_double), ("timed_launches", ctypes.c_longlong),
-                ("phase_ms", ctypes.c_double * 5), ("phase_launches", ctypes.c_longlong * 5)]
+                ("phase_ms", ctypes.c_double * 5), ("phase_launches", ctypes.c_longlong * 5),
+                ("graph_start_kernels", ctypes.c_longlong), ("graph_body_kernels", ctypes.c_longlong)]
 
 
 class ulp_map(ctypes.Structure):
@@ -252,9 +253,11 @@ class Plan:
         return {"kernel_launches": c.kernel_launches, "solver_launches": c.solver_launches,
                 "solver_ms": c.solver_ms, "timed_launches": c.timed_launches,
                 "phase_ms": {n: c.phase_ms[k] for k, n in enumerate(names)},
-                "phase_launches": {n: c.phase_launches[k] for k, n in enumerate(names)}}
+                "phase_launches": {n: c.phase_launches[k] for k, n in enumerate(names)},
+                "graph_start_kernels": c.graph_start_kernels, "graph_body_kernels": c.graph_body_kernels}
 
     def last_status(self):
+        """ulp_plan_last_status(): (worst status over the maps, stats of the first map)."""
         st = ulp_stats()
         rc = load().ulp_plan_last_status(self._h, ctypes.byref(st))
         return rc, st.as_dict()

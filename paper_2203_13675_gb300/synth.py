@@ -72,13 +72,18 @@ WORKLOADS = {
     # 4096x4096, ramp 0.02, 12 bumps, noise 0.7, p = 0.5 (mixed precision)
     "c3_4096": dict(H=4096, W=4096, seed=4, ramp=0.02, n_bumps=12, noise=0.7, mask_frac=0.0,
                     p=0.5, tau=1e-2, max_outer=5, tol=1e-6, precond="jacobi"),
+    # learned-preconditioner test map: the 256x256 generator at 2048x2048 (bump widths
+    # scaled by 8), p = 0.5; the network trains on the same generator at 512x512
+    "c5_2048": dict(H=2048, W=2048, seed=5, ramp=0.05, n_bumps=6, noise=0.3, mask_frac=0.0,
+                    p=0.5, tau=1e-2, max_outer=5, tol=1e-6, precond="jacobi", sigma_scale=8.0),
 }
 
 
 def workload_map(name: str) -> PhaseMap:
     w = WORKLOADS[name]
+    sc = w.get("sigma_scale", 1.0)
     return phase_map(w["H"], w["W"], w["seed"], ramp=w["ramp"], n_bumps=w["n_bumps"],
-                     noise=w["noise"], mask_frac=w["mask_frac"])
+                     noise=w["noise"], mask_frac=w["mask_frac"], sigma_range=(10.0 * sc, 40.0 * sc))
 
 
 def batch_specs(n: int = 64, seed0: int = 100):

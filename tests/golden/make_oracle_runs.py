@@ -23,7 +23,7 @@ import oracle  # noqa: E402
 from paper_2203_13675_gb300 import synth  # noqa: E402
 
 KINDS = {"identity": oracle.M_IDENTITY, "jacobi": oracle.M_JACOBI, "ilu0": oracle.M_ILU0,
-         "ic0": oracle.M_IC0, "ssor": oracle.M_SSOR, "dct": oracle.M_DCT}
+         "ic0": oracle.M_IC0, "ssor": oracle.M_SSOR, "dct": oracle.M_DCT, "mg": oracle.M_MG}
 
 
 def parse(name):

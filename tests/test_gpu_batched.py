@@ -84,3 +84,16 @@ def test_batched_graph_replay_matches_eager():
         rc, st = graph.unwrap_batched(b, precond="jacobi", tol=1e-6, max_outer=2)
         for x, y in zip(a, b):
             assert torch.equal(x["phi"], y["phi"])
+
+
+def test_last_status_of_a_batched_plan_is_the_first_map():
+    """ulp_plan_last_status writes one record (the first map's), never one per map."""
+    pm = _batch(seed0=900)
+    maps = [{"psi": _cuda(m.psi), "mask": _cuda(m.mask, torch.uint8) if m.mask is not None else None,
+             "phi": torch.empty(m.psi.shape, dtype=torch.float64, device="cuda"), "p": p} for m, p in pm]
+    plan = native.Plan(None, sizes=SIZES, outer_tol=0.0)
+    rc_all, per = plan.unwrap_batched(maps, precond="jacobi", tol=1e-6, max_outer=2, stats=True)
+    plan.unwrap_batched(maps, precond="jacobi", tol=1e-6, max_outer=2, stats=False)
+    for _ in range(3):
+        rc, st = plan.last_status()
+        assert rc == rc_all and st["inner"] == per[0]["inner"]

@@ -1,0 +1,77 @@
+"""Aggregation-multigrid preconditioner (one symmetric V-cycle, FP32 kernels)
+against the oracle's FP64 V-cycle, and the multigrid flexible CG (FP64
+vectors and scalars) against the oracle's multigrid PCG.
+
+One application matches to FP32 rounding: the cycle is about 10 grids of a
+few sweeps each, so the bar is 2e-5 relative in the 2-norm.  With a fixed M,
+flexible CG (Polak-Ribiere beta) and PCG (Fletcher-Reeves beta) are the same
+iteration in exact arithmetic; an M that differs from the oracle's by FP32
+rounding moves the stop point by at most a few iterations: counts within 3,
+solutions within the 1e-4 rad RMS bar.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2203_13675_gb300 import native, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _cuda(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+@pytest.mark.parametrize("H,W,mask_frac", [(128, 128, 0.0), (200, 129, 0.05), (7, 300, 0.0), (257, 63, 0.05),
+                                           (4, 4, 0.0), (2, 50, 0.0)])
+def test_mg_apply_vs_oracle(H, W, mask_frac):
+    m = synth.phase_map(H, W, 4, noise=0.6, mask_frac=mask_frac)
+    dx, dy = oracle.wrapped_diffs(m.psi)
+    U, V = oracle.weights(np.zeros((H, W)), dx, dy, m.mask, 1.0, 0.01)
+    A = oracle.assemble(U, V, dx, dy)
+    r = A.b + 0.1 * np.random.default_rng(1).standard_normal((H, W)) * (m.mask == 0 if m.mask is not None else 1)
+    ref = oracle.precond_apply(oracle.M_MG, A, r, mask=m.mask)
+    mk = _cuda(m.mask, torch.uint8) if m.mask is not None else None
+    got = native.ulp_precond_apply("mg", _cuda(U), _cuda(V), _cuda(r), mask=mk).cpu().numpy()
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < 2e-5, err
+    if m.mask is not None:
+        assert np.all(got[m.mask == 1] == 0.0)
+
+
+def _rms(a, b, keep=None):
+    e = a - b
+    if keep is not None:
+        e = e[keep]
+    e = e - e.mean()
+    return float(np.sqrt(np.mean(e ** 2)))
+
+
+@pytest.mark.parametrize("H,W,p,mask_frac", [(128, 128, 1.0, 0.05), (200, 129, 0.0, 0.05), (96, 256, 2.0, 0.0),
+                                             (256, 256, 0.5, 0.0)])
+def test_mg_fcg_unwrap_vs_oracle(H, W, p, mask_frac):
+    m = synth.phase_map(H, W, 21, ramp=0.02, n_bumps=12, noise=0.5, mask_frac=mask_frac,
+                        sigma_range=(5.0, 20.0))
+    plan = native.Plan(H, W, outer_tol=0.0)
+    mk = _cuda(m.mask, torch.uint8) if m.mask is not None else None
+    phi, st = plan.unwrap(_cuda(m.psi), mk, p=p, precond="mg", tol=1e-6, max_outer=3, max_inner=2000)
+    ref, rst = oracle.unwrap(m.psi, m.mask, p=p, kind=oracle.M_MG, tol=1e-6, max_outer=3)
+    keep = None if m.mask is None else (m.mask == 0)
+    assert st["status"] == 0, st
+    assert _rms(phi.cpu().numpy(), ref, keep) < 1e-4
+    for a, b in zip(st["inner"], rst["inner"]):
+        assert abs(a - b) <= 3, (st["inner"], rst["inner"])
+
+
+def test_mg_pcg_step_entry_point():
+    H, W = 160, 96
+    m = synth.phase_map(H, W, 9, noise=0.5)
+    dx, dy = oracle.wrapped_diffs(m.psi)
+    U, V = oracle.weights(np.zeros((H, W)), dx, dy, None, 1.0, 0.01)
+    A = oracle.assemble(U, V, dx, dy)
+    phi = torch.zeros((H, W), dtype=torch.float64, device="cuda")
+    _, st = native.ulp_pcg(_cuda(U), _cuda(V), _cuda(A.b), phi, precond="mg", tol=1e-8)
+    ref, rst = oracle.pcg(A, np.zeros((H, W)), kind=oracle.M_MG, tol=1e-8)
+    assert abs(st["inner"][0] - rst["iters"]) <= 3, (st, rst)
+    assert _rms(phi.cpu().numpy(), ref) < 1e-6

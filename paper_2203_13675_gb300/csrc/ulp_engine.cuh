@@ -143,10 +143,18 @@ enum Phase { kPhResInit = 0, kPhA = 1, kPhB = 2, kPhRes = 3, kPhFcg = 4 };
 // (alpha = delta_new / d^T q; delta_old, delta_new, beta; stop tests).
 __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, MapState* Sp, int ph, int lane) {
   volatile MapState* S = Sp;
-  const int base = M.tile_base, n = M.ntiles;
+  // the per-group sums in group order, then a fixed shuffle tree
+  const int n = M.ntiles;
+  const int ng = n < kArriveGroups ? n : kArriveGroups;
   const int cnt = (ph == kPhA) ? 1 : (ph == kPhResInit || ph == kPhFcg) ? 3 : 2;
-  double v0, v1, v2;
-  warp_sum_partials3(a.P0 + base, a.P1 + base, a.P2 + base, cnt, n, lane, v0, v1, v2);
+  const bool own = lane < ng;
+  // L2 loads: another warp wrote them, and this SM's L1 may hold an older phase's values
+  double v0 = own ? __ldcg(&Sp->gpart[0][lane]) : 0.0;
+  double v1 = (own && cnt > 1) ? __ldcg(&Sp->gpart[1][lane]) : 0.0;
+  double v2 = (own && cnt > 2) ? __ldcg(&Sp->gpart[2][lane]) : 0.0;
+  v0 = warp_sum(v0);
+  v1 = cnt > 1 ? warp_sum(v1) : 0.0;
+  v2 = cnt > 2 ? warp_sum(v2) : 0.0;
   if (lane == 0) {
     bool done = false;
     if (ph == kPhA) {
@@ -230,32 +238,64 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
 // the last tile of the map in this phase.  Arrival is counted in two levels so
 // that no counter takes more than about ntiles / 32 atomics: tile t counts into
 // group g = (t - tile_base) mod 32, and the last tile of each group counts into
-// the map's counter (thousands of warps finishing together on one address
-// otherwise serialise into a tail of tens of microseconds).  Fence before each
-// count, fence after observing the last one, as before.
+// the map's counter.  The counts are acquire-release atomics at GPU scope: the
+// release orders this warp's partial stores before its count, the acquire of
+// the group's last count (and of the map's) makes every earlier count's stores
+// visible to it, and __syncwarp passes that on to the finisher's other lanes.
+// The reduction is hierarchical for the same reason: the last tile of each
+// group sums that group's partials (the groups in parallel), and the finisher
+// reads only the 32 group sums; a single warp summing all 2432 tile partials
+// in fixed-order rounds of L2 loads took about 20 us per phase on GB300.
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 __device__ __forceinline__ void tile_arrive(const PcgArgs& a, const MapDesc& M, MapState* S, int t,
                                             int ph, double v0, double v1, double v2, int lane) {
   v0 = warp_sum(v0);
   if (ph != kPhA) v1 = warp_sum(v1);
   if (ph == kPhResInit) v2 = warp_sum(v2);
-  int last = 0;
+  const int base = M.tile_base, n = M.ntiles;
+  const int ng = n < kArriveGroups ? n : kArriveGroups;
+  const int g = (t - base) % kArriveGroups;
+  const int gsize = (n - g + kArriveGroups - 1) / kArriveGroups;
+  int glast = 0;
   if (lane == 0) {
     __stcg(a.P0 + t, v0);
     if (ph != kPhA) __stcg(a.P1 + t, v1);
     if (ph == kPhResInit) __stcg(a.P2 + t, v2);  // kPhFcg: P2 holds r_{k+1}^T s_k from phase B
-    __threadfence();
-    const int n = M.ntiles;
-    const int ng = n < kArriveGroups ? n : kArriveGroups;
-    const int g = (t - M.tile_base) % kArriveGroups;
-    const unsigned gsize = (unsigned)((n - g + kArriveGroups - 1) / kArriveGroups);
-    if (atomicAdd(&S->arrive_grp[g], 1u) == gsize - 1u) {
-      __threadfence();
-      last = atomicAdd(&S->arrive, 1u) == (unsigned)ng - 1u;
-    }
+    glast = atom_add_acq_rel(&S->arrive_grp[g], 1u) == (unsigned)gsize - 1u;
+  }
+  glast = __shfl_sync(kFull, glast, 0);
+  if (!glast) return;
+  // the group's last tile sums the group's partials (tiles base + g + 32 m, m in order of
+  // lanes then of the stride loop, then a fixed shuffle tree) in parallel with the other groups
+  __syncwarp();
+  const int cnt = (ph == kPhA) ? 1 : (ph == kPhResInit || ph == kPhFcg) ? 3 : 2;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll 4
+  for (int m = lane; m < gsize; m += 32) {
+    const int idx = base + g + kArriveGroups * m;
+    s0 += __ldcg(a.P0 + idx);
+    if (cnt > 1) s1 += __ldcg(a.P1 + idx);
+    if (cnt > 2) s2 += __ldcg(a.P2 + idx);
+  }
+  s0 = warp_sum(s0);
+  if (cnt > 1) s1 = warp_sum(s1);
+  if (cnt > 2) s2 = warp_sum(s2);
+  int last = 0;
+  if (lane == 0) {
+    volatile double* gp = &S->gpart[0][0];
+    gp[0 * kArriveGroups + g] = s0;
+    if (cnt > 1) gp[1 * kArriveGroups + g] = s1;
+    if (cnt > 2) gp[2 * kArriveGroups + g] = s2;
+    last = atom_add_acq_rel(&S->arrive, 1u) == (unsigned)ng - 1u;
   }
   last = __shfl_sync(kFull, last, 0);
   if (last) {
-    __threadfence();
+    __syncwarp();
     finish_map(a, M, S, ph, lane);
   }
 }

@@ -71,6 +71,7 @@ struct MapState {
   double outer_err;
   long long loops;          // body executions of the graph-driven solve since its start
   unsigned arrive_grp[kArriveGroups];  // two-level tile arrival: tile t counts into group (t - tile_base) % 32
+  double gpart[3][kArriveGroups];      // per-group sums of the tile partials, written by each group's last tile
   // learned preconditioner: switch to Jacobi after a stall or a breakdown
   int fallback;             // 1: s = D^-1 r from now on in this solve
   int restart;              // 1: the next beta is 0

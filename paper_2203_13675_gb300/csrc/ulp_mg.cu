@@ -201,6 +201,161 @@ __global__ void k_mg_coarsest(Grid g, const MapState* S) {
   }
 }
 
+
+// ---------------------------------------------------------------- vector kernels (wide grids)
+// A thread owns 4 consecutive pixels of a row (float4 accesses: on GB300 one
+// float per thread per load leaves too few bytes in flight to keep HBM busy), a
+// warp 128 columns of one row.  The column neighbours of a thread's pixels come
+// from the neighbouring lanes by shuffles (two scalar loads at the warp's ends),
+// the rows above and below as float4 loads.  Rows are padded to a multiple of 4
+// floats; values at columns >= W are taken as 0.  Same arithmetic per pixel as
+// the per-pixel kernels.
+enum { kSrcX1 = 0, kSrcXP = 1, kSrcT = 2, kSrcX = 3 };
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float f4(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+
+// the source vector at (i, j..j+3) of grid f (0 outside the grid)
+template <int SRC>
+__device__ __forceinline__ float4 src4(const Grid& f, const Grid& c, int i, int j) {
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (i < 0 || i >= f.H || j >= f.W) return v;
+  const size_t o = (size_t)i * f.ld + j;
+  if (SRC == kSrcX1) {
+    const float4 d = ld4(f.Dinv + o), b = ld4(f.b + o);
+    v = make_float4(kOmegaF * d.x * b.x, kOmegaF * d.y * b.y, kOmegaF * d.z * b.z, kOmegaF * d.w * b.w);
+  } else if (SRC == kSrcXP) {
+    const float4 x = ld4(f.x + o);
+    const float2 xc = *reinterpret_cast<const float2*>(c.x + (size_t)(i >> 1) * c.ld + (j >> 1));
+    v = make_float4(x.x + kCCF * xc.x, x.y + kCCF * xc.x, x.z + kCCF * xc.y, x.w + kCCF * xc.y);
+  } else if (SRC == kSrcT) {
+    v = ld4(f.t + o);
+  } else {
+    v = ld4(f.x + o);
+  }
+  if (j + 1 >= f.W) v.y = 0.f;
+  if (j + 2 >= f.W) v.z = 0.f;
+  if (j + 3 >= f.W) v.w = 0.f;
+  return v;
+}
+// one pixel of the source (halo of a warp's segment)
+template <int SRC>
+__device__ __forceinline__ float src1(const Grid& f, const Grid& c, int i, int j) {
+  if (i < 0 || i >= f.H || j < 0 || j >= f.W) return 0.f;
+  const size_t o = (size_t)i * f.ld + j;
+  if (SRC == kSrcX1) return kOmegaF * f.Dinv[o] * f.b[o];
+  if (SRC == kSrcXP) return f.x[o] + kCCF * c.x[(size_t)(i >> 1) * c.ld + (j >> 1)];
+  if (SRC == kSrcT) return f.t[o];
+  return f.x[o];
+}
+__device__ __forceinline__ float4 w4(const float* p, int i, int j, const Grid& f) {
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (i < 0 || i >= f.H || j >= f.W) return v;
+  v = ld4(p + (size_t)i * f.ld + j);
+  if (j + 1 >= f.W) v.y = 0.f;
+  if (j + 2 >= f.W) v.z = 0.f;
+  if (j + 3 >= f.W) v.w = 0.f;
+  return v;
+}
+
+// (A x) at the 4 pixels (i, j..j+3); xc, xn, xs the source at rows i, i-1, i+1
+template <int SRC>
+__device__ __forceinline__ float4 ax4(const Grid& f, const Grid& c, int i, int j, int lane, float4 xc, float4 xn,
+                                      float4 xs) {
+  const float4 U = w4(f.U, i, j, f), V = w4(f.V, i, j, f), Vn = w4(f.V, i - 1, j, f);
+  float ul = __shfl_up_sync(0xffffffffu, U.w, 1);
+  float xl = __shfl_up_sync(0xffffffffu, xc.w, 1);
+  float xr = __shfl_down_sync(0xffffffffu, xc.x, 1);
+  if (lane == 0) {
+    ul = (j > 0 && i < f.H && j - 1 < f.W) ? f.U[(size_t)i * f.ld + j - 1] : 0.f;
+    xl = src1<SRC>(f, c, i, j - 1);
+  }
+  if (lane == 31) xr = src1<SRC>(f, c, i, j + 4);
+  const float uw[4] = {ul, U.x, U.y, U.z};
+  const float ue[4] = {U.x, U.y, U.z, U.w};
+  const float xw[4] = {xl, xc.x, xc.y, xc.z};
+  const float xe[4] = {xc.y, xc.z, xc.w, xr};
+  float out[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float d = ue[k] + f4(V, k) + uw[k] + f4(Vn, k);
+    out[k] = d * f4(xc, k) - ue[k] * xe[k] - uw[k] * xw[k] - f4(V, k) * f4(xs, k) - f4(Vn, k) * f4(xn, k);
+  }
+  return make_float4(out[0], out[1], out[2], out[3]);
+}
+
+__device__ __forceinline__ bool warp_row(const Grid& f, int rows, int& i, int& j, int& lane) {
+  const int nseg = (f.W + 127) / 128;
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  lane = threadIdx.x & 31;
+  if (w >= rows * nseg) return false;
+  i = w / nseg;
+  j = (w % nseg) * 128 + 4 * lane;
+  return true;
+}
+
+// out = src + w D^-1 (b - A src) on row i (SRC x1: pre-smoothing, xp: first post-sweep, t: second)
+template <int SRC>
+__global__ void __launch_bounds__(256) k_mg_sweep_v(Grid f, Grid c, float* out, const uint8_t* mask, double* s,
+                                                    const MapState* S) {
+  if (skip_map(S)) return;
+  int i, j, lane;
+  if (!warp_row(f, f.H, i, j, lane)) return;
+  const float4 xc = src4<SRC>(f, c, i, j), xn = src4<SRC>(f, c, i - 1, j), xs = src4<SRC>(f, c, i + 1, j);
+  const float4 ax = ax4<SRC>(f, c, i, j, lane, xc, xn, xs);
+  if (j >= f.W) return;
+  const size_t o = (size_t)i * f.ld + j;
+  const float4 D = ld4(f.Dinv + o), b = ld4(f.b + o);
+  const float4 v = make_float4(xc.x + kOmegaF * D.x * (b.x - ax.x), xc.y + kOmegaF * D.y * (b.y - ax.y),
+                               xc.z + kOmegaF * D.z * (b.z - ax.z), xc.w + kOmegaF * D.w * (b.w - ax.w));
+  if (s) {
+    // the map's grid: s in FP64, 0 on masked pixels and nothing beyond column W - 1
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (j + k < f.W) s[o + k] = (mask && mask[o + k]) ? 0.0 : (double)f4(v, k);
+  } else {
+    *reinterpret_cast<float4*>(out + o) = v;
+  }
+}
+
+// residual and restriction: rows 2I, 2I+1 of a thread's 4 columns -> b_c(I, j/2), b_c(I, j/2 + 1)
+__global__ void __launch_bounds__(256) k_mg_res_v(Grid f, Grid c, const MapState* S) {
+  if (skip_map(S)) return;
+  int I, j, lane;
+  if (!warp_row(f, c.H, I, j, lane)) return;
+  const int i = 2 * I;
+  const float4 x0 = src4<kSrcX>(f, c, i - 1, j), x1 = src4<kSrcX>(f, c, i, j), x2 = src4<kSrcX>(f, c, i + 1, j),
+               x3 = src4<kSrcX>(f, c, i + 2, j);
+  const float4 a1 = ax4<kSrcX>(f, c, i, j, lane, x1, x0, x2);
+  const float4 a2 = ax4<kSrcX>(f, c, i + 1, j, lane, x2, x1, x3);
+  if (j >= f.W) return;
+  const float4 b1 = w4(f.b, i, j, f), b2 = w4(f.b, i + 1, j, f);
+  const bool r2 = i + 1 < f.H;
+  float lo = (b1.x - a1.x) + (b1.y - a1.y), hi = (b1.z - a1.z) + (b1.w - a1.w);
+  if (r2) {
+    lo += (b2.x - a2.x) + (b2.y - a2.y);
+    hi += (b2.z - a2.z) + (b2.w - a2.w);
+  }
+  // columns beyond W - 1 contribute 0: their b is 0 and A x there is 0 (zero weights, zero x)
+  *reinterpret_cast<float2*>(c.b + (size_t)I * c.ld + (j >> 1)) = make_float2(lo, hi);
+}
+
+// level 0: b = (float) r, four pixels per thread
+__global__ void k_mg_rhs_v(const double* __restrict__ r, Grid g, const MapState* S) {
+  if (skip_map(S)) return;
+  const int nq = (g.W + 3) / 4;
+  MG_LOOP(t, (long long)g.H * nq) {
+    const int i = (int)(t / nq), j = (int)(t % nq) * 4;
+    const size_t o = (size_t)i * g.ld + j;
+    float4 v;
+    v.x = (float)r[o];
+    v.y = j + 1 < g.W ? (float)r[o + 1] : 0.f;
+    v.z = j + 2 < g.W ? (float)r[o + 2] : 0.f;
+    v.w = j + 3 < g.W ? (float)r[o + 3] : 0.f;
+    *reinterpret_cast<float4*>(g.b + o) = v;
+  }
+}
+
 // The grids from index lt down (each at most kTailMax unknowns, together at
 // most kTailPx) in one block, in shared memory: U, V, D^-1 copied in, the
 // right-hand side of grid lt read from global memory, the whole rest of the
@@ -244,16 +399,36 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(TailGrids tg, const Ma
   float* sx = sD + tot;
   float* sb = sx + tot;
   float* st = sb + tot;
-  // load weights of every tail grid and the right-hand side of the first
-  for (int l = 0; l < tg.n; ++l) {
-    const Grid& g = tg.g[l];
-    const int n = g.H * g.W;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      const size_t o = (size_t)(k / g.W) * g.ld + k % g.W;
-      sU[tg.off[l] + k] = g.U[o];
-      sV[tg.off[l] + k] = g.V[o];
-      sD[tg.off[l] + k] = g.Dinv[o];
-      if (l == 0) sb[k] = g.b[o];
+  // load weights of every tail grid and the right-hand side of the first, all loads of
+  // a thread in flight together (the shared arrays are contiguous over the grids)
+  {
+    constexpr int kq = (kTailPx + kTailThreads - 1) / kTailThreads;
+    float ru[kq], rv[kq], rd[kq], rb[kq];
+#pragma unroll
+    for (int q = 0; q < kq; ++q) {
+      const int k = threadIdx.x + kTailThreads * q;
+      ru[q] = rv[q] = rd[q] = rb[q] = 0.f;
+      if (k < tot) {
+        int l = 0;
+        while (l + 1 < tg.n && k >= tg.off[l + 1]) ++l;
+        const Grid& g = tg.g[l];
+        const int e = k - tg.off[l];
+        const size_t o = (size_t)(e / g.W) * g.ld + e % g.W;
+        ru[q] = g.U[o];
+        rv[q] = g.V[o];
+        rd[q] = g.Dinv[o];
+        if (l == 0) rb[q] = g.b[o];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kq; ++q) {
+      const int k = threadIdx.x + kTailThreads * q;
+      if (k < tot) {
+        sU[k] = ru[q];
+        sV[k] = rv[q];
+        sD[k] = rd[q];
+        if (k < tg.g[0].H * tg.g[0].W) sb[k] = rb[q];
+      }
     }
   }
   __syncthreads();
@@ -356,7 +531,7 @@ size_t mg_bytes(int H, int W) {
   while ((long long)h * w > kCoarseMax) {
     h = (h + 1) / 2;
     w = (w + 1) / 2;
-    bytes += 6 * fbytes((size_t)h * w);
+    bytes += 6 * fbytes((size_t)h * ((w + 3) / 4 * 4));
   }
   return bytes + 256;
 }
@@ -393,8 +568,8 @@ MgPlan* mg_create(const MapDesc& M, void* mem, int nsm) {
     Grid c{};
     c.H = (f.H + 1) / 2;
     c.W = (f.W + 1) / 2;
-    c.ld = c.W;
-    const size_t n = (size_t)c.H * c.W;
+    c.ld = (c.W + 3) / 4 * 4;
+    const size_t n = (size_t)c.H * c.ld;
     c.U = take(n);
     c.V = take(n);
     c.Dinv = take(n);
@@ -428,6 +603,13 @@ MgPlan* mg_create(const MapDesc& M, void* mem, int nsm) {
 
 void mg_destroy(MgPlan* p) { delete p; }
 
+constexpr int kVecMinW = 64;  // grids at least this wide use the vector kernels
+
+static unsigned row_blocks(const Grid& f, int rows) {
+  const long long warps = (long long)rows * ((f.W + 127) / 128);
+  return (unsigned)((warps + 7) / 8);
+}
+
 static int mg_blocks(const MgPlan& p, long long n) {
   const long long b = (n + 255) / 256;
   const long long cap = 8LL * p.nsm;
@@ -449,7 +631,7 @@ cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st) {
 cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st) {
   const int L = (int)p.g.size();
   const Grid& g0 = p.g[0];
-  k_mg_rhs<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(p.r0, g0, S);
+  k_mg_rhs_v<<<mg_blocks(p, (long long)g0.H * ((g0.W + 3) / 4)), 256, 0, st>>>(p.r0, g0, S);
   if (L == 1) {
     k_mg_coarsest<<<1, 256, 0, st>>>(g0, S);
     k_mg_post2<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(g0, mask, p.s0, S);
@@ -458,8 +640,13 @@ cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cu
   const int stop = p.lt > 0 ? p.lt : L - 1;  // grids [0, stop) by per-grid kernels
   for (int l = 0; l < stop; ++l) {
     const Grid& f = p.g[l];
-    k_mg_pre<<<mg_blocks(p, (long long)f.H * f.W), 256, 0, st>>>(f, S);
-    k_mg_res<<<mg_blocks(p, (long long)p.g[l + 1].H * p.g[l + 1].W), 256, 0, st>>>(f, p.g[l + 1], S);
+    if (f.W >= kVecMinW) {
+      k_mg_sweep_v<kSrcX1><<<row_blocks(f, f.H), 256, 0, st>>>(f, Grid{}, f.x, nullptr, nullptr, S);
+      k_mg_res_v<<<row_blocks(f, p.g[l + 1].H), 256, 0, st>>>(f, p.g[l + 1], S);
+    } else {
+      k_mg_pre<<<mg_blocks(p, (long long)f.H * f.W), 256, 0, st>>>(f, S);
+      k_mg_res<<<mg_blocks(p, (long long)p.g[l + 1].H * p.g[l + 1].W), 256, 0, st>>>(f, p.g[l + 1], S);
+    }
   }
   if (p.lt > 0) {
     static bool attr = false;
@@ -475,9 +662,15 @@ cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cu
   }
   for (int l = stop - 1; l >= 0; --l) {
     const Grid& f = p.g[l];
-    k_mg_post1<<<mg_blocks(p, (long long)f.H * f.W), 256, 0, st>>>(f, p.g[l + 1], S);
-    k_mg_post2<<<mg_blocks(p, (long long)f.H * f.W), 256, 0, st>>>(f, l == 0 ? mask : nullptr,
-                                                                  l == 0 ? p.s0 : nullptr, S);
+    if (f.W >= kVecMinW) {
+      k_mg_sweep_v<kSrcXP><<<row_blocks(f, f.H), 256, 0, st>>>(f, p.g[l + 1], f.t, nullptr, nullptr, S);
+      k_mg_sweep_v<kSrcT><<<row_blocks(f, f.H), 256, 0, st>>>(f, Grid{}, f.x, l == 0 ? mask : nullptr,
+                                                               l == 0 ? p.s0 : nullptr, S);
+    } else {
+      k_mg_post1<<<mg_blocks(p, (long long)f.H * f.W), 256, 0, st>>>(f, p.g[l + 1], S);
+      k_mg_post2<<<mg_blocks(p, (long long)f.H * f.W), 256, 0, st>>>(f, l == 0 ? mask : nullptr,
+                                                                    l == 0 ? p.s0 : nullptr, S);
+    }
   }
   return cudaGetLastError();
 }

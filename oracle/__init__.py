@@ -40,6 +40,7 @@ _lib = None
 
 M_IDENTITY, M_JACOBI, M_ILU0, M_IC0, M_SSOR, M_DCT = range(6)
 M_MG = 7
+M_RBSSOR, M_RBILU = 8, 9
 STOP_RELRES, STOP_PAPER = 0, 1
 OK, MAXITER, INVALID, BREAKDOWN = 0, 1, -1, -3
 

@@ -261,6 +261,92 @@ static void orc_ssor_apply(const orc_precond* P, const double* r, double* s) {
   for (int i = 0; i < P->n; ++i) s[i] = s[i] * ((2.0 - w) / w);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Red-black orderings (multicolour; the paper leaves the ordering open).    */
+/* Red pixels (i + j even) come first, then black; the 5-point stencil only  */
+/* couples the two colours, so both triangular solves reduce to one pass per */
+/* colour.  The formulas are the natural-order ones of SSOR and ILU(0) taken */
+/* in that order of the unknowns.                                             */
+/* ------------------------------------------------------------------------ */
+static int orc_is_red(const orc_precond* P, int k) { return ((k / P->W) + (k % P->W)) % 2 == 0; }
+
+/* SSOR(omega) in red-black order: forward (D/w + L) y = r with red first
+ * (y_red = w r / D, y_black = w (r - A_br y_red) / D), z = (D/w) y, backward
+ * (D/w + L^T) s = z with black first (s_black = y_black, s_red = y_red - w
+ * A_rb s_black / D), times (2 - w)/w.  A zero diagonal is replaced by 1. */
+static void orc_rbssor_apply(const orc_precond* P, const double* r, double* s) {
+  double w = P->omega;
+  int n = P->n;
+  for (int k = 0; k < n; ++k)
+    if (orc_is_red(P, k)) s[k] = r[k] / (P->diag[k] / w);
+  for (int k = 0; k < n; ++k) {
+    if (orc_is_red(P, k)) continue;
+    double acc = r[k];
+    for (long t = P->indptr[k]; t < P->indptr[k + 1]; ++t)
+      if (P->indices[t] != k) acc -= P->data[t] * s[P->indices[t]];  /* all neighbours are red */
+    s[k] = acc / (P->diag[k] / w);
+  }
+  /* z = (D/w) y and the black rows of the backward solve give s_black = y_black */
+  for (int k = 0; k < n; ++k) {
+    if (!orc_is_red(P, k)) continue;
+    double acc = (P->diag[k] / w) * s[k];
+    for (long t = P->indptr[k]; t < P->indptr[k + 1]; ++t)
+      if (P->indices[t] != k) acc -= P->data[t] * s[P->indices[t]];  /* all neighbours are black */
+    s[k] = acc / (P->diag[k] / w);
+  }
+  for (int k = 0; k < n; ++k) s[k] = s[k] * ((2.0 - w) / w);
+}
+
+/* ILU(0) in red-black order: the red pivots are a_kk (no red-red coupling);
+ * a black pivot is a_bb - sum over its red neighbours k of a_bk a_kb / a_kk
+ * (the fill a red elimination would put into the black-black block falls on
+ * the diagonal only), guarded as in the natural order.  L y = r (y_red = r,
+ * y_black = r - A_br D_red^-1 y_red), U s = y (s_black = y / p, s_red =
+ * (y - A_rb s_black) / a_kk).  IC(0) in this order is the same M. */
+static void orc_rbilu_setup(orc_precond* P) {
+  for (int k = 0; k < P->n; ++k) {
+    double akk = P->data[P->dpos[k]];
+    if (orc_is_red(P, k)) {
+      P->fact[k] = orc_guard_pivot(akk, akk);
+    }
+  }
+  for (int k = 0; k < P->n; ++k) {
+    if (orc_is_red(P, k)) continue;
+    double akk = P->data[P->dpos[k]];
+    double piv = akk;
+    for (long t = P->indptr[k]; t < P->indptr[k + 1]; ++t) {
+      int j = P->indices[t];
+      if (j == k) continue;
+      long tj = orc_find(P, j, k);
+      piv -= P->data[t] * P->data[tj] / P->fact[j];
+    }
+    P->fact[k] = orc_guard_pivot(piv, akk);
+  }
+}
+
+static void orc_rbilu_apply(const orc_precond* P, const double* r, double* s) {
+  int n = P->n;
+  /* y_red = r_red, s_black = (r_black - sum a_bk y_k / p_k) / p_black */
+  for (int k = 0; k < n; ++k) {
+    if (orc_is_red(P, k)) continue;
+    double acc = r[k];
+    for (long t = P->indptr[k]; t < P->indptr[k + 1]; ++t) {
+      int j = P->indices[t];
+      if (j != k) acc -= P->data[t] / P->fact[j] * r[j];
+    }
+    s[k] = acc / P->fact[k];
+  }
+  for (int k = 0; k < n; ++k) {
+    if (!orc_is_red(P, k)) continue;
+    double acc = r[k];
+    for (long t = P->indptr[k]; t < P->indptr[k + 1]; ++t) {
+      int j = P->indices[t];
+      if (j != k) acc -= P->data[t] * s[j];
+    }
+    s[k] = acc / P->fact[k];
+  }
+}
+
 /* Orthonormal DCT-II matrix C[k][x] = c_k cos(pi k (x + 1/2) / n). */
 static void orc_dct_matrix(int n, double* C) {
   for (int k = 0; k < n; ++k) {
@@ -497,6 +583,15 @@ static int orc_precond_setup(orc_precond* P, int kind, int H, int W,
       break;
     case ORC_M_MG:
       return orc_mg_setup(P);
+    case ORC_M_RBSSOR:
+      if (!(omega > 0.0 && omega < 2.0)) return ORC_INVALID;
+      for (int i = 0; i < n; ++i) if (!(P->diag[i] > 0.0)) P->diag[i] = 1.0;
+      break;
+    case ORC_M_RBILU:
+      P->fact = (double*)malloc(sizeof(double) * n);
+      if (!P->fact) return ORC_INVALID;
+      orc_rbilu_setup(P);
+      break;
     default:
       return ORC_INVALID;
   }
@@ -527,6 +622,8 @@ static void orc_precond_solve(const orc_precond* P, const double* r, double* s) 
     case ORC_M_SSOR: orc_ssor_apply(P, r, s); break;
     case ORC_M_DCT: orc_dct_apply(P, r, s); break;
     case ORC_M_MG: orc_mg_apply(P, r, s); break;
+    case ORC_M_RBSSOR: orc_rbssor_apply(P, r, s); break;
+    case ORC_M_RBILU: orc_rbilu_apply(P, r, s); break;
   }
 }
 

@@ -25,7 +25,9 @@ enum {
   ORC_M_IC0 = 3,      /* IC(0), item 4 */
   ORC_M_SSOR = 4,     /* "SOR factorization", item 5, read as SSOR(omega) */
   ORC_M_DCT = 5,      /* unweighted Neumann-Poisson pseudo-inverse (Fourier basis, Sec. 1) */
-  ORC_M_MG = 7        /* one symmetric aggregation-multigrid V-cycle (multigrid, Sec. 1) */
+  ORC_M_MG = 7,       /* one symmetric aggregation-multigrid V-cycle (multigrid, Sec. 1) */
+  ORC_M_RBSSOR = 8,   /* SSOR(omega) with the unknowns in red-black order (red: i + j even, first) */
+  ORC_M_RBILU = 9     /* ILU(0) = IC(0) with the unknowns in red-black order */
 };
 
 /* Multigrid parameters (the method's definition, see orc_mg_*): damped-Jacobi

@@ -384,7 +384,8 @@ def run_ours(args):
                    "l2": "working set ~0.5 GB of planes > 129 MB L2 (inputs larger than L2)",
                    "inner_iterations": st["inner"], "outer_passes": st["outer"]},
         "plain": {"value": px / (ms_plain * 1e3), "unit": UNIT, "ms_per_step": ms_plain, "precond": "jacobi",
-                  "dtype": "f64", "inner_iterations": st_plain["inner"]},
+                  "dtype": "f64", "inner_iterations": st_plain["inner"],
+                  "roofline": plain_roofline(st_plain, cnt_plain, H, W, args.steps, peak, peak_kind)},
         "roofline": roofline,
         "e2e": {"value": px / (ms_e2e * 1e3), "unit": UNIT, "h2d_bytes_per_step": H * W * 8 + (H * W if mask is not None else 0),
                 "d2h_bytes_per_step": H * W * 8, "ms_per_step": ms_e2e},
@@ -408,6 +409,17 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def plain_roofline(st, cnt, H, W, steps, peak, peak_kind):
+    """The persistent FP64 Jacobi PCG kernel of the plain form: 112 algorithmic bytes per pixel
+    per iteration over its CUDA-event duration (events on the call's stream)."""
+    iters = st["inner_total"] * steps
+    s = cnt["solver_ms"] / 1e3
+    ach = ALG_BYTES[("f64", "jacobi")] * H * W * iters / s / 1e9 if s > 0 else None
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak if ach else None,
+            "kernel": "k_pcg64<jacobi> (persistent PCG)", "peak_source": f"{peak_kind} hbm_gbs",
+            "alg_bytes_per_px_iter": ALG_BYTES[("f64", "jacobi")], "solver_ms_per_step": cnt["solver_ms"] / steps}
 
 
 def gpu_launches(cnt, st, chosen, steps):

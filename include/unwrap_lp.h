@@ -46,8 +46,10 @@ extern "C" {
  * unweighted Neumann-Poisson pseudo-inverse applied through cosine transforms;
  * LEARNED is a trained network (ulp_unet) applied as M^-1 inside flexible CG;
  * MG is a multigrid cycle (the paper names multigrid among the fast solvers of
- * this system, Sec. 1).  DCT, LEARNED and MG run in flexible CG on single-map
- * FP64 plans. */
+ * this system, Sec. 1); RBSSOR and RBILU are items 3-5 with the unknowns in
+ * red-black order instead of the natural one (the paper leaves the ordering
+ * open), which makes each triangular solve one parallel pass per colour.  DCT,
+ * LEARNED, MG, RBSSOR and RBILU run in flexible CG on single-map FP64 plans. */
 typedef enum {
   ULP_PRECOND_IDENTITY = 0, /* M = I: PCG becomes CG */
   ULP_PRECOND_JACOBI = 1,   /* M = diag(A) */
@@ -56,8 +58,10 @@ typedef enum {
   ULP_PRECOND_SSOR = 4,     /* symmetric SOR, relaxation options.omega */
   ULP_PRECOND_DCT = 5,      /* s = L^+ r, L the unit-weight Neumann Laplacian */
   ULP_PRECOND_LEARNED = 6,  /* s = D^-1 r + rho N(r / rho, U, V), rho = rms(r); needs ulp_plan_set_unet */
-  ULP_PRECOND_MG = 7        /* one symmetric V-cycle of aggregation multigrid: 2x2 aggregates, Galerkin
+  ULP_PRECOND_MG = 7,       /* one symmetric V-cycle of aggregation multigrid: 2x2 aggregates, Galerkin
                                coarse operators, 2 + 2 damped-Jacobi sweeps (omega 2/3), correction x 1.5 */
+  ULP_PRECOND_RBSSOR = 8,   /* SSOR(omega) with the unknowns in red-black order (red: i + j even, first) */
+  ULP_PRECOND_RBILU = 9     /* ILU(0) (= IC(0)) with the unknowns in red-black order */
 } ulp_precond;
 
 typedef enum {

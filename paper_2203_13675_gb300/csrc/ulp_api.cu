@@ -304,8 +304,14 @@ __global__ void k_set_pt(PT pt, double* p, double* tau, int first, int n) {
   }
 }
 
+// preconditioners that run in the graph-driven flexible CG (single-map plans)
+static bool is_fcg_kind(int precond) {
+  return precond == ULP_PRECOND_DCT || precond == ULP_PRECOND_LEARNED || precond == ULP_PRECOND_MG ||
+         precond == ULP_PRECOND_RBSSOR || precond == ULP_PRECOND_RBILU;
+}
+
 static int check_solver_args(int precond, double tol, int max_outer) {
-  if (precond < ULP_PRECOND_IDENTITY || precond > ULP_PRECOND_MG)
+  if (precond < ULP_PRECOND_IDENTITY || precond > ULP_PRECOND_RBILU)
     return fail(ULP_ERR_INVALID, "unknown preconditioner %d", precond);
 
   if (!(tol > 0.0)) return fail(ULP_ERR_INVALID, "tol must be > 0");
@@ -394,8 +400,7 @@ static int enqueue_call(Plan& pl, const ulp_map* maps, int precond, double tol, 
     ULP_CU(launch_system(pl, pl.d_p, pl.d_tau, st));
     cudaEvent_t e0, e1;
     next_events(pl, &e0, &e1);
-    if (precond == ULP_PRECOND_DCT || precond == ULP_PRECOND_LEARNED || precond == ULP_PRECOND_MG)
-      ULP_CU(launch_fcg(pl, precond, a, st, e0, e1));
+    if (is_fcg_kind(precond)) ULP_CU(launch_fcg(pl, precond, a, st, e0, e1));
     else if (mixed) ULP_CU(launch_pcg32(pl, precond, a, st, e0, e1));
     else ULP_CU(launch_pcg64(pl, precond, a, st, e0, e1));
     ULP_CU(launch_outer_error(pl, pl.opt.outer_tol, max_outer, st));
@@ -460,6 +465,8 @@ extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precon
     return fail(ULP_ERR_UNSUPPORTED, "the DCT preconditioner is available on single-map plans");
   if (precond == ULP_PRECOND_MG && (pl.nmaps != 1 || !pl.mg))
     return fail(ULP_ERR_UNSUPPORTED, "the multigrid preconditioner is available on single-map plans");
+  if ((precond == ULP_PRECOND_RBSSOR || precond == ULP_PRECOND_RBILU) && pl.nmaps != 1)
+    return fail(ULP_ERR_UNSUPPORTED, "the red-black preconditioners are available on single-map plans");
   if (precond == ULP_PRECOND_LEARNED && (pl.nmaps != 1 || !pl.unet))
     return fail(ULP_ERR_UNSUPPORTED, "the learned preconditioner needs a single-map plan and ulp_plan_set_unet");
   for (int m = 0; m < pl.nmaps; ++m) {
@@ -472,8 +479,7 @@ extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precon
   pl.last_stream = st;
   // the DCT, learned and multigrid solves are themselves graphs with a WHILE node, which cannot be
   // nested: they run eagerly
-  if (pl.opt.graph && !pl.opt.profile && precond != ULP_PRECOND_DCT && precond != ULP_PRECOND_LEARNED &&
-      precond != ULP_PRECOND_MG)
+  if (pl.opt.graph && !pl.opt.profile && !is_fcg_kind(precond))
     rc = graph_call(pl, maps, precond, tol, max_outer, max_inner, st, mixed);
   else rc = enqueue_call(pl, maps, precond, tol, max_outer, max_inner, st, mixed);
   if (rc != ULP_OK) return rc;
@@ -706,6 +712,10 @@ extern "C" int ulp_precond_apply(int precond, const double* U, const double* V, 
   } else if (precond == ULP_PRECOND_IDENTITY || precond == ULP_PRECOND_JACOBI) {
     ULP_CU(launch_to_plane(pl, r, M.f.r, tp.st));
     ULP_CU(launch_jacobi_apply(pl, precond, M.f.r, M.f.s, tp.st));
+  } else if (precond == ULP_PRECOND_RBSSOR || precond == ULP_PRECOND_RBILU) {
+    ULP_CU(launch_to_plane(pl, r, M.f.r, tp.st));
+    ULP_CU(rb_setup(pl, precond, nullptr, tp.st));
+    ULP_CU(rb_apply(pl, precond, nullptr, tp.st));
   } else if (precond == ULP_PRECOND_MG) {
     ULP_CU(launch_to_plane(pl, r, M.f.r, tp.st));
     if (mask) ULP_CU(launch_mask_to_plane(pl, mask, tp.st));
@@ -745,8 +755,7 @@ extern "C" int ulp_pcg(const double* U, const double* V, const double* b, int H,
   ULP_CU(launch_to_plane(pl, b, M.f.b, tp.st));
   ULP_CU(launch_to_plane(pl, phi, M.f.phi, tp.st));
   if (precond == ULP_PRECOND_LEARNED) return fail(ULP_ERR_UNSUPPORTED, "ulp_pcg: the learned preconditioner needs a plan");
-  if (precond == ULP_PRECOND_DCT || precond == ULP_PRECOND_MG)
-    ULP_CU(launch_fcg(pl, precond, pcg_args(pl, tol, max_inner), tp.st));
+  if (is_fcg_kind(precond)) ULP_CU(launch_fcg(pl, precond, pcg_args(pl, tol, max_inner), tp.st));
   else ULP_CU(launch_pcg64(pl, precond, pcg_args(pl, tol, max_inner), tp.st, nullptr, nullptr));
   ULP_CU(launch_outer_error(pl, 0.0, 1, tp.st));
   ULP_CU(launch_from_plane(pl, M.f.phi, phi, tp.st));

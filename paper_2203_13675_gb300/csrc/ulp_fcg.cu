@@ -35,12 +35,16 @@ __global__ void k_set_args(PcgArgs a, PcgArgs* dst) { *dst = a; }
   MapState* S = a.st;                                                  \
   for (int t = gw; t < a.ntiles; t += NW)
 
-// BF16 copy of r at (i, j), (i, j+1) for the DCT's first GEMM (zero beyond column W-1)
+// BF16 copy of r at (i, j), (i, j+1) for the DCT's first GEMM, or the FP32 copy the
+// multigrid cycle starts from (zero beyond column W-1)
 __device__ __forceinline__ void put_rbf(const PcgArgs& a, const MapDesc& M, int i, int j, double2 r) {
   if (a.rbf && j < M.W) {
     const __nv_bfloat162 v = __floats2bfloat162_rn((float)r.x, j + 1 < M.W ? (float)r.y : 0.f);
     a.rbf[(size_t)i * a.rbf_ld + (j >> 1)] = *reinterpret_cast<const unsigned*>(&v);
   }
+  if (a.rf32 && j < M.W)
+    *reinterpret_cast<float2*>(a.rf32 + (size_t)i * M.pitch + j) =
+        make_float2((float)r.x, j + 1 < M.W ? (float)r.y : 0.f);
 }
 
 // The WHILE loop's own guard (one thread), run after the start phase and at the
@@ -176,27 +180,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_f_dots(const PcgArgs* pa, int i
     const double* __restrict__ sp = M.f.s;
     const double* __restrict__ bp = M.f.b;
     double rs = 0.0, rr = 0.0, bb = 0.0;
-    for (int i = g.i0; i < g.i1; i += 4) {
-      double2 rv[4], sv[4], bv[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (i + k < g.i1) {
-          const size_t off = (size_t)(i + k) * P + j;
-          rv[k] = ld2(rp, off);
-          sv[k] = ld2(sp, off);
-          if (init) bv[k] = ld2(bp, off);
-        }
+    if (init) {
+      for (int i = g.i0; i < g.i1; ++i) {
+        const size_t off = (size_t)i * P + j;
+        const double2 rv = ld2(rp, off), sv = ld2(sp, off), bv = ld2(bp, off);
+        rs = fma(rv.x, sv.x, rs);
+        rs = fma(rv.y, sv.y, rs);
+        rr = fma(rv.x, rv.x, rr);
+        rr = fma(rv.y, rv.y, rr);
+        bb = fma(bv.x, bv.x, bb);
+        bb = fma(bv.y, bv.y, bb);
       }
+    } else {
+      // rows in groups of eight, all sixteen loads of a group in flight together
+      for (int i = g.i0; i < g.i1; i += 8) {
+        double2 rv[8], sv[8];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (i + k < g.i1) {
-          rs = fma(rv[k].x, sv[k].x, rs);
-          rs = fma(rv[k].y, sv[k].y, rs);
-          rr = fma(rv[k].x, rv[k].x, rr);
-          rr = fma(rv[k].y, rv[k].y, rr);
-          if (init) {
-            bb = fma(bv[k].x, bv[k].x, bb);
-            bb = fma(bv[k].y, bv[k].y, bb);
+        for (int k = 0; k < 8; ++k) {
+          if (i + k < g.i1) {
+            const size_t off = (size_t)(i + k) * P + j;
+            rv[k] = ld2(rp, off);
+            sv[k] = ld2(sp, off);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if (i + k < g.i1) {
+            rs = fma(rv[k].x, sv[k].x, rs);
+            rs = fma(rv[k].y, sv[k].y, rs);
+            rr = fma(rv[k].x, rv[k].x, rr);
+            rr = fma(rv[k].y, rv[k].y, rr);
           }
         }
       }
@@ -232,7 +245,8 @@ static int tile_blocks(const Plan& pl) { return (pl.ntiles + kWarps - 1) / kWarp
 static cudaError_t fcg_precond(Plan& pl, int kind, cudaStream_t st) {
   const MapDesc& M = pl.hmaps[0];
   if (kind == ULP_PRECOND_DCT) return dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st, true);
-  if (kind == ULP_PRECOND_MG) return mg_apply(*pl.mg, M.f.mask, pl.dstate, st);
+  if (kind == ULP_PRECOND_MG) return mg_apply(*pl.mg, M.f.mask, pl.dstate, st, true);
+  if (kind == ULP_PRECOND_RBSSOR || kind == ULP_PRECOND_RBILU) return rb_apply(pl, kind, pl.dstate, st);
   const cudaError_t e = unet_apply_plane(*pl.unet, M.f.r, M.f.U, M.f.V, M.f.mask, M.H, M.W, M.pitch, M.f.s,
                                          &pl.dstate[0].fallback, st);
   if (e != cudaSuccess) return e;
@@ -248,6 +262,7 @@ static cudaError_t fcg_start(Plan& pl, int kind, cudaStream_t st) {
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && kind == ULP_PRECOND_DCT) e = dct_prepare_mask(*pl.dct, M.f.mask, M.pitch, st);
   if (e == cudaSuccess && kind == ULP_PRECOND_MG) e = mg_setup(*pl.mg, pl.dstate, st);
+  if (e == cudaSuccess) e = rb_setup(pl, kind, pl.dstate, st);
   if (e == cudaSuccess) e = fcg_precond(pl, kind, st);
   k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
   return e == cudaSuccess ? cudaGetLastError() : e;
@@ -348,6 +363,7 @@ static cudaError_t fcg_eager(Plan& pl, int kind, cudaStream_t st) {
   phase_mark(pl, st, 2);
   if (kind == ULP_PRECOND_DCT) e = dct_prepare_mask(*pl.dct, M.f.mask, M.pitch, st);
   if (e == cudaSuccess && kind == ULP_PRECOND_MG) e = mg_setup(*pl.mg, pl.dstate, st);
+  if (e == cudaSuccess) e = rb_setup(pl, kind, pl.dstate, st);
   if (e == cudaSuccess) e = fcg_precond(pl, kind, st);
   if (e != cudaSuccess) return e;
   phase_mark(pl, st, 3);
@@ -386,7 +402,9 @@ cudaError_t launch_fcg(Plan& pl, int kind, const PcgArgs& a_in, cudaStream_t st,
   PcgArgs a = a_in;
   a.rbf = nullptr;
   a.rbf_ld = 0;
+  a.rf32 = nullptr;
   if (kind == ULP_PRECOND_DCT) a.rbf = dct_input(*pl.dct, &a.rbf_ld);
+  if (kind == ULP_PRECOND_MG) a.rf32 = mg_input(*pl.mg);
   a.learned = kind == ULP_PRECOND_LEARNED;
   if (pl.opt.profile == 2) {
     a.cond = 0;

@@ -107,8 +107,14 @@ size_t mg_bytes(int H, int W);
 MgPlan* mg_create(const MapDesc& M, void* mem, int nsm);
 void mg_destroy(MgPlan* p);
 cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st);  // coarse grids, once per solve
-cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st);
+// packed: the FP32 copy of r (mg_input, the map's pitch) is already written
+cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st, bool packed = false);
+float* mg_input(const MgPlan& p);
 int mg_levels(const MgPlan& p);
+
+// ulp_rb.cu: red-black SSOR / ILU(0) on the map's planes (r -> s; ILU pivots in piv)
+cudaError_t rb_setup(const Plan& pl, int kind, const MapState* S, cudaStream_t st);  // once per solve
+cudaError_t rb_apply(const Plan& pl, int kind, const MapState* S, cudaStream_t st);
 
 // ulp_unet.cu: workspace for B images of Hn x Wn (multiples of 128); 0, -5 (no memory) or -2
 int unet_prepare(Unet& u, int B, int Hn, int Wn);

@@ -114,6 +114,7 @@ struct PcgArgs {
   unsigned long long cond;  // flexible-CG graph: WHILE-node handle cleared when the map stops (0 = none)
   unsigned* rbf;            // flexible-CG graph: BF16 copy of r as column pairs (the DCT input), or null
   int rbf_ld;               // its row stride in pairs
+  float* rf32;              // flexible-CG graph: FP32 copy of r (the multigrid's right-hand side), or null
   int learned;              // flexible CG with the learned preconditioner: stall / breakdown fall back to Jacobi
   int stall_window;
 };

@@ -628,10 +628,12 @@ cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st) {
 }
 
 // s = V-cycle(r) on the map's planes; mask zeroes s.
-cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st) {
+float* mg_input(const MgPlan& p) { return p.g[0].b; }
+
+cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st, bool packed) {
   const int L = (int)p.g.size();
   const Grid& g0 = p.g[0];
-  k_mg_rhs_v<<<mg_blocks(p, (long long)g0.H * ((g0.W + 3) / 4)), 256, 0, st>>>(p.r0, g0, S);
+  if (!packed) k_mg_rhs_v<<<mg_blocks(p, (long long)g0.H * ((g0.W + 3) / 4)), 256, 0, st>>>(p.r0, g0, S);
   if (L == 1) {
     k_mg_coarsest<<<1, 256, 0, st>>>(g0, S);
     k_mg_post2<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(g0, mask, p.s0, S);

@@ -14,7 +14,8 @@ import torch
 
 from . import build as _build
 
-PRECOND = {"identity": 0, "jacobi": 1, "ilu0": 2, "ic0": 3, "ssor": 4, "dct": 5, "learned": 6, "mg": 7}
+PRECOND = {"identity": 0, "jacobi": 1, "ilu0": 2, "ic0": 3, "ssor": 4, "dct": 5, "learned": 6, "mg": 7, "rbssor": 8,
+           "rbilu": 9}
 ULP_OK, ULP_WARN_MAXITER = 0, 1
 ULP_ERR_INVALID, ULP_ERR_CUDA, ULP_ERR_BREAKDOWN, ULP_ERR_TIMEOUT, ULP_ERR_NOMEM, ULP_ERR_UNSUPPORTED = \
     -1, -2, -3, -4, -5, -6

@@ -310,7 +310,10 @@ def run_ours(args):
                                           precision=native.ULP_PRECISION_MIXED if prec == "mixed" else 0)
                 if net is not None and prec == "f64":
                     plans[prec].set_unet(net)
+            # an NVTX range per form lets a profiler capture one form's kernels (ncu --nvtx-include)
+            torch.cuda.nvtx.range_push(f"form_{prec}_{pc}")
             res[(prec, pc)] = run_form(plans[prec], psi, mask, phi, w, pc, args.steps, args.warmup, dist)
+            torch.cuda.nvtx.range_pop()
             sols[(prec, pc)] = phi.cpu().numpy()
     ms_plain, st_plain, cnt_plain = res[("f64", "jacobi")]
     chosen = CHOSEN.get(wl_name, DEFAULT_CHOSEN)
@@ -472,7 +475,11 @@ def fcg_roofline(native, H, W, psi, mask, w, precond, timed_plan):
     call = dict(p=w["p"], eps=w["tau"], precond=precond, tol=w["tol"], max_outer=w["max_outer"], stats=False)
     eager.unwrap(psi, mask, **call)
     eager.counters(reset=True)
+    # kernels inside a graph with a WHILE node are invisible to ncu; this replay's are not
+    import torch
+    torch.cuda.nvtx.range_push(f"replay_{precond}")
     eager.unwrap(psi, mask, **call)
+    torch.cuda.nvtx.range_pop()
     c = eager.counters(reset=True)
     eager.close()
     Hp, Wp = (H + 127) // 128 * 128, (W + 127) // 128 * 128

@@ -260,7 +260,7 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
       cudaGetLastError();
       return fail(ULP_ERR_NOMEM, "cudaMalloc(multigrid levels): %s", cudaGetErrorString(e));
     }
-    pl.mg = mg_create(pl.hmaps[0], pl.mg_mem, pl.nsm);
+    pl.mg = mg_create(pl.hmaps[0], pl.mg_mem, pl.nsm, pl.ntiles);
   }
   ULP_CU(cudaDeviceSynchronize());  // workspace zeroed before any stream may use it
   return ULP_OK;

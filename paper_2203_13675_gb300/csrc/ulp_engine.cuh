@@ -141,11 +141,13 @@ enum Phase { kPhResInit = 0, kPhA = 1, kPhB = 2, kPhRes = 3, kPhFcg = 4 };
 // Runs in the warp whose tile arrival completed phase `ph` for map m: reduces
 // the map's tile partials in a fixed order and advances its scalars
 // (alpha = delta_new / d^T q; delta_old, delta_new, beta; stop tests).
-__device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, MapState* Sp, int ph, int lane) {
+// ngroups: how many group sums the arrival left (0: as many as the map's tiles make).
+__device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, MapState* Sp, int ph, int lane,
+                                           int ngroups = 0) {
   volatile MapState* S = Sp;
   // the per-group sums in group order, then a fixed shuffle tree
   const int n = M.ntiles;
-  const int ng = n < kArriveGroups ? n : kArriveGroups;
+  const int ng = ngroups > 0 ? ngroups : (n < kArriveGroups ? n : kArriveGroups);
   const int cnt = (ph == kPhA) ? 1 : (ph == kPhResInit || ph == kPhFcg) ? 3 : 2;
   const bool own = lane < ng;
   // L2 loads: another warp wrote them, and this SM's L1 may hold an older phase's values
@@ -297,6 +299,56 @@ __device__ __forceinline__ void tile_arrive(const PcgArgs& a, const MapDesc& M, 
   if (last) {
     __syncwarp();
     finish_map(a, M, S, ph, lane);
+  }
+}
+
+// Arrival of the flexible-CG dot phase from a kernel that covers the map with its
+// own decomposition into n warps (32 <= n <= the map's tile count), warp w: its
+// r^T s and r^T r go to P0, P1 at tile_base + w and count as above with n in
+// place of the tile count; the r_{k+1}^T s_k partials that phase B left in P2
+// are indexed by the map's tiles, so the last warp of group g sums P2 over the
+// map's tiles of group g.  Same fixed summation order on every run.
+__device__ __forceinline__ void warp_arrive_fcg(const PcgArgs& a, const MapDesc& M, MapState* S, int w, int n,
+                                                double rs, double rr, int lane) {
+  rs = warp_sum(rs);
+  rr = warp_sum(rr);
+  const int base = M.tile_base;
+  const int g = w % kArriveGroups;
+  const int gsize = (n - g + kArriveGroups - 1) / kArriveGroups;
+  const int gsize2 = g < M.ntiles ? (M.ntiles - g + kArriveGroups - 1) / kArriveGroups : 0;
+  int glast = 0;
+  if (lane == 0) {
+    __stcg(a.P0 + base + w, rs);
+    __stcg(a.P1 + base + w, rr);
+    glast = atom_add_acq_rel(&S->arrive_grp[g], 1u) == (unsigned)gsize - 1u;
+  }
+  glast = __shfl_sync(kFull, glast, 0);
+  if (!glast) return;
+  __syncwarp();
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll 4
+  for (int m = lane; m < gsize; m += 32) {
+    const int idx = base + g + kArriveGroups * m;
+    s0 += __ldcg(a.P0 + idx);
+    s1 += __ldcg(a.P1 + idx);
+  }
+#pragma unroll 4
+  for (int m = lane; m < gsize2; m += 32) s2 += __ldcg(a.P2 + base + g + kArriveGroups * m);
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  int last = 0;
+  if (lane == 0) {
+    volatile double* gp = &S->gpart[0][0];
+    gp[0 * kArriveGroups + g] = s0;
+    gp[1 * kArriveGroups + g] = s1;
+    gp[2 * kArriveGroups + g] = s2;
+    last = atom_add_acq_rel(&S->arrive, 1u) == (unsigned)kArriveGroups - 1u;
+  }
+  last = __shfl_sync(kFull, last, 0);
+  if (last) {
+    __syncwarp();
+    finish_map(a, M, S, kPhFcg, lane, kArriveGroups);
   }
 }
 

@@ -242,10 +242,11 @@ static int tile_blocks(const Plan& pl) { return (pl.ntiles + kWarps - 1) / kWarp
 
 // s = M^-1 r of the flexible solve: the DCT chain, or the network followed by its
 // Jacobi fallback (only one of the two does work in any iteration).
-static cudaError_t fcg_precond(Plan& pl, int kind, cudaStream_t st) {
+// With fuse_dots the multigrid cycle's last kernel also runs the dot phase D.
+static cudaError_t fcg_precond(Plan& pl, int kind, cudaStream_t st, bool fuse_dots = false) {
   const MapDesc& M = pl.hmaps[0];
   if (kind == ULP_PRECOND_DCT) return dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st, true);
-  if (kind == ULP_PRECOND_MG) return mg_apply(*pl.mg, M.f.mask, pl.dstate, st, true);
+  if (kind == ULP_PRECOND_MG) return mg_apply(*pl.mg, M.f.mask, pl.dstate, st, true, fuse_dots ? pl.dargs : nullptr);
   if (kind == ULP_PRECOND_RBSSOR || kind == ULP_PRECOND_RBILU) return rb_apply(pl, kind, pl.dstate, st);
   const cudaError_t e = unet_apply_plane(*pl.unet, M.f.r, M.f.U, M.f.V, M.f.mask, M.H, M.W, M.pitch, M.f.s,
                                          &pl.dstate[0].fallback, st);
@@ -268,15 +269,19 @@ static cudaError_t fcg_start(Plan& pl, int kind, cudaStream_t st) {
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
+// D rides on the multigrid cycle's last kernel where the plan allows it
+static bool fused_dots(const Plan& pl, int kind) { return kind == ULP_PRECOND_MG && mg_fuses_dots(*pl.mg); }
+
 // One iteration: A, B, R, s = M^-1 r, D.
 static cudaError_t fcg_iteration(Plan& pl, int kind, cudaStream_t st) {
   const int nb = tile_blocks(pl);
+  const bool fd = fused_dots(pl, kind);
   k_f_a<<<nb, kThreads, 0, st>>>(pl.dargs);
   k_f_b<<<nb, kThreads, 0, st>>>(pl.dargs);
   k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = fcg_precond(pl, kind, st);
-  k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
+  if (e == cudaSuccess) e = fcg_precond(pl, kind, st, fd);
+  if (!fd) k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
@@ -381,10 +386,13 @@ static cudaError_t fcg_eager(Plan& pl, int kind, cudaStream_t st) {
     phase_mark(pl, st, 1);
     k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
     phase_mark(pl, st, 2);
-    if ((e = fcg_precond(pl, kind, st)) != cudaSuccess) return e;
+    const bool fd = fused_dots(pl, kind);
+    if ((e = fcg_precond(pl, kind, st, fd)) != cudaSuccess) return e;
     phase_mark(pl, st, 3);
-    k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
-    phase_mark(pl, st, 4);
+    if (!fd) {
+      k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
+      phase_mark(pl, st, 4);
+    }
   }
   return cudaGetLastError();
 }

@@ -104,11 +104,15 @@ int dct_error(const DctPlan& d);  // 1 if a GEMM wait ran out since the last cal
 // ulp_fcg.cu
 // ulp_mg.cu: aggregation multigrid on the map's planes (U, V, D^-1; r -> s, y as scratch)
 size_t mg_bytes(int H, int W);
-MgPlan* mg_create(const MapDesc& M, void* mem, int nsm);
+MgPlan* mg_create(const MapDesc& M, void* mem, int nsm, int ntiles);
 void mg_destroy(MgPlan* p);
 cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st);  // coarse grids, once per solve
-// packed: the FP32 copy of r (mg_input, the map's pitch) is already written
-cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st, bool packed = false);
+// packed: the FP32 copy of r (mg_input, the map's pitch) is already written; dots (device
+// arguments of a flexible-CG solve, or null): the cycle's last kernel also does the solve's
+// dot phase (r^T s, r^T r, beta, stop test), if mg_fuses_dots
+cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st, bool packed = false,
+                     const PcgArgs* dots = nullptr);
+bool mg_fuses_dots(const MgPlan& p);
 float* mg_input(const MgPlan& p);
 int mg_levels(const MgPlan& p);
 

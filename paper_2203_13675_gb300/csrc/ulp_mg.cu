@@ -26,6 +26,7 @@
 // FP32 rounding.
 #include <vector>
 
+#include "ulp_engine.cuh"
 #include "ulp_host.h"
 
 namespace ulp {
@@ -356,6 +357,241 @@ __global__ void k_mg_rhs_v(const double* __restrict__ r, Grid g, const MapState*
   }
 }
 
+// ---------------------------------------------------------------- fused row walkers
+// One launch per grid and direction instead of two.  A warp owns a window of 128
+// columns starting at j0 = 120 k - 4 (four pixels per lane, float4 accesses) and
+// a band of rows, and walks down the band keeping the last rows of every
+// quantity in registers.  Lanes 1..30 produce the window's inner 120 columns;
+// lanes 0 and 31 only supply the column neighbours, whose values two sweeps deep
+// are exact because the window extends four columns past the output on each
+// side.  The rows two sweeps deep above and below the band are recomputed, not
+// read back, so no value crosses between warps within a launch.
+//   k_mg_down: x1 = w D^-1 b, x2 = x1 + w D^-1 (b - A x1) (both pre-sweeps), x = x2
+//              written, and b_c = P^T (b - A x2) (residual + restriction)
+//   k_mg_up:   x' = x + cc P x_c, t = x' + w D^-1 (b - A x'), s = t + w D^-1 (b - A t);
+//              s goes to the grid's t plane (x is still being read by the
+//              neighbouring bands), or on the map's grid to the FP64 s (0 on
+//              masked pixels), where the warp also sums r^T s and r^T r for the
+//              flexible CG's dot phase.
+// Per pixel the arithmetic is that of the per-step kernels above.
+constexpr int kSegOut = 120;
+
+// row i of a plane at the lane's 4 columns from j: 0 outside the grid
+__device__ __forceinline__ float4 lrow(const float* p, const Grid& f, int i, int j) {
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (i >= 0 && i < f.H && j >= 0 && j < f.W) v = ld4(p + (size_t)i * f.ld + j);
+  v.y = j + 1 < f.W ? v.y : 0.f;
+  v.z = j + 2 < f.W ? v.z : 0.f;
+  v.w = j + 3 < f.W ? v.w : 0.f;
+  return v;
+}
+
+// (A y) at the lane's 4 pixels of row i: y at rows i-1, i, i+1, U and V of row i, V of
+// row i-1; column neighbours from the adjacent lanes (lanes 0 and 31 take 0 outside)
+__device__ __forceinline__ float4 arow(const float4& yn, const float4& yc, const float4& ys, const float4& U,
+                                       const float4& V, const float4& Vn, int lane) {
+  float ul = __shfl_up_sync(0xffffffffu, U.w, 1);
+  float yl = __shfl_up_sync(0xffffffffu, yc.w, 1);
+  float yr = __shfl_down_sync(0xffffffffu, yc.x, 1);
+  if (lane == 0) ul = yl = 0.f;
+  if (lane == 31) yr = 0.f;
+  const float uw[4] = {ul, U.x, U.y, U.z};
+  const float ue[4] = {U.x, U.y, U.z, U.w};
+  const float yw[4] = {yl, yc.x, yc.y, yc.z};
+  const float ye[4] = {yc.y, yc.z, yc.w, yr};
+  float out[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float d = ue[k] + f4(V, k) + uw[k] + f4(Vn, k);
+    out[k] = d * f4(yc, k) - ue[k] * ye[k] - uw[k] * yw[k] - f4(V, k) * f4(ys, k) - f4(Vn, k) * f4(yn, k);
+  }
+  return make_float4(out[0], out[1], out[2], out[3]);
+}
+
+// y + w D^-1 (b - a)
+__device__ __forceinline__ float4 jac4(const float4& y, const float4& D, const float4& b, const float4& a) {
+  return make_float4(y.x + kOmegaF * D.x * (b.x - a.x), y.y + kOmegaF * D.y * (b.y - a.y),
+                     y.z + kOmegaF * D.z * (b.z - a.z), y.w + kOmegaF * D.w * (b.w - a.w));
+}
+
+__device__ __forceinline__ bool walk_warp(int W, int bands, int& seg, int& band, int& j, int& lane) {
+  const int nseg = (W + kSegOut - 1) / kSegOut;
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  lane = threadIdx.x & 31;
+  if (w >= nseg * bands) return false;
+  seg = w % nseg;
+  band = w / nseg;
+  j = seg * kSegOut - 4 + 4 * lane;
+  return true;
+}
+
+// The raw loads of one row, issued one row ahead of the arithmetic that uses them
+// (a warp's walk is otherwise one memory round trip per row).
+struct DownRow {
+  float4 U, V, D, B;
+};
+__device__ __forceinline__ DownRow down_row(const Grid& f, int r, int j) {
+  return DownRow{lrow(f.U, f, r, j), lrow(f.V, f, r, j), lrow(f.Dinv, f, r, j), lrow(f.b, f, r, j)};
+}
+
+// pre-smoothing + residual + restriction for the coarse rows [RB band, RB band + RB)
+__global__ void __launch_bounds__(256, 2) k_mg_down(Grid f, Grid c, int RB, const MapState* S) {
+  if (skip_map(S)) return;
+  int seg, band, j, lane;
+  if (!walk_warp(f.W, (c.H + RB - 1) / RB, seg, band, j, lane)) return;
+  const bool out = lane >= 1 && lane <= 30 && j < f.W;
+  const int I0 = band * RB, I1 = min(c.H, I0 + RB);
+  const int r0 = 2 * I0, r1 = min(f.H, 2 * I1);
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  // rows r-1, r-2, r-3 of the window (m1, m2, m3)
+  float4 Um1 = z, Um2 = z, Vm1 = z, Vm2 = z, Vm3 = z, Dm1 = z, Bm1 = z, Bm2 = z;
+  float4 X1m1 = z, X1m2 = z, X2m2 = z, X2m3 = z;
+  float lo = 0.f, hi = 0.f;
+  DownRow nx = down_row(f, r0 - 2, j);
+  for (int r = r0 - 2; r <= r1 + 1; ++r) {
+    const DownRow cu = nx;
+    if (r + 1 <= r1 + 1) nx = down_row(f, r + 1, j);
+    const float4 U = cu.U, V = cu.V, D = cu.D, B = cu.B;
+    const float4 X1 = make_float4(kOmegaF * D.x * B.x, kOmegaF * D.y * B.y, kOmegaF * D.z * B.z, kOmegaF * D.w * B.w);
+    // x2 at row q = r - 1
+    const int q = r - 1;
+    float4 X2 = z;
+    if (q >= r0 - 1 && q >= 0 && q < f.H) {
+      X2 = jac4(X1m1, Dm1, Bm1, arow(X1m2, X1m1, X1, Um1, Vm1, Vm2, lane));
+      if (out && q >= r0 && q < r1) *reinterpret_cast<float4*>(f.x + (size_t)q * f.ld + j) = X2;
+    }
+    // residual at row p = r - 2, summed over the aggregate's two columns and two rows
+    const int p = r - 2;
+    if (p >= r0 && p < r1) {
+      const float4 a = arow(X2m3, X2m2, X2, Um2, Vm2, Vm3, lane);
+      if ((p & 1) == 0) {
+        lo = (Bm2.x - a.x) + (Bm2.y - a.y);
+        hi = (Bm2.z - a.z) + (Bm2.w - a.w);
+      } else {
+        lo += (Bm2.x - a.x) + (Bm2.y - a.y);
+        hi += (Bm2.z - a.z) + (Bm2.w - a.w);
+      }
+      if (out && ((p & 1) || p + 1 >= f.H))
+        *reinterpret_cast<float2*>(c.b + (size_t)(p >> 1) * c.ld + (j >> 1)) = make_float2(lo, hi);
+    }
+    Vm3 = Vm2; Vm2 = Vm1; Vm1 = V;
+    Um2 = Um1; Um1 = U;
+    Dm1 = D;
+    Bm2 = Bm1; Bm1 = B;
+    X1m2 = X1m1; X1m1 = X1;
+    X2m3 = X2m2; X2m2 = X2;
+  }
+}
+
+struct UpRow {
+  float4 U, V, D, B, XP;  // row r
+  double2 ra, rb;         // the map's r at row r - 2 (dot phase)
+  uchar4 mk;              // the mask at row r - 2
+};
+template <bool MAP>
+__device__ __forceinline__ UpRow up_row(const Grid& f, const Grid& c, const float* xc, const uint8_t* mask,
+                                        const double* rv, int r, int j) {
+  UpRow u;
+  u.U = lrow(f.U, f, r, j);
+  u.V = lrow(f.V, f, r, j);
+  u.D = lrow(f.Dinv, f, r, j);
+  u.B = lrow(f.b, f, r, j);
+  u.XP = lrow(f.x, f, r, j);
+  if (r >= 0 && r < f.H && j >= 0 && j < f.W) {
+    const float2 e = *reinterpret_cast<const float2*>(xc + (size_t)(r >> 1) * c.ld + (j >> 1));
+    u.XP = make_float4(u.XP.x + kCCF * e.x, u.XP.y + kCCF * e.x, u.XP.z + kCCF * e.y, u.XP.w + kCCF * e.y);
+    if (j + 1 >= f.W) u.XP.y = 0.f;
+    if (j + 2 >= f.W) u.XP.z = 0.f;
+    if (j + 3 >= f.W) u.XP.w = 0.f;
+  }
+  u.ra = u.rb = make_double2(0.0, 0.0);
+  u.mk = make_uchar4(0, 0, 0, 0);
+  if (MAP) {
+    const int p = r - 2;
+    if (p >= 0 && p < f.H && j >= 0 && j < f.W) {
+      const size_t o = (size_t)p * f.ld + j;
+      if (mask) u.mk = *reinterpret_cast<const uchar4*>(mask + o);
+      if (rv) {
+        u.ra = *reinterpret_cast<const double2*>(rv + o);
+        u.rb = *reinterpret_cast<const double2*>(rv + o + 2);
+      }
+    }
+  }
+  return u;
+}
+
+// prolongation + correction + both post-sweeps for the rows [R band, R band + R).
+// xc: the coarse grid's corrected solution.  MAP (the map's grid): s in FP64; with pa,
+// r^T s and r^T r (r: the map's FP64 residual) over the warp's pixels arrive in the
+// flexible CG's dot phase.
+template <bool MAP>
+__global__ void __launch_bounds__(256, 2) k_mg_up(Grid f, Grid c, const float* __restrict__ xc, int R,
+                                                  const uint8_t* mask, double* s, const double* __restrict__ rv,
+                                                  const PcgArgs* pa, const MapState* S) {
+  if (skip_map(S)) return;
+  int seg, band, j, lane;
+  const int bands = (f.H + R - 1) / R;
+  if (!walk_warp(f.W, bands, seg, band, j, lane)) return;
+  const bool out = lane >= 1 && lane <= 30 && j < f.W;
+  const int i0 = band * R, i1 = min(f.H, i0 + R);
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 Um1 = z, Um2 = z, Vm1 = z, Vm2 = z, Vm3 = z, Dm1 = z, Dm2 = z, Bm1 = z, Bm2 = z;
+  float4 XPm1 = z, XPm2 = z, Tm2 = z, Tm3 = z;
+  double rs = 0.0, rr = 0.0;
+  UpRow nx = up_row<MAP>(f, c, xc, mask, rv, i0 - 2, j);
+  for (int r = i0 - 2; r <= i1 + 1; ++r) {
+    const UpRow cu = nx;
+    if (r + 1 <= i1 + 1) nx = up_row<MAP>(f, c, xc, mask, rv, r + 1, j);
+    const float4 U = cu.U, V = cu.V, D = cu.D, B = cu.B, XP = cu.XP;
+    // t at row q = r - 1
+    const int q = r - 1;
+    float4 T = z;
+    if (q >= i0 - 1 && q >= 0 && q < f.H) T = jac4(XPm1, Dm1, Bm1, arow(XPm2, XPm1, XP, Um1, Vm1, Vm2, lane));
+    // s at row p = r - 2
+    const int p = r - 2;
+    if (p >= i0 && p < i1) {
+      const float4 v = jac4(Tm2, Dm2, Bm2, arow(Tm3, Tm2, T, Um2, Vm2, Vm3, lane));
+      const size_t o = (size_t)p * f.ld + j;
+      if (!MAP) {
+        if (out) *reinterpret_cast<float4*>(f.t + o) = v;
+      } else if (out) {
+        // the map's grid: FP64 s, 0 on masked pixels and nothing beyond column W - 1
+        const uchar4 mk = cu.mk;
+        const double sv[4] = {mk.x ? 0.0 : (double)v.x, mk.y ? 0.0 : (double)v.y, mk.z ? 0.0 : (double)v.z,
+                              mk.w ? 0.0 : (double)v.w};
+        if (j + 4 <= f.W) {
+          *reinterpret_cast<double2*>(s + o) = make_double2(sv[0], sv[1]);
+          *reinterpret_cast<double2*>(s + o + 2) = make_double2(sv[2], sv[3]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (j + k < f.W) s[o + k] = sv[k];
+        }
+        if (rv) {
+          const double rk[4] = {cu.ra.x, cu.ra.y, cu.rb.x, cu.rb.y};
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (j + k < f.W) {
+              rs = fma(rk[k], sv[k], rs);
+              rr = fma(rk[k], rk[k], rr);
+            }
+        }
+      }
+    }
+    Vm3 = Vm2; Vm2 = Vm1; Vm1 = V;
+    Um2 = Um1; Um1 = U;
+    Dm2 = Dm1; Dm1 = D;
+    Bm2 = Bm1; Bm1 = B;
+    XPm2 = XPm1; XPm1 = XP;
+    Tm3 = Tm2; Tm2 = T;
+  }
+  if (MAP && pa) {
+    const PcgArgs a = *pa;
+    const int nseg = (f.W + kSegOut - 1) / kSegOut;
+    warp_arrive_fcg(a, a.maps[0], a.st, band * nseg + seg, nseg * bands, rs, rr, lane);
+  }
+}
+
 // The grids from index lt down (each at most kTailMax unknowns, together at
 // most kTailPx) in one block, in shared memory: U, V, D^-1 copied in, the
 // right-hand side of grid lt read from global memory, the whole rest of the
@@ -513,6 +749,8 @@ using namespace mg;
 
 struct MgPlan {
   std::vector<Grid> g;   // FP32 grids; g[0] has the map's size and pitch
+  std::vector<int> walk_rb, walk_r;  // per grid: walker bands (coarse rows down, rows up), 0: per-step kernels
+  int dots_warps = 0;    // warps of the map's up walker when it also does the dot phase (0: it does not)
   int lt = -1;           // first grid handled by the shared-memory tail kernel (-1: none)
   TailGrids tail{};
   size_t tail_smem = 0;
@@ -536,7 +774,17 @@ size_t mg_bytes(int H, int W) {
   return bytes + 256;
 }
 
-MgPlan* mg_create(const MapDesc& M, void* mem, int nsm) {
+constexpr int kVecMinW = 64;  // grids at least this wide use the vector kernels and walkers
+
+// Rows per band: at least rmin, and no more warps than target.
+static int walk_rows(int rows, int W, int rmin, long long target) {
+  const long long nseg = (W + kSegOut - 1) / kSegOut;
+  int R = rmin;
+  while (nseg * ((rows + R - 1) / R) > target) ++R;
+  return R;
+}
+
+MgPlan* mg_create(const MapDesc& M, void* mem, int nsm, int ntiles) {
   MgPlan* p = new MgPlan();
   p->mem = mem;
   p->nsm = nsm;
@@ -578,6 +826,20 @@ MgPlan* mg_create(const MapDesc& M, void* mem, int nsm) {
     c.t = take(n);
     p->g.push_back(c);
   }
+  // walker bands: the shortest bands (fewest sequential rows per warp) that keep the
+  // warps to one resident wave of 16 per SM; on the map's grid also no more warps than
+  // the plan has tiles (the dot phase's partial arrays)
+  const long long target = 16LL * nsm;
+  for (size_t l = 0; l < p->g.size(); ++l) {
+    const Grid& f = p->g[l];
+    const bool walk = l + 1 < p->g.size() && f.W >= kVecMinW;
+    p->walk_rb.push_back(walk ? walk_rows(p->g[l + 1].H, f.W, 1, target) : 0);
+    p->walk_r.push_back(walk ? walk_rows(f.H, f.W, 2, l == 0 ? (target < ntiles ? target : ntiles) : target) : 0);
+  }
+  if (p->walk_r[0] > 0) {
+    const long long n = (long long)((M.W + kSegOut - 1) / kSegOut) * ((M.H + p->walk_r[0] - 1) / p->walk_r[0]);
+    if (n >= kArriveGroups && n <= ntiles) p->dots_warps = (int)n;
+  }
   // the tail: the smallest suffix of grids, from the first with at most kTailMax unknowns,
   // if it fits the shared-memory budget and there is a grid before it
   const int L = (int)p->g.size();
@@ -603,7 +865,7 @@ MgPlan* mg_create(const MapDesc& M, void* mem, int nsm) {
 
 void mg_destroy(MgPlan* p) { delete p; }
 
-constexpr int kVecMinW = 64;  // grids at least this wide use the vector kernels
+bool mg_fuses_dots(const MgPlan& p) { return p.dots_warps > 0; }
 
 static unsigned row_blocks(const Grid& f, int rows) {
   const long long warps = (long long)rows * ((f.W + 127) / 128);
@@ -630,7 +892,13 @@ cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st) {
 // s = V-cycle(r) on the map's planes; mask zeroes s.
 float* mg_input(const MgPlan& p) { return p.g[0].b; }
 
-cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st, bool packed) {
+static unsigned walk_blocks(const Grid& f, int rows, int R) {
+  const long long warps = (long long)((f.W + kSegOut - 1) / kSegOut) * ((rows + R - 1) / R);
+  return (unsigned)((warps + 7) / 8);
+}
+
+cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st, bool packed,
+                     const PcgArgs* dots) {
   const int L = (int)p.g.size();
   const Grid& g0 = p.g[0];
   if (!packed) k_mg_rhs_v<<<mg_blocks(p, (long long)g0.H * ((g0.W + 3) / 4)), 256, 0, st>>>(p.r0, g0, S);
@@ -642,7 +910,10 @@ cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cu
   const int stop = p.lt > 0 ? p.lt : L - 1;  // grids [0, stop) by per-grid kernels
   for (int l = 0; l < stop; ++l) {
     const Grid& f = p.g[l];
-    if (f.W >= kVecMinW) {
+    if (p.walk_rb[l] > 0) {
+      const Grid& c = p.g[l + 1];
+      k_mg_down<<<walk_blocks(f, c.H, p.walk_rb[l]), 256, 0, st>>>(f, c, p.walk_rb[l], S);
+    } else if (f.W >= kVecMinW) {
       k_mg_sweep_v<kSrcX1><<<row_blocks(f, f.H), 256, 0, st>>>(f, Grid{}, f.x, nullptr, nullptr, S);
       k_mg_res_v<<<row_blocks(f, p.g[l + 1].H), 256, 0, st>>>(f, p.g[l + 1], S);
     } else {
@@ -664,7 +935,19 @@ cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cu
   }
   for (int l = stop - 1; l >= 0; --l) {
     const Grid& f = p.g[l];
-    if (f.W >= kVecMinW) {
+    if (p.walk_r[l] > 0) {
+      // the coarse grid's corrected solution: the t plane if a walker made it, else x
+      const Grid& c = p.g[l + 1];
+      const float* xc = (l + 1 < stop && p.walk_r[l + 1] > 0) ? c.t : c.x;
+      const int R = p.walk_r[l];
+      if (l == 0) {
+        const bool d = dots && p.dots_warps > 0;
+        k_mg_up<true><<<walk_blocks(f, f.H, R), 256, 0, st>>>(f, c, xc, R, mask, p.s0, d ? p.r0 : nullptr,
+                                                              d ? dots : nullptr, S);
+      } else {
+        k_mg_up<false><<<walk_blocks(f, f.H, R), 256, 0, st>>>(f, c, xc, R, nullptr, nullptr, nullptr, nullptr, S);
+      }
+    } else if (f.W >= kVecMinW) {
       k_mg_sweep_v<kSrcXP><<<row_blocks(f, f.H), 256, 0, st>>>(f, p.g[l + 1], f.t, nullptr, nullptr, S);
       k_mg_sweep_v<kSrcT><<<row_blocks(f, f.H), 256, 0, st>>>(f, Grid{}, f.x, l == 0 ? mask : nullptr,
                                                                l == 0 ? p.s0 : nullptr, S);

@@ -7,12 +7,15 @@ tolerance 1e-6, Algorithm 1's inner test delta_new <= eps^2 delta_0 with
 eps = 0.005, l_max = 2MN.  Records the inner iterations (the paper's Fig. 2)
 and the time (Fig. 3) per size and preconditioner; --oracle adds the FP64 CPU
 oracle's iteration counts and time for the sizes up to --oracle-max pixels.
+--preconds picks the columns (default: the paper's five; "all" adds the
+red-black, DCT and multigrid preconditioners).
 
 The paper's 640x480 map (Fig. 1) is not available; each size uses the seeded
 generator of synth.py (ramp 0.05 rad/px, 6 bumps with widths scaled to the
 size, noise 0.3 rad).
 
 usage: python -m paper_2203_13675_gb300.experiment_table1 [--out table1.json] [--oracle]
+                                                         [--preconds identity,jacobi,...|all]
 """
 import argparse
 import json
@@ -24,6 +27,9 @@ from . import native, synth
 
 SIZES = [(160, 120), (320, 240), (480, 360), (640, 480), (800, 600), (960, 720), (1120, 840), (1280, 960)]
 PRECONDS = ["identity", "jacobi", "ilu0", "ic0", "ssor"]
+# beyond the paper's list: red-black orderings of its SSOR and ILU(0), the DCT
+# Poisson solve and the multigrid V-cycle (all in flexible CG)
+EXTRA = ["rbssor", "rbilu", "dct", "mg"]
 
 
 def make_map(cols, rows, seed=1):
@@ -53,7 +59,8 @@ def run(out, with_oracle=False, oracle_max=640 * 480, sizes=SIZES, preconds=PREC
             if with_oracle and rows * cols <= oracle_max:
                 import oracle  # test infrastructure: the CPU baseline of the experiment
                 kinds = {"identity": oracle.M_IDENTITY, "jacobi": oracle.M_JACOBI, "ilu0": oracle.M_ILU0,
-                         "ic0": oracle.M_IC0, "ssor": oracle.M_SSOR}
+                         "ic0": oracle.M_IC0, "ssor": oracle.M_SSOR, "rbssor": oracle.M_RBSSOR,
+                         "rbilu": oracle.M_RBILU, "dct": oracle.M_DCT, "mg": oracle.M_MG}
                 t0 = time.perf_counter()
                 _, ost = oracle.unwrap(m.psi, None, p=p, kind=kinds[pc], tol=0.005, max_outer=500,
                                        outer_tol=1e-6, stop_mode=oracle.STOP_PAPER)
@@ -74,8 +81,10 @@ def main():
     ap.add_argument("--oracle", action="store_true")
     ap.add_argument("--oracle-max", type=int, default=640 * 480)
     ap.add_argument("--p", type=float, default=1.0)
+    ap.add_argument("--preconds", default=",".join(PRECONDS))
     a = ap.parse_args()
-    run(a.out, a.oracle, a.oracle_max, p=a.p)
+    pcs = PRECONDS + EXTRA if a.preconds == "all" else a.preconds.split(",")
+    run(a.out, a.oracle, a.oracle_max, preconds=pcs, p=a.p)
 
 
 if __name__ == "__main__":

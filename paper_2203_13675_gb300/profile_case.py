@@ -21,7 +21,7 @@ def main():
     ap.add_argument("--max-inner", type=int, default=200)
     ap.add_argument("--max-outer", type=int, default=1)
     ap.add_argument("--calls", type=int, default=2)
-    ap.add_argument("--eager", action="store_true", help="host-driven DCT solve (every kernel a host launch)")
+    ap.add_argument("--eager", action="store_true", help="host-driven flexible-CG solve (every kernel a host launch, visible to ncu)")
     a = ap.parse_args()
     w = synth.WORKLOADS[a.workload]
     m = synth.workload_map(a.workload)

@@ -48,21 +48,24 @@ ALG_BYTES = {("f64", "jacobi"): 112, ("f64", "identity"): 96, ("mixed", "jacobi"
              ("f64", "dct"): 146}
 ALG_BYTES[("f64", "learned")] = 146
 ALG_BYTES[("f64", "mg")] = 146
+ALG_BYTES[("mixed", "mg")] = 52
 KERNEL = {("f64", "jacobi"): "k_pcg64", ("f64", "identity"): "k_pcg64", ("mixed", "jacobi"): "k_pcg32",
           ("mixed", "identity"): "k_pcg32", ("f64", "dct"): "flexible-CG graph (k_f_*, k_gemm_nt x4)",
           ("f64", "learned"): "flexible-CG graph (k_f_*, U-Net)",
-          ("f64", "mg"): "flexible-CG graph (k_f_*, multigrid V-cycle)"}
-# Multigrid V-cycle (FP32 grids) HBM bytes per pixel of the map: on the map's grid, r in FP64 to
-# the FP32 right-hand side (12), the fused pre-smoother reads b, D^-1, U, V and writes x (20), the
-# residual/restriction reads x, b, U, V (16 + 1), the first post-smoother reads x, b, U, V, D^-1 and
-# writes t (24 + 1 for the coarse x), the second reads t, b, U, V, D^-1 and writes s in FP64 (28):
-# 102 B/px; the coarser grids (FP32 throughout, 86 B per pixel of each) add a third of 86.
-MG_BYTES_PER_PX = 102.0 + 86.0 / 3.0
+          ("f64", "mg"): "flexible-CG graph (k_f_*, multigrid V-cycle)",
+          ("mixed", "mg"): "mixed flexible-CG graph (k_x_*, multigrid V-cycle)"}
+# Multigrid V-cycle (FP32 grids, one fused walker per grid and direction) HBM bytes per pixel of
+# the map.  Map's grid: the down walker reads U, V, D^-1, b and writes x and the coarse b (21); the
+# up walker reads x, b, U, V, D^-1, the coarse x and the mask (22) and writes s -- in FP64 with the
+# dot phase reading the FP64 r (+16), or in FP32 in the mixed form (+4).  Each coarser grid moves 21
+# down and 25 up per pixel of its own, a third of the map's pixels in all.
+MG_COARSE_PER_PX = (21.0 + 25.0) / 3.0
+MG_BYTES_PER_PX = {"f64": 21.0 + 38.0 + MG_COARSE_PER_PX, "mixed": 21.0 + 26.0 + MG_COARSE_PER_PX}
 # forms compared on each workload: the first is the plain form (the paper's method as written);
 # CHOSEN is the form the workload's configuration is about and that `value` reports
 FORMS = {"c5_2048": [("f64", "jacobi"), ("f64", "dct"), ("f64", "mg"), ("f64", "learned")],
          "c3_4096": [("f64", "jacobi"), ("mixed", "jacobi"), ("f64", "mg")]}
-DEFAULT_FORMS = [("f64", "jacobi"), ("mixed", "jacobi"), ("f64", "dct"), ("f64", "mg")]
+DEFAULT_FORMS = [("f64", "jacobi"), ("mixed", "jacobi"), ("f64", "dct"), ("f64", "mg"), ("mixed", "mg")]
 CHOSEN = {"c5_2048": ("f64", "learned"), "c3_4096": ("mixed", "jacobi")}
 DEFAULT_CHOSEN = ("f64", "mg")
 ORACLE_KIND = {"jacobi": "jacobi", "identity": "identity", "mg": "mg", "dct": "dct", "learned": "jacobi"}
@@ -76,6 +79,10 @@ DTYPE = {"f64": "f64", "mixed": "f32+f64"}
 # DCT the four BF16 GEMMs, 4 Hp Wp (Hp + Wp) flop per application (tensor-bound).
 FCG_BYTES = {"A": 56, "B": 58, "D": 16}
 FCG_KERNEL = {"A": "k_f_a", "B": "k_f_b", "R": "k_f_res", "D": "k_f_dots", "M": "k_gemm_nt x4 (DCT chain)"}
+# mixed flexible CG: A reads s, d_old, U, V and writes d, q in FP32 (24); B reads d, x, q, r, s and
+# writes x, r (28); the dot phase rides on the multigrid cycle's last kernel
+FCG_BYTES_MIXED = {"A": 24, "B": 28, "D": 16}
+FCG_KERNEL_MIXED = {"A": "k_x_a", "B": "k_x_b", "R": "k_x_res", "D": "k_x_dots"}
 
 
 def env_rank():
@@ -337,7 +344,7 @@ def run_ours(args):
                 "peak_source": f"{peak_kind} hbm_gbs", "alg_bytes_per_px_iter": ALG_BYTES[chosen],
                 "solver_ms_per_step": cnt["solver_ms"] / args.steps}
     if chosen[1] in ("dct", "learned", "mg"):
-        roofline = fcg_roofline(native, H, W, psi, mask, w, chosen[1], plan)
+        roofline = fcg_roofline(native, H, W, psi, mask, w, chosen[1], plan, chosen[0])
 
     # end to end: host (pinned) buffers in, host buffer out, inside the timed region
     psi_h = torch.from_numpy(m.psi).pin_memory()
@@ -462,14 +469,17 @@ def learned_net(native, args):
                  "loss_first": losses[0], "loss_last": sum(losses[-20:]) / 20}
 
 
-def fcg_roofline(native, H, W, psi, mask, w, precond, timed_plan):
+def fcg_roofline(native, H, W, psi, mask, w, precond, timed_plan, prec="f64"):
     """Roofline of the dominant kernel of a flexible-CG solve.  Kernels inside the
     solve's graph cannot carry their own events, so the same solve is replayed
     host-driven (options.profile = 2) with an event after every phase; the
     dominant phase (largest summed time) is reported with its algorithmic bytes
     (or, for the DCT chain, tensor flops) per launch over its mean duration."""
     peaks = load_peaks_all()
-    eager = native.Plan(H, W, outer_tol=0.0, profile=2)
+    eager = native.Plan(H, W, outer_tol=0.0, profile=2,
+                        precision=native.ULP_PRECISION_MIXED if prec == "mixed" else 0)
+    fbytes = FCG_BYTES_MIXED if prec == "mixed" else FCG_BYTES
+    fkern = FCG_KERNEL_MIXED if prec == "mixed" else FCG_KERNEL
     if precond == "learned":
         eager.set_unet(timed_plan._unet)
     call = dict(p=w["p"], eps=w["tau"], precond=precond, tol=w["tol"], max_outer=w["max_outer"], stats=False)
@@ -489,25 +499,26 @@ def fcg_roofline(native, H, W, psi, mask, w, precond, timed_plan):
         if n == 0 or ms <= 0:
             continue
         mean_s = ms / n / 1e3
-        kname = FCG_KERNEL[ph]
+        kname = fkern.get(ph, FCG_KERNEL.get(ph))
         if ph == "M" and precond == "learned":
             kname = "k_conv3x3 x7 + U-Net glue"
         elif ph == "M" and precond == "mg":
-            kname = "k_mg_pre/res/post1/post2 per grid + k_mg_coarsest"
+            kname = "k_mg_down/k_mg_up per grid + k_mg_tail (dot phase in the last k_mg_up)"
         ent = {"ms_total": ms, "launches": n, "us_per_launch": mean_s * 1e6, "kernel": kname}
-        if ph in FCG_BYTES:
-            ent.update(bound="hbm", achieved=FCG_BYTES[ph] * H * W / mean_s / 1e9, unit="GB/s",
+        if ph in fbytes:
+            ent.update(bound="hbm", achieved=fbytes[ph] * H * W / mean_s / 1e9, unit="GB/s",
                        peak=peaks["hbm"][0], peak_source=peaks["hbm"][1] + " hbm_gbs",
-                       alg_per_launch=f"{FCG_BYTES[ph]} B/px x {H}x{W}")
+                       alg_per_launch=f"{fbytes[ph]} B/px x {H}x{W}")
         elif ph == "M" and precond == "dct":
             fl = 4.0 * Hp * Wp * (Hp + Wp)
             ent.update(bound="tensor", achieved=fl / mean_s / 1e12, unit="TFLOP/s",
                        peak=peaks["bf16_sust"][0], peak_source=peaks["bf16_sust"][1],
                        alg_per_launch=f"4 Hp Wp (Hp + Wp) = {fl:.3g} flop")
         elif ph == "M" and precond == "mg":
-            ent.update(bound="hbm", achieved=MG_BYTES_PER_PX * H * W / mean_s / 1e9, unit="GB/s",
+            mb = MG_BYTES_PER_PX[prec]
+            ent.update(bound="hbm", achieved=mb * H * W / mean_s / 1e9, unit="GB/s",
                        peak=peaks["hbm"][0], peak_source=peaks["hbm"][1] + " hbm_gbs",
-                       alg_per_launch=f"{MG_BYTES_PER_PX:.0f} B/px x {H}x{W} (V-cycle, all grids)")
+                       alg_per_launch=f"{mb:.0f} B/px x {H}x{W} (V-cycle, all grids)")
         elif ph == "M" and precond == "learned":
             fl = UNET_FLOP_PER_PX * Hp * Wp
             ent.update(bound="tensor", achieved=fl / mean_s / 1e12, unit="TFLOP/s",

@@ -83,7 +83,11 @@ typedef enum {
 typedef enum {
   ULP_PRECISION_FP64 = 0,  /* every vector, weight and reduction in FP64 */
   ULP_PRECISION_MIXED = 1  /* FP32 vectors/weights/stencil, FP64-accurate dot products and
-                              alpha/beta, FP64 phi and true residual every refresh period */
+                              alpha/beta, FP64 phi and true residual every refresh period.
+                              Applies to ULP_PRECOND_IDENTITY, ULP_PRECOND_JACOBI (persistent
+                              PCG) and ULP_PRECOND_MG (flexible CG, FP32 V-cycle; a stop seen
+                              on the FP32 recurrence is confirmed on the FP64 true residual);
+                              other preconditioners return ULP_ERR_UNSUPPORTED */
 } ulp_precision;
 
 typedef enum {

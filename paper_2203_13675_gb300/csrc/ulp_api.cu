@@ -459,8 +459,8 @@ extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precon
   int rc = check_solver_args(precond, tol, max_outer);
   if (rc != ULP_OK) return rc;
   const bool mixed = pl.opt.precision == ULP_PRECISION_MIXED;
-  if (mixed && precond != ULP_PRECOND_IDENTITY && precond != ULP_PRECOND_JACOBI)
-    return fail(ULP_ERR_UNSUPPORTED, "mixed precision supports the identity and Jacobi preconditioners");
+  if (mixed && precond != ULP_PRECOND_IDENTITY && precond != ULP_PRECOND_JACOBI && precond != ULP_PRECOND_MG)
+    return fail(ULP_ERR_UNSUPPORTED, "mixed precision supports the identity, Jacobi and multigrid preconditioners");
   if (precond == ULP_PRECOND_DCT && (pl.nmaps != 1 || !pl.dct))
     return fail(ULP_ERR_UNSUPPORTED, "the DCT preconditioner is available on single-map plans");
   if (precond == ULP_PRECOND_MG && (pl.nmaps != 1 || !pl.mg))

@@ -159,6 +159,7 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
   v2 = cnt > 2 ? warp_sum(v2) : 0.0;
   if (lane == 0) {
     bool done = false;
+    bool refreshed = true;  // r is the true residual (mixed flexible CG: this iteration recomputed it)
     if (ph == kPhA) {
       S->dq = v0;
       if ((!(v0 > 0.0) || !isfinite(v0)) && a.learned && !S->fallback) {
@@ -185,6 +186,7 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
         S->stall = 0;
       } else if (ph == kPhFcg) {
         // flexible CG (Polak-Ribiere): beta = r_{k+1}^T (s_{k+1} - s_k) / (r_k^T s_k), v2 = r_{k+1}^T s_k
+        refreshed = (S->iter % M.refresh) == 0 || S->force_refresh;
         const double dold = S->delta;
         S->delta = v0;
         S->rr = v1;
@@ -215,8 +217,15 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
       if (S->stop_after) {
         done = true;
       } else if (S->bb == 0.0 || conv) {
-        done = true;
-        S->status = 0;
+        if (ph == kPhFcg && a.xfcg && !refreshed && S->bb != 0.0) {
+          // the FP32 recurrence says converged: from here on every iteration recomputes the
+          // true residual, and the solve stops on that (a single confirmation that lands just
+          // above the tolerance would otherwise cost two iterations per attempt)
+          S->force_refresh = 1;
+        } else {
+          done = true;
+          S->status = 0;
+        }
       } else if (S->iter >= (a.lmax > 0 ? a.lmax : 2LL * M.H * M.W)) {
         done = true;
         S->status = 1;

@@ -18,7 +18,7 @@
 //                 D: r^T s, r^T r -> beta, stop test, WHILE condition
 #include <cuda_bf16.h>
 
-#include "ulp_engine.cuh"
+#include "ulp_mixed.cuh"
 
 #include "ulp_host.h"
 
@@ -218,6 +218,176 @@ __global__ void __launch_bounds__(kThreads, 2) k_f_dots(const PcgArgs* pa, int i
   }
 }
 
+// ---------------------------------------------------------------- mixed flexible CG
+// The multigrid solve with the precision split of the mixed form: the Krylov
+// recurrence (d, q = A d, r, s and the correction x since the last refresh) on
+// FP32 planes with FP32 weights, the inner products as double-float sums of
+// exact FP32 products, alpha, beta and the stop tests in FP64, and phi in FP64:
+// every refresh period the correction is folded into phi and r = b - A phi is
+// recomputed with the FP64 weights.  The multigrid cycle
+// reads r directly (its FP32 right-hand side is the recurrence's r plane) and
+// writes s in FP32.  Once the recurrence reports convergence, every remaining
+// iteration is a refresh iteration, so the solve stops on a true residual.
+//   A: d = s + beta d, q = A d, d^T q  (the mixed engine's phase A)
+//   B: x += alpha d; r -= alpha q and r_{k+1}^T s_k, or on refresh iterations phi += x, x = 0
+//   R: on refresh iterations r = b - A phi (FP64, rounded to FP32) and r_{k+1}^T s_k
+//   M: the V-cycle, whose last kernel also runs the dot phase
+
+__device__ __forceinline__ bool x_refresh(const MapDesc& M, MapState* S) {
+  const long long it = *(volatile long long*)&S->iter;
+  return (it % M.refresh) == 0 || *(volatile int*)&S->force_refresh;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_x_a(const PcgArgs* pa) {
+  const PcgArgs a = *pa;
+  FCG_TILE_LOOP(a) {
+    if (*(volatile int*)&S->done) return;
+    a32_tile<kJacobi>(a, M, S, t, lane);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_x_b(const PcgArgs* pa) {
+  const PcgArgs a = *pa;
+  FCG_TILE_LOOP(a) {
+    if (*(volatile int*)&S->done) return;
+    const bool refresh = x_refresh(M, S);
+    const long long it = *(volatile long long*)&S->iter;
+    const TileGeo g = tile_geo(M, t, a.R);
+    const size_t P = M.pitch;
+    const float* __restrict__ d = (it & 1) ? M.h.d0 : M.h.d1;
+    const float alpha = (float)*(volatile double*)&S->alpha;
+    const int j = g.j0 + 2 * lane;
+    DF rsp;
+    // rows in groups of four, all loads of a group issued before its stores
+    for (int i = g.i0; i < g.i1; i += 4) {
+      float2 dv[4], xv[4], qv[4], rv[4], sv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (i + k < g.i1) {
+          const size_t off = (size_t)(i + k) * P + j;
+          dv[k] = ldf2(d, off);
+          xv[k] = ldf2(M.h.x, off);
+          if (!refresh) {
+            qv[k] = ldf2(M.h.q, off);
+            rv[k] = ldf2(M.h.r, off);
+            sv[k] = ldf2(M.h.s, off);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (i + k < g.i1) {
+          const size_t off = (size_t)(i + k) * P + j;
+          float2 x = xv[k];
+          x.x = __fmaf_rn(alpha, dv[k].x, x.x);
+          x.y = __fmaf_rn(alpha, dv[k].y, x.y);
+          if (refresh) {
+            double2 ph = ld2(M.f.phi, off);
+            ph.x += (double)x.x;
+            ph.y += (double)x.y;
+            st2(M.f.phi, off, ph);
+            stf2(M.h.x, off, make_float2(0.f, 0.f));
+          } else {
+            stf2(M.h.x, off, x);
+            float2 r = rv[k];
+            r.x = __fmaf_rn(-alpha, qv[k].x, r.x);
+            r.y = __fmaf_rn(-alpha, qv[k].y, r.y);
+            stf2(M.h.r, off, r);
+            rsp.add_prod(r.x, sv[k].x);
+            rsp.add_prod(r.y, sv[k].y);
+          }
+        }
+      }
+    }
+    if (!refresh) {
+      const double v = warp_sum(rsp.value());
+      if (lane == 0) __stcg(a.P2 + t, v);
+    }
+  }
+}
+
+// r = b - A phi in FP64, rounded to FP32 (x = 0 with it at the start); on refresh
+// iterations also r_{k+1}^T s_k.
+__global__ void __launch_bounds__(kThreads, 2) k_x_res(const PcgArgs* pa, int init) {
+  const PcgArgs a = *pa;
+  FCG_TILE_LOOP(a) {
+    if (*(volatile int*)&S->done) return;
+    if (!init && !x_refresh(M, S)) return;
+    const TileGeo g = tile_geo(M, t, a.R);
+    XPlane x{M.f.phi, (size_t)M.pitch};
+    DF rsp;
+    auto epi = [&](size_t off, double2, double2 ax) {
+      const double2 bv = ld2(M.f.b, off);
+      const float2 r = make_float2((float)(bv.x - ax.x), (float)(bv.y - ax.y));
+      stf2(M.h.r, off, r);
+      if (init) {
+        stf2(M.h.x, off, make_float2(0.f, 0.f));
+      } else {
+        const float2 sv = ldf2(M.h.s, off);
+        rsp.add_prod(r.x, sv.x);
+        rsp.add_prod(r.y, sv.y);
+      }
+    };
+    stencil_tile(M, g.i0, g.i1, g.j0, lane, M.f.U, M.f.V, M.f.D, x, epi);
+    if (!init) {
+      const double v = warp_sum(rsp.value());
+      if (lane == 0) __stcg(a.P2 + t, v);
+    }
+  }
+}
+
+// r^T s, r^T r (double-float) and, at the start of the solve, b^T b (FP64) -> delta, beta,
+// stop test (used where the multigrid cycle cannot carry the dot phase)
+__global__ void __launch_bounds__(kThreads, 2) k_x_dots(const PcgArgs* pa, int init) {
+  const PcgArgs a = *pa;
+  FCG_TILE_LOOP(a) {
+    if (*(volatile int*)&S->done) return;
+    const TileGeo g = tile_geo(M, t, a.R);
+    const size_t P = M.pitch;
+    const int j = g.j0 + 2 * lane;
+    DF rs, rr;
+    double bb = 0.0;
+    for (int i = g.i0; i < g.i1; ++i) {
+      const size_t off = (size_t)i * P + j;
+      const float2 rv = ldf2(M.h.r, off), sv = ldf2(M.h.s, off);
+      rs.add_prod(rv.x, sv.x);
+      rs.add_prod(rv.y, sv.y);
+      rr.add_prod(rv.x, rv.x);
+      rr.add_prod(rv.y, rv.y);
+      if (init) {
+        const double2 bv = ld2(M.f.b, off);
+        bb = fma(bv.x, bv.x, bb);
+        bb = fma(bv.y, bv.y, bb);
+      }
+    }
+    tile_arrive(a, M, S, t, init ? kPhResInit : kPhFcg, rs.value(), rr.value(), bb, lane);
+  }
+}
+
+// end of the solve: phi += x (zero after a confirmed stop; not after l_max or a breakdown)
+__global__ void __launch_bounds__(kThreads) k_x_fold(const PcgArgs* pa) {
+  const PcgArgs a = *pa;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int NW = gridDim.x * (blockDim.x >> 5);
+  const MapDesc& M = a.maps[0];
+  if (!a.st->outer_active) return;
+  for (int t = gw; t < a.ntiles; t += NW) {
+    const TileGeo g = tile_geo(M, t, a.R);
+    const size_t P = M.pitch;
+    const int j = g.j0 + 2 * lane;
+    for (int i = g.i0; i < g.i1; ++i) {
+      const size_t off = (size_t)i * P + j;
+      const float2 xv = ldf2(M.h.x, off);
+      double2 ph = ld2(M.f.phi, off);
+      ph.x += (double)xv.x;
+      ph.y += (double)xv.y;
+      st2(M.f.phi, off, ph);
+      stf2(M.h.x, off, make_float2(0.f, 0.f));
+    }
+  }
+}
+
 // Learned preconditioner's fallback: s = D^-1 r once the map's fallback flag is
 // set (the network kernels skip themselves from then on).
 __global__ void __launch_bounds__(kThreads) k_f_jacobi(const PcgArgs* pa) {
@@ -242,11 +412,18 @@ static int tile_blocks(const Plan& pl) { return (pl.ntiles + kWarps - 1) / kWarp
 
 // s = M^-1 r of the flexible solve: the DCT chain, or the network followed by its
 // Jacobi fallback (only one of the two does work in any iteration).
+// the mixed flexible CG runs for the multigrid preconditioner on mixed-precision plans
+static bool mixed_fcg(const Plan& pl, int kind) {
+  return kind == ULP_PRECOND_MG && pl.opt.precision == ULP_PRECISION_MIXED;
+}
+
 // With fuse_dots the multigrid cycle's last kernel also runs the dot phase D.
 static cudaError_t fcg_precond(Plan& pl, int kind, cudaStream_t st, bool fuse_dots = false) {
   const MapDesc& M = pl.hmaps[0];
   if (kind == ULP_PRECOND_DCT) return dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st, true);
-  if (kind == ULP_PRECOND_MG) return mg_apply(*pl.mg, M.f.mask, pl.dstate, st, true, fuse_dots ? pl.dargs : nullptr);
+  if (kind == ULP_PRECOND_MG)
+    return mg_apply(*pl.mg, M.f.mask, pl.dstate, st, true, fuse_dots ? pl.dargs : nullptr,
+                    mixed_fcg(pl, kind) ? M.h.s : nullptr);
   if (kind == ULP_PRECOND_RBSSOR || kind == ULP_PRECOND_RBILU) return rb_apply(pl, kind, pl.dstate, st);
   const cudaError_t e = unet_apply_plane(*pl.unet, M.f.r, M.f.U, M.f.V, M.f.mask, M.H, M.W, M.pitch, M.f.s,
                                          &pl.dstate[0].fallback, st);
@@ -259,6 +436,14 @@ static cudaError_t fcg_precond(Plan& pl, int kind, cudaStream_t st, bool fuse_do
 static cudaError_t fcg_start(Plan& pl, int kind, cudaStream_t st) {
   const MapDesc& M = pl.hmaps[0];
   const int nb = tile_blocks(pl);
+  if (mixed_fcg(pl, kind)) {
+    k_x_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = mg_setup(*pl.mg, pl.dstate, st);
+    if (e == cudaSuccess) e = fcg_precond(pl, kind, st);
+    k_x_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+    return e == cudaSuccess ? cudaGetLastError() : e;
+  }
   k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && kind == ULP_PRECOND_DCT) e = dct_prepare_mask(*pl.dct, M.f.mask, M.pitch, st);
@@ -276,6 +461,15 @@ static bool fused_dots(const Plan& pl, int kind) { return kind == ULP_PRECOND_MG
 static cudaError_t fcg_iteration(Plan& pl, int kind, cudaStream_t st) {
   const int nb = tile_blocks(pl);
   const bool fd = fused_dots(pl, kind);
+  if (mixed_fcg(pl, kind)) {
+    k_x_a<<<nb, kThreads, 0, st>>>(pl.dargs);
+    k_x_b<<<nb, kThreads, 0, st>>>(pl.dargs);
+    k_x_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = fcg_precond(pl, kind, st, fd);
+    if (!fd) k_x_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
+    return e == cudaSuccess ? cudaGetLastError() : e;
+  }
   k_f_a<<<nb, kThreads, 0, st>>>(pl.dargs);
   k_f_b<<<nb, kThreads, 0, st>>>(pl.dargs);
   k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
@@ -323,6 +517,10 @@ static cudaError_t fcg_build(Plan& pl, int kind) {
     e = cudaGraphAddNode(&cn, g, deps, nullptr, ndeps, &cp);
   }
   if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(st, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e == cudaSuccess && mixed_fcg(pl, kind)) {
+    k_x_fold<<<tile_blocks(pl), kThreads, 0, st>>>(pl.dargs);
+    e = cudaGetLastError();
+  }
   cudaGraph_t gout = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(st, &gout);
   if (e == cudaSuccess) e = e2;
@@ -359,7 +557,43 @@ static cudaError_t fcg_build(Plan& pl, int kind) {
 // Host-driven form of the same solve (options.profile = 2): every kernel is a
 // host launch, so a profiler sees each one; the host reads the stop flag after
 // every iteration.  For measurement only.
+static cudaError_t fcg_eager_mixed(Plan& pl, int kind, cudaStream_t st) {
+  const int nb = tile_blocks(pl);
+  const bool fd = fused_dots(pl, kind);
+  cudaError_t e = cudaSuccess;
+  phase_mark(pl, st, -1);
+  k_x_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+  phase_mark(pl, st, 2);
+  if ((e = mg_setup(*pl.mg, pl.dstate, st)) != cudaSuccess) return e;
+  if ((e = fcg_precond(pl, kind, st)) != cudaSuccess) return e;
+  phase_mark(pl, st, 3);
+  k_x_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+  phase_mark(pl, st, 4);
+  for (long long l = 0;; ++l) {
+    int done = 0;
+    if ((e = cudaMemcpyAsync(&done, &pl.dstate->done, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    if (done || l > (1LL << 24)) break;
+    phase_mark(pl, st, -1);
+    k_x_a<<<nb, kThreads, 0, st>>>(pl.dargs);
+    phase_mark(pl, st, 0);
+    k_x_b<<<nb, kThreads, 0, st>>>(pl.dargs);
+    phase_mark(pl, st, 1);
+    k_x_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
+    phase_mark(pl, st, 2);
+    if ((e = fcg_precond(pl, kind, st, fd)) != cudaSuccess) return e;
+    phase_mark(pl, st, 3);
+    if (!fd) {
+      k_x_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
+      phase_mark(pl, st, 4);
+    }
+  }
+  k_x_fold<<<nb, kThreads, 0, st>>>(pl.dargs);
+  return cudaGetLastError();
+}
+
 static cudaError_t fcg_eager(Plan& pl, int kind, cudaStream_t st) {
+  if (mixed_fcg(pl, kind)) return fcg_eager_mixed(pl, kind, st);
   const MapDesc& M = pl.hmaps[0];
   const int nb = tile_blocks(pl);
   cudaError_t e = cudaSuccess;
@@ -412,7 +646,8 @@ cudaError_t launch_fcg(Plan& pl, int kind, const PcgArgs& a_in, cudaStream_t st,
   a.rbf_ld = 0;
   a.rf32 = nullptr;
   if (kind == ULP_PRECOND_DCT) a.rbf = dct_input(*pl.dct, &a.rbf_ld);
-  if (kind == ULP_PRECOND_MG) a.rf32 = mg_input(*pl.mg);
+  a.xfcg = mixed_fcg(pl, kind);
+  if (kind == ULP_PRECOND_MG && !a.xfcg) a.rf32 = mg_input(*pl.mg);
   a.learned = kind == ULP_PRECOND_LEARNED;
   if (pl.opt.profile == 2) {
     a.cond = 0;

@@ -522,6 +522,7 @@ __global__ void k_pcg_reset(MapState* S, int nmaps, int* n_active, Barrier* bar)
     s->fallback = 0;
     s->restart = 0;
     s->stall = 0;
+    s->force_refresh = 0;
     s->rr_best = 0.0;
     if (act) atomicAdd(&s_cnt, 1);
   }

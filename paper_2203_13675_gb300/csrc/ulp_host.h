@@ -110,8 +110,9 @@ cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st);  // c
 // packed: the FP32 copy of r (mg_input, the map's pitch) is already written; dots (device
 // arguments of a flexible-CG solve, or null): the cycle's last kernel also does the solve's
 // dot phase (r^T s, r^T r, beta, stop test), if mg_fuses_dots
+// s32 (or null): s is written in FP32 there instead of the map's FP64 s plane (the mixed flexible CG)
 cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st, bool packed = false,
-                     const PcgArgs* dots = nullptr);
+                     const PcgArgs* dots = nullptr, float* s32 = nullptr);
 bool mg_fuses_dots(const MgPlan& p);
 float* mg_input(const MgPlan& p);
 int mg_levels(const MgPlan& p);

@@ -76,7 +76,7 @@ struct MapState {
   int fallback;             // 1: s = D^-1 r from now on in this solve
   int restart;              // 1: the next beta is 0
   int stall;                // iterations since rr last fell below 0.99 rr_best
-  int pad_;
+  int force_refresh;        // mixed flexible CG: every further iteration recomputes the true residual
   double rr_best;
 };
 
@@ -117,6 +117,8 @@ struct PcgArgs {
   float* rf32;              // flexible-CG graph: FP32 copy of r (the multigrid's right-hand side), or null
   int learned;              // flexible CG with the learned preconditioner: stall / breakdown fall back to Jacobi
   int stall_window;
+  int xfcg;                 // mixed flexible CG: convergence of the FP32 recurrence is confirmed on the
+                            // FP64 true residual before the solve stops
 };
 
 // ------------------------------------------------------------------ helpers

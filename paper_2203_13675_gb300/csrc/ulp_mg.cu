@@ -26,7 +26,7 @@
 // FP32 rounding.
 #include <vector>
 
-#include "ulp_engine.cuh"
+#include "ulp_mixed.cuh"
 #include "ulp_host.h"
 
 namespace ulp {
@@ -521,13 +521,17 @@ __device__ __forceinline__ UpRow up_row(const Grid& f, const Grid& c, const floa
 }
 
 // prolongation + correction + both post-sweeps for the rows [R band, R band + R).
-// xc: the coarse grid's corrected solution.  MAP (the map's grid): s in FP64; with pa,
-// r^T s and r^T r (r: the map's FP64 residual) over the warp's pixels arrive in the
-// flexible CG's dot phase.
-template <bool MAP>
+// xc: the coarse grid's corrected solution.  MODE kUpCoarse: s to the grid's t plane.
+// kUp64 (the map's grid): s in FP64; with pa, r^T s and r^T r (r: the map's FP64
+// residual) over the warp's pixels arrive in the flexible CG's dot phase.  kUp32 (the
+// map's grid, mixed flexible CG): s in FP32 into s32; with pa, the same dot phase in
+// double-float sums of exact FP32 products, r being the cycle's right-hand side.
+enum { kUpCoarse = 0, kUp64 = 1, kUp32 = 2 };
+template <int MODE>
 __global__ void __launch_bounds__(256, 2) k_mg_up(Grid f, Grid c, const float* __restrict__ xc, int R,
                                                   const uint8_t* mask, double* s, const double* __restrict__ rv,
-                                                  const PcgArgs* pa, const MapState* S) {
+                                                  float* s32, const PcgArgs* pa, const MapState* S) {
+  constexpr bool MAP = MODE != kUpCoarse;
   if (skip_map(S)) return;
   int seg, band, j, lane;
   const int bands = (f.H + R - 1) / R;
@@ -538,6 +542,7 @@ __global__ void __launch_bounds__(256, 2) k_mg_up(Grid f, Grid c, const float* _
   float4 Um1 = z, Um2 = z, Vm1 = z, Vm2 = z, Vm3 = z, Dm1 = z, Dm2 = z, Bm1 = z, Bm2 = z;
   float4 XPm1 = z, XPm2 = z, Tm2 = z, Tm3 = z;
   double rs = 0.0, rr = 0.0;
+  DF rs32, rr32;
   UpRow nx = up_row<MAP>(f, c, xc, mask, rv, i0 - 2, j);
   for (int r = i0 - 2; r <= i1 + 1; ++r) {
     const UpRow cu = nx;
@@ -552,8 +557,25 @@ __global__ void __launch_bounds__(256, 2) k_mg_up(Grid f, Grid c, const float* _
     if (p >= i0 && p < i1) {
       const float4 v = jac4(Tm2, Dm2, Bm2, arow(Tm3, Tm2, T, Um2, Vm2, Vm3, lane));
       const size_t o = (size_t)p * f.ld + j;
-      if (!MAP) {
+      if (MODE == kUpCoarse) {
         if (out) *reinterpret_cast<float4*>(f.t + o) = v;
+      } else if (MODE == kUp32) {
+        if (out) {
+          const uchar4 mk = cu.mk;
+          const float4 sv = make_float4(mk.x ? 0.f : v.x, mk.y ? 0.f : v.y, mk.z ? 0.f : v.z, mk.w ? 0.f : v.w);
+          *reinterpret_cast<float4*>(s32 + o) = sv;
+          if (pa) {
+            // r is the cycle's right-hand side (zero beyond column W - 1, as is s there)
+            rs32.add_prod(Bm2.x, sv.x);
+            rs32.add_prod(Bm2.y, sv.y);
+            rs32.add_prod(Bm2.z, sv.z);
+            rs32.add_prod(Bm2.w, sv.w);
+            rr32.add_prod(Bm2.x, Bm2.x);
+            rr32.add_prod(Bm2.y, Bm2.y);
+            rr32.add_prod(Bm2.z, Bm2.z);
+            rr32.add_prod(Bm2.w, Bm2.w);
+          }
+        }
       } else if (out) {
         // the map's grid: FP64 s, 0 on masked pixels and nothing beyond column W - 1
         const uchar4 mk = cu.mk;
@@ -588,7 +610,20 @@ __global__ void __launch_bounds__(256, 2) k_mg_up(Grid f, Grid c, const float* _
   if (MAP && pa) {
     const PcgArgs a = *pa;
     const int nseg = (f.W + kSegOut - 1) / kSegOut;
+    if (MODE == kUp32) {
+      rs = rs32.value();
+      rr = rr32.value();
+    }
     warp_arrive_fcg(a, a.maps[0], a.st, band * nseg + seg, nseg * bands, rs, rr, lane);
+  }
+}
+
+// level 0 without a walker (grids narrower than 64 columns): the FP64 s rounded to FP32
+__global__ void k_mg_to32(const double* __restrict__ s, float* s32, Grid g, const MapState* S) {
+  if (skip_map(S)) return;
+  MG_LOOP(t, (long long)g.H * g.W) {
+    const size_t o = (size_t)(t / g.W) * g.ld + (t % g.W);
+    s32[o] = (float)s[o];
   }
 }
 
@@ -764,7 +799,7 @@ static size_t fbytes(size_t elems) { return (elems * 4 + 255) & ~(size_t)255; }
 
 size_t mg_bytes(int H, int W) {
   const int pitch = (W + 63) / 64 * 64;
-  size_t bytes = 6 * fbytes((size_t)H * pitch);
+  size_t bytes = 2 * fbytes((size_t)H * pitch);  // x, t of the map's grid (U, V, D^-1, b are the map's FP32 planes)
   int h = H, w = W;
   while ((long long)h * w > kCoarseMax) {
     h = (h + 1) / 2;
@@ -804,11 +839,13 @@ MgPlan* mg_create(const MapDesc& M, void* mem, int nsm, int ntiles) {
   g0.W = M.W;
   g0.ld = M.pitch;
   const size_t n0 = (size_t)M.H * M.pitch;
-  g0.U = take(n0);
-  g0.V = take(n0);
-  g0.Dinv = take(n0);
+  // the map's grid uses the map's FP32 planes for its weights, D^-1 and right-hand side
+  // (the FP32 residual of the mixed flexible CG is the cycle's input as it stands)
+  g0.U = M.h.U;
+  g0.V = M.h.V;
+  g0.Dinv = M.h.Dinv;
+  g0.b = M.h.r;
   g0.x = take(n0);
-  g0.b = take(n0);
   g0.t = take(n0);
   p->g.push_back(g0);
   while ((long long)p->g.back().H * p->g.back().W > kCoarseMax) {
@@ -898,13 +935,14 @@ static unsigned walk_blocks(const Grid& f, int rows, int R) {
 }
 
 cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st, bool packed,
-                     const PcgArgs* dots) {
+                     const PcgArgs* dots, float* s32) {
   const int L = (int)p.g.size();
   const Grid& g0 = p.g[0];
   if (!packed) k_mg_rhs_v<<<mg_blocks(p, (long long)g0.H * ((g0.W + 3) / 4)), 256, 0, st>>>(p.r0, g0, S);
   if (L == 1) {
     k_mg_coarsest<<<1, 256, 0, st>>>(g0, S);
     k_mg_post2<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(g0, mask, p.s0, S);
+    if (s32) k_mg_to32<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(p.s0, s32, g0, S);
     return cudaGetLastError();
   }
   const int stop = p.lt > 0 ? p.lt : L - 1;  // grids [0, stop) by per-grid kernels
@@ -940,12 +978,17 @@ cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cu
       const Grid& c = p.g[l + 1];
       const float* xc = (l + 1 < stop && p.walk_r[l + 1] > 0) ? c.t : c.x;
       const int R = p.walk_r[l];
-      if (l == 0) {
+      if (l == 0 && s32) {
         const bool d = dots && p.dots_warps > 0;
-        k_mg_up<true><<<walk_blocks(f, f.H, R), 256, 0, st>>>(f, c, xc, R, mask, p.s0, d ? p.r0 : nullptr,
-                                                              d ? dots : nullptr, S);
+        k_mg_up<kUp32><<<walk_blocks(f, f.H, R), 256, 0, st>>>(f, c, xc, R, mask, nullptr, nullptr, s32,
+                                                               d ? dots : nullptr, S);
+      } else if (l == 0) {
+        const bool d = dots && p.dots_warps > 0;
+        k_mg_up<kUp64><<<walk_blocks(f, f.H, R), 256, 0, st>>>(f, c, xc, R, mask, p.s0, d ? p.r0 : nullptr,
+                                                               nullptr, d ? dots : nullptr, S);
       } else {
-        k_mg_up<false><<<walk_blocks(f, f.H, R), 256, 0, st>>>(f, c, xc, R, nullptr, nullptr, nullptr, nullptr, S);
+        k_mg_up<kUpCoarse><<<walk_blocks(f, f.H, R), 256, 0, st>>>(f, c, xc, R, nullptr, nullptr, nullptr,
+                                                                   nullptr, nullptr, S);
       }
     } else if (f.W >= kVecMinW) {
       k_mg_sweep_v<kSrcXP><<<row_blocks(f, f.H), 256, 0, st>>>(f, p.g[l + 1], f.t, nullptr, nullptr, S);
@@ -957,6 +1000,8 @@ cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cu
                                                                     l == 0 ? p.s0 : nullptr, S);
     }
   }
+  if (s32 && !(p.walk_r[0] > 0 && stop > 0))
+    k_mg_to32<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(p.s0, s32, g0, S);
   return cudaGetLastError();
 }
 

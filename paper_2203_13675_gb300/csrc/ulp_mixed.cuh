@@ -1,0 +1,163 @@
+// ulp_mixed.cuh -- FP32 pieces of the mixed-precision solvers shared by the
+// persistent reliable-update PCG (ulp_mixed.cu) and the mixed flexible CG
+// (ulp_fcg.cu): double-float accumulation of FP32 products, the FP32
+// sliding-window stencil, and phase A (d = s + beta d, q = A d, d^T q).
+#pragma once
+#include "ulp_engine.cuh"
+
+namespace ulp {
+
+// Double-float accumulator of FP32 products: a*b = p + e exactly (FMA), and
+// the running sum is carried as hi + lo with Knuth's two-sum.
+struct DF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ float2 ldf2(const float* base, size_t off) {
+  return __ldcg(reinterpret_cast<const float2*>(base + off));
+}
+__device__ __forceinline__ void stf2(float* base, size_t off, float2 v) {
+  __stcg(reinterpret_cast<float2*>(base + off), v);
+}
+
+struct XDir32 {  // d = s + beta d_old (FP32), d = s on the first iteration
+  const float* s;
+  const float* dold;
+  float beta;
+  bool first;
+  size_t P;
+  struct Raw {
+    float2 s, d;
+  };
+  __device__ __forceinline__ static Raw zero() { return Raw{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+  __device__ __forceinline__ Raw load(int i, int j) const {
+    const size_t off = (size_t)i * P + j;
+    Raw r;
+    r.s = ldf2(s, off);
+    r.d = first ? make_float2(0.f, 0.f) : ldf2(dold, off);
+    return r;
+  }
+  __device__ __forceinline__ float2 make(const Raw& r) const {
+    if (first) return r.s;
+    return make_float2(__fmaf_rn(beta, r.d.x, r.s.x), __fmaf_rn(beta, r.d.y, r.s.y));
+  }
+  __device__ __forceinline__ float at(int i, int c) const {
+    const size_t off = (size_t)i * P + c;
+    const float sv = __ldcg(s + off);
+    return first ? sv : __fmaf_rn(beta, __ldcg(dold + off), sv);
+  }
+};
+
+// FP32 sliding-window stencil (same tiling as the FP64 walker), summed over the
+// edges as w (x_i - x_j) from the FP32 weights: the FP32 operator keeps A 1 = 0
+// exactly, and for the smooth directions of a well-preconditioned solve its error
+// stays relative to |A x| rather than to |A| |x|.  FP32 rows move half the bytes of FP64
+// ones, so loads run two rows ahead of the arithmetic to keep enough in flight.
+template <class X, class Epi>
+__device__ __forceinline__ void stencil_tile32(const MapDesc& M, int i0, int i1, int j0, int lane,
+                                               const float* U, const float* V, const X& x, Epi& epi) {
+  using Raw = typename X::Raw;
+  const int j = j0 + 2 * lane;
+  const bool hw = (lane == 0) && (j0 > 0);
+  const bool he = (lane == 31) && (j0 + kStrip < M.pitch);
+  const bool halo = hw || he;
+  const int hc = (lane == 0) ? j0 - 1 : j0 + kStrip;
+  const size_t P = (size_t)M.pitch;
+  const float2 z2 = make_float2(0.f, 0.f);
+  float2 xn = z2, vn = z2;
+  if (i0 > 0) {
+    xn = x.make(x.load(i0 - 1, j));
+    vn = ldf2(V, (size_t)(i0 - 1) * P + j);
+  }
+  float2 xc = x.make(x.load(i0, j));
+  // raw x of rows i+1, i+2; weights and halo of rows i, i+1
+  Raw r1 = (i0 + 1 < M.H) ? x.load(i0 + 1, j) : X::zero();
+  Raw r2 = (i0 + 2 < M.H && i0 + 1 < i1) ? x.load(i0 + 2, j) : X::zero();
+  size_t off = (size_t)i0 * P + j;
+  float2 u0 = ldf2(U, off), v0 = ldf2(V, off), u1 = z2, v1 = z2;
+  float h0 = halo ? x.at(i0, hc) : 0.f, h1 = 0.f;
+  float w0 = hw ? __ldcg(U + off - j + hc) : 0.f, w1 = 0.f;
+  if (i0 + 1 < i1) {
+    u1 = ldf2(U, off + P);
+    v1 = ldf2(V, off + P);
+    if (halo) h1 = x.at(i0 + 1, hc);
+    if (hw) w1 = __ldcg(U + off + P - j + hc);
+  }
+  for (int i = i0; i < i1; ++i) {
+    // issue the loads two rows ahead
+    Raw r3 = (i + 3 < M.H && i + 2 < i1) ? x.load(i + 3, j) : X::zero();
+    float2 u2 = z2, v2 = z2;
+    float h2 = 0.f, w2 = 0.f;
+    if (i + 2 < i1) {
+      const size_t o2 = off + 2 * P;
+      u2 = ldf2(U, o2);
+      v2 = ldf2(V, o2);
+      if (halo) h2 = x.at(i + 2, hc);
+      if (hw) w2 = __ldcg(U + o2 - j + hc);
+    }
+    const float2 xs = (i + 1 < M.H) ? x.make(r1) : z2;
+    float west = __shfl_up_sync(kFull, xc.y, 1);
+    float east = __shfl_down_sync(kFull, xc.x, 1);
+    float uw = __shfl_up_sync(kFull, u0.y, 1);
+    if (lane == 0) { west = h0; uw = w0; }
+    if (lane == 31) east = h0;
+    // sum over the four edges of w (x_i - x_j): the neighbour differences are nearly
+    // exact for a smooth x, where D x_i - sum w x_j would cancel to a few bits
+    float2 ax;
+    ax.x = __fmul_rn(u0.x, __fsub_rn(xc.x, xc.y));
+    ax.x = __fmaf_rn(uw, __fsub_rn(xc.x, west), ax.x);
+    ax.x = __fmaf_rn(vn.x, __fsub_rn(xc.x, xn.x), ax.x);
+    ax.x = __fmaf_rn(v0.x, __fsub_rn(xc.x, xs.x), ax.x);
+    ax.y = __fmul_rn(u0.y, __fsub_rn(xc.y, east));
+    ax.y = __fmaf_rn(u0.x, __fsub_rn(xc.y, xc.x), ax.y);
+    ax.y = __fmaf_rn(vn.y, __fsub_rn(xc.y, xn.y), ax.y);
+    ax.y = __fmaf_rn(v0.y, __fsub_rn(xc.y, xs.y), ax.y);
+    epi(off, xc, ax);
+    xn = xc;
+    xc = xs;
+    vn = v0;
+    r1 = r2;
+    r2 = r3;
+    u0 = u1;
+    v0 = v1;
+    u1 = u2;
+    v1 = v2;
+    h0 = h1;
+    h1 = h2;
+    w0 = w1;
+    w1 = w2;
+    off += P;
+  }
+}
+
+// d = s + beta d_old, q = A d in FP32, d^T q FP64-accurate.
+template <int KIND>
+__device__ __forceinline__ void a32_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t, int lane) {
+  const TileGeo g = tile_geo(M, t, a.R);
+  const long long it = *(volatile long long*)&S->iter;
+  const float* sv = (KIND == kIdentity) ? M.h.r : M.h.s;
+  const float* dold = (it & 1) ? M.h.d1 : M.h.d0;
+  float* dnew = (it & 1) ? M.h.d0 : M.h.d1;
+  XDir32 x{sv, dold, (float)*(volatile double*)&S->beta, it == 0, (size_t)M.pitch};
+  DF dq;
+  auto epi = [&](size_t off, float2 xc, float2 ax) {
+    stf2(dnew, off, xc);
+    stf2(M.h.q, off, ax);
+    dq.add_prod(xc.x, ax.x);
+    dq.add_prod(xc.y, ax.y);
+  };
+  stencil_tile32(M, g.i0, g.i1, g.j0, lane, M.h.U, M.h.V, x, epi);
+  tile_arrive(a, M, S, t, kPhA, dq.value(), 0.0, 0.0, lane);
+}
+
+}  // namespace ulp

@@ -75,3 +75,48 @@ def test_mg_pcg_step_entry_point():
     ref, rst = oracle.pcg(A, np.zeros((H, W)), kind=oracle.M_MG, tol=1e-8)
     assert abs(st["inner"][0] - rst["iters"]) <= 3, (st, rst)
     assert _rms(phi.cpu().numpy(), ref) < 1e-6
+
+
+# Mixed flexible CG with the multigrid cycle: FP32 recurrence and V-cycle, FP64
+# inner products, phi and true residual.  Its iterates follow the FP64 solve to
+# FP32 rounding, and a stop seen on the FP32 recurrence costs one more iteration
+# to confirm on the true residual, so each pass may take up to 3 + 1 iterations
+# more or 3 fewer than the oracle; the solution meets the same 1e-4 rad bar.
+@pytest.mark.parametrize("H,W,p,mask_frac", [(128, 128, 1.0, 0.05), (200, 129, 0.0, 0.05), (96, 256, 2.0, 0.0),
+                                             (256, 256, 0.5, 0.0), (40, 50, 1.0, 0.0)])
+def test_mixed_mg_fcg_unwrap_vs_oracle(H, W, p, mask_frac):
+    m = synth.phase_map(H, W, 21, ramp=0.02, n_bumps=12, noise=0.5, mask_frac=mask_frac,
+                        sigma_range=(5.0, 20.0))
+    plan = native.Plan(H, W, outer_tol=0.0, precision=native.ULP_PRECISION_MIXED)
+    mk = _cuda(m.mask, torch.uint8) if m.mask is not None else None
+    phi, st = plan.unwrap(_cuda(m.psi), mk, p=p, precond="mg", tol=1e-6, max_outer=3, max_inner=2000)
+    ref, rst = oracle.unwrap(m.psi, m.mask, p=p, kind=oracle.M_MG, tol=1e-6, max_outer=3)
+    keep = None if m.mask is None else (m.mask == 0)
+    assert st["status"] == 0, st
+    assert _rms(phi.cpu().numpy(), ref, keep) < 1e-4
+    for a, b in zip(st["inner"], rst["inner"]):
+        assert -3 <= a - b <= 4, (st["inner"], rst["inner"])
+
+
+@pytest.mark.parametrize("H,W", [(160, 96), (33, 70)])
+@pytest.mark.parametrize("tol", [1e-6, 1e-9])
+def test_mixed_mg_pcg_true_residual(H, W, tol):
+    """The mixed solve stops on the FP64 true residual: ||b - A phi|| / ||b|| <= tol,
+    checked here with the oracle's FP64 CSR operator on the returned phi, also below
+    FP32 resolution (1e-9), where every refresh restarts the FP32 recurrence from
+    the FP64 residual and the solve takes more iterations than the FP64 one; at the
+    bench tolerance (1e-6) the counts follow the oracle's within the bar above."""
+    m = synth.phase_map(H, W, 9, noise=0.5)
+    dx, dy = oracle.wrapped_diffs(m.psi)
+    U, V = oracle.weights(np.zeros((H, W)), dx, dy, None, 1.0, 0.01)
+    A = oracle.assemble(U, V, dx, dy)
+    phi = torch.zeros((H, W), dtype=torch.float64, device="cuda")
+    _, st = native.ulp_pcg(_cuda(U), _cuda(V), _cuda(A.b), phi, precond="mg", tol=tol,
+                           precision=native.ULP_PRECISION_MIXED)
+    x = phi.cpu().numpy()
+    res = np.linalg.norm(A.b.ravel() - A.matvec(x).ravel()) / np.linalg.norm(A.b)
+    assert st["status"] == 0, st
+    assert res <= tol * (1 + 1e-3), res
+    if tol >= 1e-6:
+        _, rst = oracle.pcg(A, np.zeros((H, W)), kind=oracle.M_MG, tol=tol)
+        assert -3 <= st["inner"][0] - rst["iters"] <= 4, (st, rst)

@@ -67,7 +67,7 @@ FORMS = {"c5_2048": [("f64", "jacobi"), ("f64", "dct"), ("f64", "mg"), ("f64", "
          "c3_4096": [("f64", "jacobi"), ("mixed", "jacobi"), ("f64", "mg")]}
 DEFAULT_FORMS = [("f64", "jacobi"), ("mixed", "jacobi"), ("f64", "dct"), ("f64", "mg"), ("mixed", "mg")]
 CHOSEN = {"c5_2048": ("f64", "learned"), "c3_4096": ("mixed", "jacobi")}
-DEFAULT_CHOSEN = ("f64", "mg")
+DEFAULT_CHOSEN = ("mixed", "mg")
 ORACLE_KIND = {"jacobi": "jacobi", "identity": "identity", "mg": "mg", "dct": "dct", "learned": "jacobi"}
 # U-Net forward flop per pixel of the padded map: 2 x 9 x sum over layers of Cin Cout / 4^level
 UNET_FLOP_PER_PX = 18 * (16 * 16 + 16 * 32 / 4 + 32 * 64 / 16 + 64 * 128 / 64 + 192 * 64 / 16 + 96 * 32 / 4 + 48 * 16)

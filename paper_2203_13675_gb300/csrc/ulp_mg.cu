@@ -660,16 +660,132 @@ __device__ __forceinline__ float tail_ax(const float* U, const float* V, int H, 
   return d * x[o] + acc;
 }
 
+// Shared-memory grids of the tail: grid l at offset off[l] of each array, row-major H x W.
+struct TailSmem {
+  float *U, *V, *D, *x, *b, *t;
+};
+
+// f(i, j) over grid (H, W).  WARPS = 32: the whole block, rows by warp and columns
+// by lane (no per-element index division).  WARPS = 8: the first 256 threads, one
+// unknown per thread (grids of at most kTailWarpPx unknowns), synchronised by a
+// named barrier so the other warps never wait on these steps.
+constexpr int kTailSmallThreads = 256;
+template <int WARPS, class F>
+__device__ __forceinline__ void tail_for(int H, int W, int warp, int lane, const F& f) {
+  if (WARPS == kTailThreads / 32) {
+    for (int i = warp; i < H; i += WARPS)
+      for (int j = lane; j < W; j += 32) f(i, j);
+  } else {
+    const int k = warp * 32 + lane;
+    if (k < H * W) {
+      const int i = k / W;
+      f(i, k - i * W);
+    }
+  }
+}
+
+template <int WARPS>
+__device__ __forceinline__ void tail_sync() {
+  if (WARPS == kTailThreads / 32) __syncthreads();
+  else asm volatile("bar.sync 1, %0;" ::"n"(kTailSmallThreads) : "memory");
+}
+
+// Down-step of tail grid l (pre-sweeps, residual, restriction into grid l+1).
+template <int WARPS>
+__device__ __forceinline__ void tail_down(const TailGrids& tg, const TailSmem& sm, int l, int warp, int lane) {
+  const int H = tg.g[l].H, W = tg.g[l].W, o0 = tg.off[l];
+  const float* U = sm.U + o0;
+  const float* V = sm.V + o0;
+  const float* D = sm.D + o0;
+  float* x = sm.x + o0;
+  float* b = sm.b + o0;
+  float* t = sm.t + o0;
+  tail_for<WARPS>(H, W, warp, lane, [&](int i, int j) { t[i * W + j] = kOmegaF * D[i * W + j] * b[i * W + j]; });
+  tail_sync<WARPS>();
+  tail_for<WARPS>(H, W, warp, lane, [&](int i, int j) {
+    const int k = i * W + j;
+    x[k] = t[k] + kOmegaF * D[k] * (b[k] - tail_ax(U, V, H, W, i, j, t));
+  });
+  tail_sync<WARPS>();
+  const int Hc = tg.g[l + 1].H, Wc = tg.g[l + 1].W;
+  float* bc = sm.b + tg.off[l + 1];
+  tail_for<WARPS>(Hc, Wc, warp, lane, [&](int I, int J) {
+    float acc = 0.f;
+    for (int i = 2 * I; i <= 2 * I + 1 && i < H; ++i)
+      for (int j = 2 * J; j <= 2 * J + 1 && j < W; ++j) acc += b[i * W + j] - tail_ax(U, V, H, W, i, j, x);
+    bc[I * Wc + J] = acc;
+  });
+  tail_sync<WARPS>();
+}
+
+// Up-step of tail grid l (correction from grid l+1, two post-sweeps).
+template <int WARPS>
+__device__ __forceinline__ void tail_up(const TailGrids& tg, const TailSmem& sm, int l, int warp, int lane) {
+  const int H = tg.g[l].H, W = tg.g[l].W, o0 = tg.off[l];
+  const float* U = sm.U + o0;
+  const float* V = sm.V + o0;
+  const float* D = sm.D + o0;
+  float* x = sm.x + o0;
+  float* b = sm.b + o0;
+  float* t = sm.t + o0;
+  const int Wc = tg.g[l + 1].W;
+  const float* xc = sm.x + tg.off[l + 1];
+  tail_for<WARPS>(H, W, warp, lane, [&](int i, int j) { x[i * W + j] += kCCF * xc[(i >> 1) * Wc + (j >> 1)]; });
+  tail_sync<WARPS>();
+  tail_for<WARPS>(H, W, warp, lane, [&](int i, int j) {
+    const int k = i * W + j;
+    t[k] = x[k] + kOmegaF * D[k] * (b[k] - tail_ax(U, V, H, W, i, j, x));
+  });
+  tail_sync<WARPS>();
+  tail_for<WARPS>(H, W, warp, lane, [&](int i, int j) {
+    const int k = i * W + j;
+    x[k] = t[k] + kOmegaF * D[k] * (b[k] - tail_ax(U, V, H, W, i, j, t));
+  });
+  tail_sync<WARPS>();
+}
+
+// Coarsest tail grid: thirty sweeps from zero (x and t ping-pong), result in x.
+template <int WARPS>
+__device__ __forceinline__ void tail_coarsest(const TailGrids& tg, const TailSmem& sm, int l, int warp, int lane) {
+  const int H = tg.g[l].H, W = tg.g[l].W, o0 = tg.off[l];
+  const float* U = sm.U + o0;
+  const float* V = sm.V + o0;
+  const float* D = sm.D + o0;
+  const float* b = sm.b + o0;
+  float* src = sm.x + o0;
+  float* dst = sm.t + o0;
+  tail_for<WARPS>(H, W, warp, lane, [&](int i, int j) { src[i * W + j] = 0.f; });
+  tail_sync<WARPS>();
+  for (int s = 0; s < kCoarseSweeps; ++s) {
+    tail_for<WARPS>(H, W, warp, lane, [&](int i, int j) {
+      const int k = i * W + j;
+      dst[k] = src[k] + kOmegaF * D[k] * (b[k] - tail_ax(U, V, H, W, i, j, src));
+    });
+    tail_sync<WARPS>();
+    float* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  if (src != sm.x + o0) {
+    tail_for<WARPS>(H, W, warp, lane, [&](int i, int j) { sm.x[o0 + i * W + j] = src[i * W + j]; });
+    tail_sync<WARPS>();
+  }
+}
+
+// Grids of at most this many unknowns run on the first kTailSmallThreads threads.
+constexpr int kTailWarpPx = kTailSmallThreads;
+
 __global__ void __launch_bounds__(kTailThreads) k_mg_tail(TailGrids tg, const MapState* S) {
   if (skip_map(S)) return;
-  extern __shared__ float sm[];
+  extern __shared__ float smem[];
   const int tot = tg.off[tg.n - 1] + tg.g[tg.n - 1].H * tg.g[tg.n - 1].W;
-  float* sU = sm;
-  float* sV = sU + tot;
-  float* sD = sV + tot;
-  float* sx = sD + tot;
-  float* sb = sx + tot;
-  float* st = sb + tot;
+  TailSmem sm;
+  sm.U = smem;
+  sm.V = sm.U + tot;
+  sm.D = sm.V + tot;
+  sm.x = sm.D + tot;
+  sm.b = sm.x + tot;
+  sm.t = sm.b + tot;
   // load weights of every tail grid and the right-hand side of the first, all loads of
   // a thread in flight together (the shared arrays are contiguous over the grids)
   {
@@ -695,87 +811,32 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(TailGrids tg, const Ma
     for (int q = 0; q < kq; ++q) {
       const int k = threadIdx.x + kTailThreads * q;
       if (k < tot) {
-        sU[k] = ru[q];
-        sV[k] = rv[q];
-        sD[k] = rd[q];
-        if (k < tg.g[0].H * tg.g[0].W) sb[k] = rb[q];
+        sm.U[k] = ru[q];
+        sm.V[k] = rv[q];
+        sm.D[k] = rd[q];
+        if (k < tg.g[0].H * tg.g[0].W) sm.b[k] = rb[q];
       }
     }
   }
   __syncthreads();
-  // down
-  for (int l = 0; l + 1 < tg.n; ++l) {
-    const int H = tg.g[l].H, W = tg.g[l].W, n = H * W, o0 = tg.off[l];
-    const float* U = sU + o0;
-    const float* V = sV + o0;
-    const float* D = sD + o0;
-    float* x = sx + o0;
-    float* b = sb + o0;
-    float* t = st + o0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) t[k] = kOmegaF * D[k] * b[k];  // first sweep
-    __syncthreads();
-    for (int k = threadIdx.x; k < n; k += blockDim.x)
-      x[k] = t[k] + kOmegaF * D[k] * (b[k] - tail_ax(U, V, H, W, k / W, k % W, t));
-    __syncthreads();
-    const int Hc = tg.g[l + 1].H, Wc = tg.g[l + 1].W;
-    float* bc = sb + tg.off[l + 1];
-    for (int k = threadIdx.x; k < Hc * Wc; k += blockDim.x) {
-      const int I = k / Wc, J = k % Wc;
-      float acc = 0.f;
-      for (int i = 2 * I; i <= 2 * I + 1 && i < H; ++i)
-        for (int j = 2 * J; j <= 2 * J + 1 && j < W; ++j) acc += b[i * W + j] - tail_ax(U, V, H, W, i, j, x);
-      bc[k] = acc;
-    }
-    __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int L = tg.n;
+  // leading grids of more than kTailWarpPx unknowns: the whole block; the rest (always
+  // including the coarsest, at most 16 unknowns): the first 8 warps, one unknown each
+  constexpr int kSmallWarps = kTailSmallThreads / 32;
+  int nb = 0;
+  while (nb < L && tg.g[nb].H * tg.g[nb].W > kTailWarpPx) ++nb;
+  for (int l = 0; l < nb && l + 1 < L; ++l) tail_down<kTailThreads / 32>(tg, sm, l, warp, lane);
+  if (warp < kSmallWarps) {
+    for (int l = nb; l + 1 < L; ++l) tail_down<kSmallWarps>(tg, sm, l, warp, lane);
+    tail_coarsest<kSmallWarps>(tg, sm, L - 1, warp, lane);
+    for (int l = L - 2; l >= nb; --l) tail_up<kSmallWarps>(tg, sm, l, warp, lane);
   }
-  // coarsest: sweeps from zero, x and t ping-pong
-  {
-    const int l = tg.n - 1;
-    const int H = tg.g[l].H, W = tg.g[l].W, n = H * W, o0 = tg.off[l];
-    const float* U = sU + o0;
-    const float* V = sV + o0;
-    const float* D = sD + o0;
-    float* b = sb + o0;
-    float* src = sx + o0;
-    float* dst = st + o0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) src[k] = 0.f;
-    __syncthreads();
-    for (int s = 0; s < kCoarseSweeps; ++s) {
-      for (int k = threadIdx.x; k < n; k += blockDim.x)
-        dst[k] = src[k] + kOmegaF * D[k] * (b[k] - tail_ax(U, V, H, W, k / W, k % W, src));
-      __syncthreads();
-      float* tmp = src;
-      src = dst;
-      dst = tmp;
-    }
-    if (src != sx + o0) {
-      for (int k = threadIdx.x; k < n; k += blockDim.x) sx[o0 + k] = src[k];
-      __syncthreads();
-    }
-  }
-  // up
-  for (int l = tg.n - 2; l >= 0; --l) {
-    const int H = tg.g[l].H, W = tg.g[l].W, n = H * W, o0 = tg.off[l];
-    const float* U = sU + o0;
-    const float* V = sV + o0;
-    const float* D = sD + o0;
-    float* x = sx + o0;
-    float* b = sb + o0;
-    float* t = st + o0;
-    const int Wc = tg.g[l + 1].W;
-    const float* xc = sx + tg.off[l + 1];
-    for (int k = threadIdx.x; k < n; k += blockDim.x) x[k] += kCCF * xc[(k / W >> 1) * Wc + ((k % W) >> 1)];
-    __syncthreads();
-    for (int k = threadIdx.x; k < n; k += blockDim.x)
-      t[k] = x[k] + kOmegaF * D[k] * (b[k] - tail_ax(U, V, H, W, k / W, k % W, x));
-    __syncthreads();
-    for (int k = threadIdx.x; k < n; k += blockDim.x)
-      x[k] = t[k] + kOmegaF * D[k] * (b[k] - tail_ax(U, V, H, W, k / W, k % W, t));
-    __syncthreads();
-  }
+  __syncthreads();
+  for (int l = (nb < L - 1 ? nb : L - 1) - 1; l >= 0; --l) tail_up<kTailThreads / 32>(tg, sm, l, warp, lane);
   const Grid& g0 = tg.g[0];
-  for (int k = threadIdx.x; k < g0.H * g0.W; k += blockDim.x)
-    g0.x[(size_t)(k / g0.W) * g0.ld + k % g0.W] = sx[k];
+  tail_for<kTailThreads / 32>(g0.H, g0.W, warp, lane,
+                              [&](int i, int j) { g0.x[(size_t)i * g0.ld + j] = sm.x[i * g0.W + j]; });
 }
 
 }  // namespace mg

@@ -61,9 +61,10 @@ struct XDir32 {  // d = s + beta d_old (FP32), d = s on the first iteration
 // FP32 sliding-window stencil (same tiling as the FP64 walker), summed over the
 // edges as w (x_i - x_j) from the FP32 weights: the FP32 operator keeps A 1 = 0
 // exactly, and for the smooth directions of a well-preconditioned solve its error
-// stays relative to |A x| rather than to |A| |x|.  FP32 rows move half the bytes of FP64
-// ones, so loads run two rows ahead of the arithmetic to keep enough in flight.
-template <class X, class Epi>
+// stays relative to |A x| rather than to |A| |x|.  FP32 rows move half the bytes of
+// FP64 ones, so loads run LA rows ahead of the arithmetic (a ring of raw rows in
+// registers) to keep enough bytes in flight with two blocks per SM.
+template <class X, class Epi, int LA = 4>
 __device__ __forceinline__ void stencil_tile32(const MapDesc& M, int i0, int i1, int j0, int lane,
                                                const float* U, const float* V, const X& x, Epi& epi) {
   using Raw = typename X::Raw;
@@ -80,37 +81,46 @@ __device__ __forceinline__ void stencil_tile32(const MapDesc& M, int i0, int i1,
     vn = ldf2(V, (size_t)(i0 - 1) * P + j);
   }
   float2 xc = x.make(x.load(i0, j));
-  // raw x of rows i+1, i+2; weights and halo of rows i, i+1
-  Raw r1 = (i0 + 1 < M.H) ? x.load(i0 + 1, j) : X::zero();
-  Raw r2 = (i0 + 2 < M.H && i0 + 1 < i1) ? x.load(i0 + 2, j) : X::zero();
-  size_t off = (size_t)i0 * P + j;
-  float2 u0 = ldf2(U, off), v0 = ldf2(V, off), u1 = z2, v1 = z2;
-  float h0 = halo ? x.at(i0, hc) : 0.f, h1 = 0.f;
-  float w0 = hw ? __ldcg(U + off - j + hc) : 0.f, w1 = 0.f;
-  if (i0 + 1 < i1) {
-    u1 = ldf2(U, off + P);
-    v1 = ldf2(V, off + P);
-    if (halo) h1 = x.at(i0 + 1, hc);
-    if (hw) w1 = __ldcg(U + off + P - j + hc);
-  }
-  for (int i = i0; i < i1; ++i) {
-    // issue the loads two rows ahead
-    Raw r3 = (i + 3 < M.H && i + 2 < i1) ? x.load(i + 3, j) : X::zero();
-    float2 u2 = z2, v2 = z2;
-    float h2 = 0.f, w2 = 0.f;
-    if (i + 2 < i1) {
-      const size_t o2 = off + 2 * P;
-      u2 = ldf2(U, o2);
-      v2 = ldf2(V, o2);
-      if (halo) h2 = x.at(i + 2, hc);
-      if (hw) w2 = __ldcg(U + o2 - j + hc);
+  // rings: raw x of rows i+1 .. i+LA (row r is needed while row r-1 is in the tile);
+  // weights and halo of rows i .. i+LA-1
+  Raw rx[LA];
+  float2 uu[LA], vv[LA];
+  float hh[LA], ww[LA];
+#pragma unroll
+  for (int k = 0; k < LA; ++k) {
+    const int ri = i0 + 1 + k, wi = i0 + k;
+    rx[k] = (ri < M.H && ri - 1 < i1) ? x.load(ri, j) : X::zero();
+    uu[k] = vv[k] = z2;
+    hh[k] = ww[k] = 0.f;
+    if (wi < i1) {
+      const size_t o = (size_t)wi * P + j;
+      uu[k] = ldf2(U, o);
+      vv[k] = ldf2(V, o);
+      if (halo) hh[k] = x.at(wi, hc);
+      if (hw) ww[k] = __ldcg(U + o - j + hc);
     }
-    const float2 xs = (i + 1 < M.H) ? x.make(r1) : z2;
+  }
+  size_t off = (size_t)i0 * P + j;
+  for (int i = i0; i < i1; ++i) {
+    // issue the loads LA rows ahead
+    const int rn = i + 1 + LA, wn = i + LA;
+    const Raw rnew = (rn < M.H && rn - 1 < i1) ? x.load(rn, j) : X::zero();
+    float2 unew = z2, vnew = z2;
+    float hnew = 0.f, wnew = 0.f;
+    if (wn < i1) {
+      const size_t o = off + (size_t)LA * P;
+      unew = ldf2(U, o);
+      vnew = ldf2(V, o);
+      if (halo) hnew = x.at(wn, hc);
+      if (hw) wnew = __ldcg(U + o - j + hc);
+    }
+    const float2 u0 = uu[0], v0 = vv[0];
+    const float2 xs = (i + 1 < M.H) ? x.make(rx[0]) : z2;
     float west = __shfl_up_sync(kFull, xc.y, 1);
     float east = __shfl_down_sync(kFull, xc.x, 1);
     float uw = __shfl_up_sync(kFull, u0.y, 1);
-    if (lane == 0) { west = h0; uw = w0; }
-    if (lane == 31) east = h0;
+    if (lane == 0) { west = hh[0]; uw = ww[0]; }
+    if (lane == 31) east = hh[0];
     // sum over the four edges of w (x_i - x_j): the neighbour differences are nearly
     // exact for a smooth x, where D x_i - sum w x_j would cancel to a few bits
     float2 ax;
@@ -126,16 +136,19 @@ __device__ __forceinline__ void stencil_tile32(const MapDesc& M, int i0, int i1,
     xn = xc;
     xc = xs;
     vn = v0;
-    r1 = r2;
-    r2 = r3;
-    u0 = u1;
-    v0 = v1;
-    u1 = u2;
-    v1 = v2;
-    h0 = h1;
-    h1 = h2;
-    w0 = w1;
-    w1 = w2;
+#pragma unroll
+    for (int k = 0; k + 1 < LA; ++k) {
+      rx[k] = rx[k + 1];
+      uu[k] = uu[k + 1];
+      vv[k] = vv[k + 1];
+      hh[k] = hh[k + 1];
+      ww[k] = ww[k + 1];
+    }
+    rx[LA - 1] = rnew;
+    uu[LA - 1] = unew;
+    vv[LA - 1] = vnew;
+    hh[LA - 1] = hnew;
+    ww[LA - 1] = wnew;
     off += P;
   }
 }

@@ -396,8 +396,11 @@ static int enqueue_call(Plan& pl, const ulp_map* maps, int precond, double tol, 
     ULP_CU(launch_pack(pl, m, maps[m].psi, maps[m].mask, user_phi0 ? maps[m].phi : nullptr, st));
   ULP_CU(launch_check(pl, st));
   const PcgArgs a = pcg_args(pl, tol, max_inner);
+  // the mixed multigrid form takes its weights in FP32 straight into the planes it reads
+  pl.system_x = mixed && precond == ULP_PRECOND_MG && pl.nmaps == 1;
   for (int k = 0; k < max_outer; ++k) {
-    ULP_CU(launch_system(pl, pl.d_p, pl.d_tau, st));
+    if (pl.system_x) ULP_CU(launch_system_x(pl, pl.d_p, pl.d_tau, st));
+    else ULP_CU(launch_system(pl, pl.d_p, pl.d_tau, st));
     cudaEvent_t e0, e1;
     next_events(pl, &e0, &e1);
     if (is_fcg_kind(precond)) ULP_CU(launch_fcg(pl, precond, a, st, e0, e1));

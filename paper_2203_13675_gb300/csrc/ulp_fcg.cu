@@ -439,7 +439,7 @@ static cudaError_t fcg_start(Plan& pl, int kind, cudaStream_t st) {
   if (mixed_fcg(pl, kind)) {
     k_x_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = mg_setup(*pl.mg, pl.dstate, st);
+    if (e == cudaSuccess) e = mg_setup(*pl.mg, pl.dstate, st, !pl.system_x);
     if (e == cudaSuccess) e = fcg_precond(pl, kind, st);
     k_x_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
     return e == cudaSuccess ? cudaGetLastError() : e;
@@ -564,7 +564,7 @@ static cudaError_t fcg_eager_mixed(Plan& pl, int kind, cudaStream_t st) {
   phase_mark(pl, st, -1);
   k_x_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
   phase_mark(pl, st, 2);
-  if ((e = mg_setup(*pl.mg, pl.dstate, st)) != cudaSuccess) return e;
+  if ((e = mg_setup(*pl.mg, pl.dstate, st, !pl.system_x)) != cudaSuccess) return e;
   if ((e = fcg_precond(pl, kind, st)) != cudaSuccess) return e;
   phase_mark(pl, st, 3);
   k_x_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);

@@ -120,6 +120,102 @@ __global__ void k_system(const MapDesc* __restrict__ maps, MapState* S) {
   }
 }
 
+// ------------------------------------------------------------------ mixed multigrid system
+// The mixed-precision multigrid form takes Eq. (UV)'s weights in FP32: the edge
+// residual e is formed in FP64 from the FP64 phi, the weight tau / (|e|^(2-p) + tau)
+// in FP32.  They are written as the FP32 planes that the FP32 stencil and the
+// V-cycle read, and as their exact FP64 promotions, from which D (their FP64 sum,
+// exact) and b follow as in k_system for the FP64 true residual; D^-1 is FP32.
+// Two pixels per thread.
+__device__ __forceinline__ float irls_weight32(double e, float p, float tau, int pcase) {
+  const float a = fabsf((float)e);
+  float t;
+  switch (pcase) {
+    case 2: t = 1.f; break;
+    case 1: t = a; break;
+    case 0: t = __fmul_rn(a, a); break;
+    default: t = powf(a, 2.f - p); break;
+  }
+  return __fdiv_rn(tau, __fadd_rn(t, tau));
+}
+
+__global__ void k_weights_x(const MapDesc* __restrict__ maps, MapState* S, const double* __restrict__ pv,
+                            const double* __restrict__ tauv) {
+  const MapDesc& M = maps[0];
+  if (!S[0].outer_active) return;
+  const float p = (float)pv[0], tau = (float)tauv[0];
+  const int pc = p_case(pv[0]);
+  const unsigned half = (unsigned)M.pitch / 2u;
+  const size_t n = (size_t)M.H * half;
+  const size_t P = M.pitch;
+  for (size_t t2 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t2 < n; t2 += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)((unsigned)t2 / half), j = 2 * (int)((unsigned)t2 - (unsigned)i * half);
+    const size_t o = (size_t)i * P + j;
+    const double2 ph = ld2(M.f.phi, o);
+    float2 u = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
+    if (j < M.W) {
+      const double2 dxv = ld2(M.f.dx, o);
+      const bool m0 = M.f.mask[o] != 0, m1 = M.f.mask[o + 1] != 0;
+      // east edges of (i, j) and (i, j+1)
+      if (j + 1 < M.W && !m0 && !m1) u.x = irls_weight32(__dsub_rn(__dsub_rn(ph.y, ph.x), dxv.x), p, tau, pc);
+      if (j + 2 < M.W && !m1 && !M.f.mask[o + 2])
+        u.y = irls_weight32(__dsub_rn(__dsub_rn(M.f.phi[o + 2], ph.y), dxv.y), p, tau, pc);
+      // south edges
+      if (i + 1 < M.H) {
+        const double2 dyv = ld2(M.f.dy, o), ps = ld2(M.f.phi, o + P);
+        if (!m0 && !M.f.mask[o + P]) v.x = irls_weight32(__dsub_rn(__dsub_rn(ps.x, ph.x), dyv.x), p, tau, pc);
+        if (j + 1 < M.W && !m1 && !M.f.mask[o + P + 1])
+          v.y = irls_weight32(__dsub_rn(__dsub_rn(ps.y, ph.y), dyv.y), p, tau, pc);
+      }
+    }
+    *reinterpret_cast<float2*>(M.h.U + o) = u;
+    *reinterpret_cast<float2*>(M.h.V + o) = v;
+    st2(M.f.U, o, make_double2((double)u.x, (double)u.y));
+    st2(M.f.V, o, make_double2((double)v.x, (double)v.y));
+    st2(M.f.phi_prev, o, ph);
+  }
+}
+
+__global__ void k_system_x(const MapDesc* __restrict__ maps, MapState* S) {
+  const MapDesc& M = maps[0];
+  if (!S[0].outer_active) return;
+  const unsigned half = (unsigned)M.pitch / 2u;
+  const size_t n = (size_t)M.H * half;
+  const size_t P = M.pitch;
+  for (size_t t2 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t2 < n; t2 += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)((unsigned)t2 / half), j = 2 * (int)((unsigned)t2 - (unsigned)i * half);
+    const size_t o = (size_t)i * P + j;
+    const double2 ue = ld2(M.f.U, o), vs = ld2(M.f.V, o), dxv = ld2(M.f.dx, o), dyv = ld2(M.f.dy, o);
+    const double uw0 = (j > 0) ? M.f.U[o - 1] : 0.0;
+    const double dxw = (j > 0) ? M.f.dx[o - 1] : 0.0;
+    double2 vn = make_double2(0.0, 0.0), dyn = make_double2(0.0, 0.0);
+    if (i > 0) {
+      vn = ld2(M.f.V, o - P);
+      dyn = ld2(M.f.dy, o - P);
+    }
+    const double uw[2] = {uw0, ue.x}, uev[2] = {ue.x, ue.y}, vnv[2] = {vn.x, vn.y}, vsv[2] = {vs.x, vs.y};
+    const double dxwv[2] = {dxw, dxv.x}, dxv2[2] = {dxv.x, dxv.y}, dynv[2] = {dyn.x, dyn.y},
+                 dyv2[2] = {dyv.x, dyv.y};
+    double d2[2], b2[2];
+    float di[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const double d = __dadd_rn(__dadd_rn(__dadd_rn(uw[k], uev[k]), vnv[k]), vsv[k]);
+      double bk = 0.0;
+      if (j + k > 0) bk = __dadd_rn(bk, __dmul_rn(dxwv[k], uw[k]));
+      bk = __dsub_rn(bk, __dmul_rn(dxv2[k], uev[k]));
+      if (i > 0) bk = __dadd_rn(bk, __dmul_rn(dynv[k], vnv[k]));
+      bk = __dsub_rn(bk, __dmul_rn(dyv2[k], vsv[k]));
+      d2[k] = d;
+      b2[k] = bk;
+      di[k] = (d > 0.0) ? __fdiv_rn(1.f, (float)d) : 0.f;
+    }
+    st2(M.f.D, o, make_double2(d2[0], d2[1]));
+    st2(M.f.b, o, make_double2(b2[0], b2[1]));
+    *reinterpret_cast<float2*>(M.h.Dinv + o) = make_float2(di[0], di[1]);
+  }
+}
+
 // r = b - A phi, s = M^{-1} r, partials r^T s, r^T r (and b^T b at the start).
 template <int KIND>
 __device__ __forceinline__ void res_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t,
@@ -714,6 +810,14 @@ cudaError_t launch_system(const Plan& pl, const double* d_p, const double* d_tau
   pl.kernel_launches += 2;
   k_weights<<<grid, kThreads, 0, st>>>(pl.dmaps, pl.dstate, d_p, d_tau);
   k_system<<<grid, kThreads, 0, st>>>(pl.dmaps, pl.dstate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_system_x(const Plan& pl, const double* d_p, const double* d_tau, cudaStream_t st) {
+  if (pl.nmaps != 1) return cudaErrorNotSupported;
+  pl.kernel_launches += 2;
+  k_weights_x<<<pl.bx_elem, kThreads, 0, st>>>(pl.dmaps, pl.dstate, d_p, d_tau);
+  k_system_x<<<pl.bx_elem, kThreads, 0, st>>>(pl.dmaps, pl.dstate);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ struct Plan {
   int R = 32;                // rows per warp tile
   int bps = 1;               // resident blocks per SM of the persistent solvers
   int bx_elem = 1;           // blocks per map of the elementwise kernels
+  bool system_x = false;     // the current call builds its system with launch_system_x
   ulp_options opt{};
   std::vector<MapDesc> hmaps;
   MapDesc* dmaps = nullptr;
@@ -82,6 +83,9 @@ cudaError_t launch_begin(const Plan& pl, cudaStream_t st);
 cudaError_t launch_check(const Plan& pl, cudaStream_t st);
 cudaError_t launch_diag(const Plan& pl, cudaStream_t st);
 cudaError_t launch_system(const Plan& pl, const double* d_p, const double* d_tau, cudaStream_t st);
+// mixed multigrid form (single-map plans): FP32 weights and D^-1 in the map's FP32 planes, their
+// FP64 promotions, D and b in the FP64 planes
+cudaError_t launch_system_x(const Plan& pl, const double* d_p, const double* d_tau, cudaStream_t st);
 cudaError_t launch_outer_error(const Plan& pl, double outer_tol, int max_outer, cudaStream_t st);
 cudaError_t launch_pcg64(const Plan& pl, int kind, const PcgArgs& a, cudaStream_t st, cudaEvent_t e0 = nullptr,
                          cudaEvent_t e1 = nullptr);
@@ -106,7 +110,9 @@ int dct_error(const DctPlan& d);  // 1 if a GEMM wait ran out since the last cal
 size_t mg_bytes(int H, int W);
 MgPlan* mg_create(const MapDesc& M, void* mem, int nsm, int ntiles);
 void mg_destroy(MgPlan* p);
-cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st);  // coarse grids, once per solve
+// coarse grids, once per solve; level0: make the map grid's FP32 weights and D^-1 from the FP64
+// planes (false when launch_system_x already wrote them)
+cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st, bool level0 = true);
 // packed: the FP32 copy of r (mg_input, the map's pitch) is already written; dots (device
 // arguments of a flexible-CG solve, or null): the cycle's last kernel also does the solve's
 // dot phase (r^T s, r^T r, beta, stop test), if mg_fuses_dots

@@ -977,9 +977,9 @@ static int mg_blocks(const MgPlan& p, long long n) {
 }
 
 // FP32 level 0 and the coarse grids for the current weights (once per inner solve).
-cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st) {
+cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st, bool level0) {
   const Grid& g0 = p.g[0];
-  k_mg_level0<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(p.U0, p.V0, p.Dinv0, g0, S);
+  if (level0) k_mg_level0<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(p.U0, p.V0, p.Dinv0, g0, S);
   for (size_t l = 0; l + 1 < p.g.size(); ++l) {
     const Grid& c = p.g[l + 1];
     k_mg_coarsen<<<mg_blocks(p, (long long)c.H * c.W), 256, 0, st>>>(p.g[l], c, S);

@@ -357,24 +357,31 @@ __global__ void k_mg_rhs_v(const double* __restrict__ r, Grid g, const MapState*
   }
 }
 
-// ---------------------------------------------------------------- fused row walkers
-// One launch per grid and direction instead of two.  A warp owns a window of 128
-// columns starting at j0 = 120 k - 4 (four pixels per lane, float4 accesses) and
-// a band of rows, and walks down the band keeping the last rows of every
-// quantity in registers.  Lanes 1..30 produce the window's inner 120 columns;
-// lanes 0 and 31 only supply the column neighbours, whose values two sweeps deep
-// are exact because the window extends four columns past the output on each
-// side.  The rows two sweeps deep above and below the band are recomputed, not
-// read back, so no value crosses between warps within a launch.
+// ---------------------------------------------------------------- tiled fused kernels
+// One launch per grid and direction.  A block of 256 threads owns a tile: a
+// window of 128 columns starting at j0 = 120 k - 4 (four pixels per lane, float4
+// accesses; lanes 1..30 produce the window's inner 120 columns, lanes 0 and 31
+// only supply column neighbours, exact two sweeps deep because the window extends
+// four columns past the output on each side) and TR rows, plus the two rows above
+// and below that two sweeps reach.  The block issues every load of its tile at
+// once into shared memory (one memory round trip), then runs each sweep over the
+// tile from shared memory with a block barrier in between; the halo rows and
+// columns are recomputed, so no value crosses between blocks within a launch.
 //   k_mg_down: x1 = w D^-1 b, x2 = x1 + w D^-1 (b - A x1) (both pre-sweeps), x = x2
 //              written, and b_c = P^T (b - A x2) (residual + restriction)
 //   k_mg_up:   x' = x + cc P x_c, t = x' + w D^-1 (b - A x'), s = t + w D^-1 (b - A t);
 //              s goes to the grid's t plane (x is still being read by the
-//              neighbouring bands), or on the map's grid to the FP64 s (0 on
-//              masked pixels), where the warp also sums r^T s and r^T r for the
-//              flexible CG's dot phase.
+//              neighbouring tiles), or on the map's grid to the FP64 s (0 on
+//              masked pixels) or to the FP32 s of the mixed solve, where the block
+//              also sums r^T s and r^T r for the flexible CG's dot phase.
 // Per pixel the arithmetic is that of the per-step kernels above.
 constexpr int kSegOut = 120;
+constexpr int kWin = 128;
+constexpr int kTileThreads = 256;
+constexpr int kTileWarps = kTileThreads / 32;
+constexpr int kTileMaxRows = 16;                                   // TR <= 16
+constexpr int kTilePlane = (kTileMaxRows + 4) * kWin;              // floats per shared plane
+constexpr size_t kTileSmem = 6 * kTilePlane * sizeof(float);        // six planes: 61,440 bytes
 
 // row i of a plane at the lane's 4 columns from j: 0 outside the grid
 __device__ __forceinline__ float4 lrow(const float* p, const Grid& f, int i, int j) {
@@ -414,6 +421,235 @@ __device__ __forceinline__ float4 jac4(const float4& y, const float4& D, const f
                      y.z + kOmegaF * D.z * (b.z - a.z), y.w + kOmegaF * D.w * (b.w - a.w));
 }
 
+__device__ __forceinline__ float4 lds4(const float* p, int rr, int lane) {
+  return *reinterpret_cast<const float4*>(p + rr * kWin + 4 * lane);
+}
+__device__ __forceinline__ void sts4(float* p, int rr, int lane, const float4& v) {
+  *reinterpret_cast<float4*>(p + rr * kWin + 4 * lane) = v;
+}
+
+// pre-smoothing + residual + restriction for the fine rows [TR band, TR band + TR), TR even
+__global__ void __launch_bounds__(kTileThreads) k_mg_down_t(Grid f, Grid c, int TR, const MapState* S) {
+  if (skip_map(S)) return;
+  extern __shared__ float4 tsm4[];
+  float* sU = reinterpret_cast<float*>(tsm4);
+  float* sV = sU + kTilePlane;
+  float* sD = sV + kTilePlane;
+  float* sB = sD + kTilePlane;
+  float* sX1 = sB + kTilePlane;
+  float* sX2 = sX1 + kTilePlane;
+  const int nseg = (f.W + kSegOut - 1) / kSegOut;
+  const int seg = blockIdx.x % nseg, band = blockIdx.x / nseg;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = seg * kSegOut - 4 + 4 * lane;
+  const bool out = lane >= 1 && lane <= 30 && j < f.W;
+  const int r0 = band * TR, r1 = min(f.H, r0 + TR);
+  const int nrow = r1 - r0 + 4;  // rows r0-2 .. r1+1, shared row rr = r - r0 + 2
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int rr = warp; rr < nrow; rr += kTileWarps) {
+    const int r = r0 - 2 + rr;
+    const float4 U = lrow(f.U, f, r, j), V = lrow(f.V, f, r, j), D = lrow(f.Dinv, f, r, j), B = lrow(f.b, f, r, j);
+    sts4(sU, rr, lane, U);
+    sts4(sV, rr, lane, V);
+    sts4(sD, rr, lane, D);
+    sts4(sB, rr, lane, B);
+    sts4(sX1, rr, lane,
+         make_float4(kOmegaF * D.x * B.x, kOmegaF * D.y * B.y, kOmegaF * D.z * B.z, kOmegaF * D.w * B.w));
+  }
+  __syncthreads();
+  // x2 at rows r0-1 .. r1 (0 outside the grid)
+  for (int rr = 1 + warp; rr <= nrow - 2; rr += kTileWarps) {
+    const int r = r0 - 2 + rr;
+    float4 X2 = z;
+    if (r >= 0 && r < f.H) {
+      const float4 xc = lds4(sX1, rr, lane);
+      X2 = jac4(xc, lds4(sD, rr, lane), lds4(sB, rr, lane),
+                arow(lds4(sX1, rr - 1, lane), xc, lds4(sX1, rr + 1, lane), lds4(sU, rr, lane), lds4(sV, rr, lane),
+                     lds4(sV, rr - 1, lane), lane));
+      if (out && r >= r0 && r < r1) *reinterpret_cast<float4*>(f.x + (size_t)r * f.ld + j) = X2;
+    }
+    sts4(sX2, rr, lane, X2);
+  }
+  __syncthreads();
+  // residual at the fine rows 2I, 2I+1, summed over the aggregate's two columns and two rows
+  for (int I = r0 / 2 + warp; 2 * I < r1; I += kTileWarps) {
+    const int p = 2 * I, rr = p - r0 + 2;
+    const float4 x0 = lds4(sX2, rr - 1, lane), x1 = lds4(sX2, rr, lane), x2 = lds4(sX2, rr + 1, lane);
+    const float4 a1 = arow(x0, x1, x2, lds4(sU, rr, lane), lds4(sV, rr, lane), lds4(sV, rr - 1, lane), lane);
+    const float4 b1 = lds4(sB, rr, lane);
+    float lo = (b1.x - a1.x) + (b1.y - a1.y), hi = (b1.z - a1.z) + (b1.w - a1.w);
+    if (p + 1 < f.H) {
+      const float4 a2 = arow(x1, x2, lds4(sX2, rr + 2, lane), lds4(sU, rr + 1, lane), lds4(sV, rr + 1, lane),
+                             lds4(sV, rr, lane), lane);
+      const float4 b2 = lds4(sB, rr + 1, lane);
+      lo += (b2.x - a2.x) + (b2.y - a2.y);
+      hi += (b2.z - a2.z) + (b2.w - a2.w);
+    }
+    if (out) *reinterpret_cast<float2*>(c.b + (size_t)I * c.ld + (j >> 1)) = make_float2(lo, hi);
+  }
+}
+
+// prolongation + correction + both post-sweeps for the rows [TR band, TR band + TR).
+// xc: the coarse grid's corrected solution.  MODE kUpCoarse: s to the grid's t plane.
+// kUp64 (the map's grid): s in FP64; with pa, r^T s and r^T r (r: the map's FP64
+// residual) over the block's pixels arrive in the flexible CG's dot phase.  kUp32 (the
+// map's grid, mixed flexible CG): s in FP32 into s32; with pa, the same dot phase in
+// double-float sums of exact FP32 products, r being the cycle's right-hand side.
+enum { kUpCoarse = 0, kUp64 = 1, kUp32 = 2 };
+template <int MODE>
+__global__ void __launch_bounds__(kTileThreads) k_mg_up_t(Grid f, Grid c, const float* __restrict__ xc, int TR,
+                                                        const uint8_t* mask, double* s, const double* __restrict__ rv,
+                                                        float* s32, const PcgArgs* pa, const MapState* S) {
+  constexpr bool MAP = MODE != kUpCoarse;
+  constexpr int kOut = kTileMaxRows / kTileWarps;  // output rows per warp at most
+  if (skip_map(S)) return;
+  extern __shared__ float4 tsm4[];
+  __shared__ double red[2][kTileWarps];
+  float* sU = reinterpret_cast<float*>(tsm4);
+  float* sV = sU + kTilePlane;
+  float* sD = sV + kTilePlane;
+  float* sB = sD + kTilePlane;
+  float* sXP = sB + kTilePlane;
+  float* sT = sXP + kTilePlane;
+  const int nseg = (f.W + kSegOut - 1) / kSegOut;
+  const int seg = blockIdx.x % nseg, band = blockIdx.x / nseg;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = seg * kSegOut - 4 + 4 * lane;
+  const bool out = lane >= 1 && lane <= 30 && j < f.W;
+  const int r0 = band * TR, r1 = min(f.H, r0 + TR);
+  const int nrow = r1 - r0 + 4;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  // the map's grid: mask and FP64 r of this warp's output rows, loaded with the tile
+  uchar4 mk[kOut];
+  double2 ra[kOut], rb[kOut];
+#pragma unroll
+  for (int k = 0; k < kOut; ++k) {
+    mk[k] = make_uchar4(0, 0, 0, 0);
+    ra[k] = rb[k] = make_double2(0.0, 0.0);
+    const int r = r0 + warp + kTileWarps * k;
+    if (MAP && r < r1 && j >= 0 && j < f.W) {
+      const size_t o = (size_t)r * f.ld + j;
+      if (mask) mk[k] = *reinterpret_cast<const uchar4*>(mask + o);
+      if (MODE == kUp64 && rv) {
+        ra[k] = *reinterpret_cast<const double2*>(rv + o);
+        rb[k] = *reinterpret_cast<const double2*>(rv + o + 2);
+      }
+    }
+  }
+  for (int rr = warp; rr < nrow; rr += kTileWarps) {
+    const int r = r0 - 2 + rr;
+    sts4(sU, rr, lane, lrow(f.U, f, r, j));
+    sts4(sV, rr, lane, lrow(f.V, f, r, j));
+    sts4(sD, rr, lane, lrow(f.Dinv, f, r, j));
+    sts4(sB, rr, lane, lrow(f.b, f, r, j));
+    float4 XP = lrow(f.x, f, r, j);
+    if (r >= 0 && r < f.H && j >= 0 && j < f.W) {
+      const float2 e = *reinterpret_cast<const float2*>(xc + (size_t)(r >> 1) * c.ld + (j >> 1));
+      XP = make_float4(XP.x + kCCF * e.x, XP.y + kCCF * e.x, XP.z + kCCF * e.y, XP.w + kCCF * e.y);
+      if (j + 1 >= f.W) XP.y = 0.f;
+      if (j + 2 >= f.W) XP.z = 0.f;
+      if (j + 3 >= f.W) XP.w = 0.f;
+    }
+    sts4(sXP, rr, lane, XP);
+  }
+  __syncthreads();
+  // t at rows r0-1 .. r1 (0 outside the grid)
+  for (int rr = 1 + warp; rr <= nrow - 2; rr += kTileWarps) {
+    const int r = r0 - 2 + rr;
+    float4 T = z;
+    if (r >= 0 && r < f.H) {
+      const float4 xp = lds4(sXP, rr, lane);
+      T = jac4(xp, lds4(sD, rr, lane), lds4(sB, rr, lane),
+               arow(lds4(sXP, rr - 1, lane), xp, lds4(sXP, rr + 1, lane), lds4(sU, rr, lane), lds4(sV, rr, lane),
+                    lds4(sV, rr - 1, lane), lane));
+    }
+    sts4(sT, rr, lane, T);
+  }
+  __syncthreads();
+  // s at rows r0 .. r1-1
+  double rs = 0.0, rr2 = 0.0;
+  DF rs32, rr32;
+#pragma unroll
+  for (int k = 0; k < kOut; ++k) {
+    const int r = r0 + warp + kTileWarps * k;
+    if (r >= r1) continue;
+    const int rr = r - r0 + 2;
+    const float4 tc = lds4(sT, rr, lane), B = lds4(sB, rr, lane);
+    const float4 v = jac4(tc, lds4(sD, rr, lane), B,
+                          arow(lds4(sT, rr - 1, lane), tc, lds4(sT, rr + 1, lane), lds4(sU, rr, lane),
+                               lds4(sV, rr, lane), lds4(sV, rr - 1, lane), lane));
+    if (!out) continue;
+    const size_t o = (size_t)r * f.ld + j;
+    if (MODE == kUpCoarse) {
+      *reinterpret_cast<float4*>(f.t + o) = v;
+    } else if (MODE == kUp32) {
+      const float4 sv = make_float4(mk[k].x ? 0.f : v.x, mk[k].y ? 0.f : v.y, mk[k].z ? 0.f : v.z,
+                                    mk[k].w ? 0.f : v.w);
+      *reinterpret_cast<float4*>(s32 + o) = sv;
+      if (pa) {
+        // r is the cycle's right-hand side (zero beyond column W - 1, as is s there)
+        rs32.add_prod(B.x, sv.x);
+        rs32.add_prod(B.y, sv.y);
+        rs32.add_prod(B.z, sv.z);
+        rs32.add_prod(B.w, sv.w);
+        rr32.add_prod(B.x, B.x);
+        rr32.add_prod(B.y, B.y);
+        rr32.add_prod(B.z, B.z);
+        rr32.add_prod(B.w, B.w);
+      }
+    } else {
+      // FP64 s, 0 on masked pixels and nothing beyond column W - 1
+      const double sv[4] = {mk[k].x ? 0.0 : (double)v.x, mk[k].y ? 0.0 : (double)v.y,
+                            mk[k].z ? 0.0 : (double)v.z, mk[k].w ? 0.0 : (double)v.w};
+      if (j + 4 <= f.W) {
+        *reinterpret_cast<double2*>(s + o) = make_double2(sv[0], sv[1]);
+        *reinterpret_cast<double2*>(s + o + 2) = make_double2(sv[2], sv[3]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (j + q < f.W) s[o + q] = sv[q];
+      }
+      if (pa && rv) {
+        const double rk[4] = {ra[k].x, ra[k].y, rb[k].x, rb[k].y};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (j + q < f.W) {
+            rs = fma(rk[q], sv[q], rs);
+            rr2 = fma(rk[q], rk[q], rr2);
+          }
+      }
+    }
+  }
+  if (MAP && pa) {
+    if (MODE == kUp32) {
+      rs = rs32.value();
+      rr2 = rr32.value();
+    }
+    // block sums in warp order, then the arrival of the block as one unit
+    rs = warp_sum(rs);
+    rr2 = warp_sum(rr2);
+    if (lane == 0) {
+      red[0][warp] = rs;
+      red[1][warp] = rr2;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const PcgArgs a = *pa;
+      const double v0 = lane < kTileWarps ? red[0][lane] : 0.0, v1 = lane < kTileWarps ? red[1][lane] : 0.0;
+      warp_arrive_fcg(a, a.maps[0], a.st, (int)blockIdx.x, (int)gridDim.x, v0, v1, lane);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- row walkers (wide grids)
+// On grids wide and tall enough to give every SM a full wave of warps, the same two
+// fused steps run as row walkers: a warp owns one 128-column window (as in a tile)
+// and a band of rows, and walks down the band keeping the last rows of every
+// quantity in registers, the next row's loads issued one row ahead.  There the
+// walkers keep more bytes in flight than shared-memory tiles, whose 61 KB per
+// block leave little of the SM's L1 for the tile loads (measured at 2048^2:
+// map-grid up step 45 us as a walker, 70 us as tiles; the 512^2 and smaller grids
+// go the other way, 4.6-7.3 us as tiles against 8-9 us).
 __device__ __forceinline__ bool walk_warp(int W, int bands, int& seg, int& band, int& j, int& lane) {
   const int nseg = (W + kSegOut - 1) / kSegOut;
   const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -435,7 +671,7 @@ __device__ __forceinline__ DownRow down_row(const Grid& f, int r, int j) {
 }
 
 // pre-smoothing + residual + restriction for the coarse rows [RB band, RB band + RB)
-__global__ void __launch_bounds__(256, 2) k_mg_down(Grid f, Grid c, int RB, const MapState* S) {
+__global__ void __launch_bounds__(256, 2) k_mg_down_w(Grid f, Grid c, int RB, const MapState* S) {
   if (skip_map(S)) return;
   int seg, band, j, lane;
   if (!walk_warp(f.W, (c.H + RB - 1) / RB, seg, band, j, lane)) return;
@@ -520,15 +756,10 @@ __device__ __forceinline__ UpRow up_row(const Grid& f, const Grid& c, const floa
   return u;
 }
 
-// prolongation + correction + both post-sweeps for the rows [R band, R band + R).
-// xc: the coarse grid's corrected solution.  MODE kUpCoarse: s to the grid's t plane.
-// kUp64 (the map's grid): s in FP64; with pa, r^T s and r^T r (r: the map's FP64
-// residual) over the warp's pixels arrive in the flexible CG's dot phase.  kUp32 (the
-// map's grid, mixed flexible CG): s in FP32 into s32; with pa, the same dot phase in
-// double-float sums of exact FP32 products, r being the cycle's right-hand side.
-enum { kUpCoarse = 0, kUp64 = 1, kUp32 = 2 };
+// prolongation + correction + both post-sweeps for the rows [R band, R band + R); modes
+// and outputs as k_mg_up_t (the dot phase's arrival counted per warp).
 template <int MODE>
-__global__ void __launch_bounds__(256, 2) k_mg_up(Grid f, Grid c, const float* __restrict__ xc, int R,
+__global__ void __launch_bounds__(256, 2) k_mg_up_w(Grid f, Grid c, const float* __restrict__ xc, int R,
                                                   const uint8_t* mask, double* s, const double* __restrict__ rv,
                                                   float* s32, const PcgArgs* pa, const MapState* S) {
   constexpr bool MAP = MODE != kUpCoarse;
@@ -618,7 +849,7 @@ __global__ void __launch_bounds__(256, 2) k_mg_up(Grid f, Grid c, const float* _
   }
 }
 
-// level 0 without a walker (grids narrower than 64 columns): the FP64 s rounded to FP32
+// level 0 without the fused kernels (grids narrower than 64 columns): the FP64 s rounded to FP32
 __global__ void k_mg_to32(const double* __restrict__ s, float* s32, Grid g, const MapState* S) {
   if (skip_map(S)) return;
   MG_LOOP(t, (long long)g.H * g.W) {
@@ -845,8 +1076,11 @@ using namespace mg;
 
 struct MgPlan {
   std::vector<Grid> g;   // FP32 grids; g[0] has the map's size and pitch
-  std::vector<int> walk_rb, walk_r;  // per grid: walker bands (coarse rows down, rows up), 0: per-step kernels
-  int dots_warps = 0;    // warps of the map's up walker when it also does the dot phase (0: it does not)
+  // per grid: kind of the fused kernels (kPerStep, kWalk, kTile) and their rows (walker:
+  // coarse rows per band down, rows per band up; tile: rows per tile down (even) and up)
+  std::vector<int> kind, rows_down, rows_up;
+  int dots_units = 0;    // warps (walker) or blocks (tile) of the map grid's up kernel when it
+                         // also does the dot phase (0: it does not)
   int lt = -1;           // first grid handled by the shared-memory tail kernel (-1: none)
   TailGrids tail{};
   size_t tail_smem = 0;
@@ -870,14 +1104,33 @@ size_t mg_bytes(int H, int W) {
   return bytes + 256;
 }
 
-constexpr int kVecMinW = 64;  // grids at least this wide use the vector kernels and walkers
+constexpr int kVecMinW = 64;  // grids at least this wide use the fused kernels
+enum { kPerStep = 0, kWalk = 1, kTile = 2 };
 
-// Rows per band: at least rmin, and no more warps than target.
+// Rows per walker band: at least rmin, and no more warps than target.
 static int walk_rows(int rows, int W, int rmin, long long target) {
   const long long nseg = (W + kSegOut - 1) / kSegOut;
   int R = rmin;
   while (nseg * ((rows + R - 1) / R) > target) ++R;
   return R;
+}
+
+static unsigned walk_blocks(const Grid& f, int rows, int R) {
+  const long long warps = (long long)((f.W + kSegOut - 1) / kSegOut) * ((rows + R - 1) / R);
+  return (unsigned)((warps + 7) / 8);
+}
+
+// Rows per tile: the most (up to kTileMaxRows) that still give every SM two blocks,
+// 2 at least; even for the down kernel, whose coarse rows must not straddle tiles.
+static int tile_rows(int H, int W, int nsm, bool even) {
+  const long long nseg = (W + kSegOut - 1) / kSegOut;
+  int TR = kTileMaxRows;
+  while (TR > 2 && nseg * ((H + TR - 1) / TR) < 2LL * nsm) TR -= even ? 2 : 1;
+  return TR;
+}
+
+static unsigned tile_blocks(const Grid& f, int TR) {
+  return (unsigned)(((f.W + kSegOut - 1) / kSegOut) * ((f.H + TR - 1) / TR));
 }
 
 MgPlan* mg_create(const MapDesc& M, void* mem, int nsm, int ntiles) {
@@ -924,19 +1177,43 @@ MgPlan* mg_create(const MapDesc& M, void* mem, int nsm, int ntiles) {
     c.t = take(n);
     p->g.push_back(c);
   }
-  // walker bands: the shortest bands (fewest sequential rows per warp) that keep the
-  // warps to one resident wave of 16 per SM; on the map's grid also no more warps than
-  // the plan has tiles (the dot phase's partial arrays)
-  const long long target = 16LL * nsm;
+  // tiles of the fused kernels on every grid at least kVecMinW wide; the map grid's up
+  // kernel carries the dot phase if its blocks fit the plan's per-tile partial arrays
+  // walkers where even two-row bands give a full wave of 16 warps per SM, tiles on the
+  // smaller grids (see the walker section for the measurements)
+  const long long wave = 16LL * nsm;
   for (size_t l = 0; l < p->g.size(); ++l) {
     const Grid& f = p->g[l];
-    const bool walk = l + 1 < p->g.size() && f.W >= kVecMinW;
-    p->walk_rb.push_back(walk ? walk_rows(p->g[l + 1].H, f.W, 1, target) : 0);
-    p->walk_r.push_back(walk ? walk_rows(f.H, f.W, 2, l == 0 ? (target < ntiles ? target : ntiles) : target) : 0);
+    const long long nseg = (f.W + kSegOut - 1) / kSegOut;
+    int kind = kPerStep, rd = 0, ru = 0;
+    if (l + 1 < p->g.size() && f.W >= kVecMinW) {
+      if (nseg * ((f.H + 1) / 2) >= wave) {
+        kind = kWalk;
+        rd = walk_rows(p->g[l + 1].H, f.W, 1, wave);
+        ru = walk_rows(f.H, f.W, 2, l == 0 ? (wave < ntiles ? wave : ntiles) : wave);
+      } else {
+        kind = kTile;
+        rd = tile_rows(f.H, f.W, nsm, true);
+        ru = tile_rows(f.H, f.W, nsm, false);
+      }
+    }
+    p->kind.push_back(kind);
+    p->rows_down.push_back(rd);
+    p->rows_up.push_back(ru);
   }
-  if (p->walk_r[0] > 0) {
-    const long long n = (long long)((M.W + kSegOut - 1) / kSegOut) * ((M.H + p->walk_r[0] - 1) / p->walk_r[0]);
-    if (n >= kArriveGroups && n <= ntiles) p->dots_warps = (int)n;
+  if (p->kind[0] != kPerStep) {
+    const long long n = p->kind[0] == kWalk
+                            ? (long long)((M.W + kSegOut - 1) / kSegOut) * ((M.H + p->rows_up[0] - 1) / p->rows_up[0])
+                            : (long long)tile_blocks(p->g[0], p->rows_up[0]);
+    if (n >= kArriveGroups && n <= ntiles) p->dots_units = (int)n;
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_mg_down_t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    cudaFuncSetAttribute(k_mg_up_t<kUpCoarse>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    cudaFuncSetAttribute(k_mg_up_t<kUp64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    cudaFuncSetAttribute(k_mg_up_t<kUp32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    attr = true;
   }
   // the tail: the smallest suffix of grids, from the first with at most kTailMax unknowns,
   // if it fits the shared-memory budget and there is a grid before it
@@ -963,7 +1240,7 @@ MgPlan* mg_create(const MapDesc& M, void* mem, int nsm, int ntiles) {
 
 void mg_destroy(MgPlan* p) { delete p; }
 
-bool mg_fuses_dots(const MgPlan& p) { return p.dots_warps > 0; }
+bool mg_fuses_dots(const MgPlan& p) { return p.dots_units > 0; }
 
 static unsigned row_blocks(const Grid& f, int rows) {
   const long long warps = (long long)rows * ((f.W + 127) / 128);
@@ -990,11 +1267,6 @@ cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st, bool l
 // s = V-cycle(r) on the map's planes; mask zeroes s.
 float* mg_input(const MgPlan& p) { return p.g[0].b; }
 
-static unsigned walk_blocks(const Grid& f, int rows, int R) {
-  const long long warps = (long long)((f.W + kSegOut - 1) / kSegOut) * ((rows + R - 1) / R);
-  return (unsigned)((warps + 7) / 8);
-}
-
 cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st, bool packed,
                      const PcgArgs* dots, float* s32) {
   const int L = (int)p.g.size();
@@ -1009,9 +1281,12 @@ cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cu
   const int stop = p.lt > 0 ? p.lt : L - 1;  // grids [0, stop) by per-grid kernels
   for (int l = 0; l < stop; ++l) {
     const Grid& f = p.g[l];
-    if (p.walk_rb[l] > 0) {
+    if (p.kind[l] == kWalk) {
       const Grid& c = p.g[l + 1];
-      k_mg_down<<<walk_blocks(f, c.H, p.walk_rb[l]), 256, 0, st>>>(f, c, p.walk_rb[l], S);
+      k_mg_down_w<<<walk_blocks(f, c.H, p.rows_down[l]), 256, 0, st>>>(f, c, p.rows_down[l], S);
+    } else if (p.kind[l] == kTile) {
+      const Grid& c = p.g[l + 1];
+      k_mg_down_t<<<tile_blocks(f, p.rows_down[l]), kTileThreads, kTileSmem, st>>>(f, c, p.rows_down[l], S);
     } else if (f.W >= kVecMinW) {
       k_mg_sweep_v<kSrcX1><<<row_blocks(f, f.H), 256, 0, st>>>(f, Grid{}, f.x, nullptr, nullptr, S);
       k_mg_res_v<<<row_blocks(f, p.g[l + 1].H), 256, 0, st>>>(f, p.g[l + 1], S);
@@ -1034,22 +1309,28 @@ cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cu
   }
   for (int l = stop - 1; l >= 0; --l) {
     const Grid& f = p.g[l];
-    if (p.walk_r[l] > 0) {
-      // the coarse grid's corrected solution: the t plane if a walker made it, else x
+    if (p.kind[l] != kPerStep) {
+      // the coarse grid's corrected solution: the t plane if a fused kernel made it, else x
       const Grid& c = p.g[l + 1];
-      const float* xc = (l + 1 < stop && p.walk_r[l + 1] > 0) ? c.t : c.x;
-      const int R = p.walk_r[l];
-      if (l == 0 && s32) {
-        const bool d = dots && p.dots_warps > 0;
-        k_mg_up<kUp32><<<walk_blocks(f, f.H, R), 256, 0, st>>>(f, c, xc, R, mask, nullptr, nullptr, s32,
-                                                               d ? dots : nullptr, S);
-      } else if (l == 0) {
-        const bool d = dots && p.dots_warps > 0;
-        k_mg_up<kUp64><<<walk_blocks(f, f.H, R), 256, 0, st>>>(f, c, xc, R, mask, p.s0, d ? p.r0 : nullptr,
-                                                               nullptr, d ? dots : nullptr, S);
+      const float* xc = (l + 1 < stop && p.kind[l + 1] != kPerStep) ? c.t : c.x;
+      const int R = p.rows_up[l];
+      const bool d = l == 0 && dots && p.dots_units > 0;
+      const PcgArgs* pa = d ? dots : nullptr;
+      const int mode = l > 0 ? kUpCoarse : (s32 ? kUp32 : kUp64);
+      const double* rv = (mode == kUp64 && d) ? p.r0 : nullptr;
+      double* s64 = mode == kUp64 ? p.s0 : nullptr;
+      const uint8_t* mk = l == 0 ? mask : nullptr;
+      float* o32 = mode == kUp32 ? s32 : nullptr;
+      if (p.kind[l] == kWalk) {
+        const unsigned nb = walk_blocks(f, f.H, R);
+        if (mode == kUp32) k_mg_up_w<kUp32><<<nb, 256, 0, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
+        else if (mode == kUp64) k_mg_up_w<kUp64><<<nb, 256, 0, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
+        else k_mg_up_w<kUpCoarse><<<nb, 256, 0, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
       } else {
-        k_mg_up<kUpCoarse><<<walk_blocks(f, f.H, R), 256, 0, st>>>(f, c, xc, R, nullptr, nullptr, nullptr,
-                                                                   nullptr, nullptr, S);
+        const unsigned nb = tile_blocks(f, R);
+        if (mode == kUp32) k_mg_up_t<kUp32><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
+        else if (mode == kUp64) k_mg_up_t<kUp64><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
+        else k_mg_up_t<kUpCoarse><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
       }
     } else if (f.W >= kVecMinW) {
       k_mg_sweep_v<kSrcXP><<<row_blocks(f, f.H), 256, 0, st>>>(f, p.g[l + 1], f.t, nullptr, nullptr, S);
@@ -1061,7 +1342,7 @@ cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cu
                                                                     l == 0 ? p.s0 : nullptr, S);
     }
   }
-  if (s32 && !(p.walk_r[0] > 0 && stop > 0))
+  if (s32 && !(p.kind[0] != kPerStep && stop > 0))
     k_mg_to32<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(p.s0, s32, g0, S);
   return cudaGetLastError();
 }

@@ -529,7 +529,7 @@ def fcg_roofline(native, H, W, psi, mask, w, precond, timed_plan, prec="f64"):
         phases[ph] = ent
     dom = max((k for k in phases if "achieved" in phases[k]), key=lambda k: phases[k]["ms_total"])
     d = phases[dom]
-    tpx = profile_traffic(f"fcg_{precond}_{dom}_c2_2048")
+    tpx = profile_traffic(f"fcg_{prec}_{precond}_{dom}_c2_2048")
     return {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
             "frac": d["frac"], "traffic": (tpx * H * W if tpx is not None else None),
             "kernel": f"{d['kernel']} (flexible-CG phase {dom}, dominant)", "peak_source": d["peak_source"],

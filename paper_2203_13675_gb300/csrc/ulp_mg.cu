@@ -663,31 +663,78 @@ __device__ __forceinline__ bool walk_warp(int W, int bands, int& seg, int& band,
 
 // The raw loads of one row, issued one row ahead of the arithmetic that uses them
 // (a warp's walk is otherwise one memory round trip per row).
-struct DownRow {
-  float4 U, V, D, B;
+// Row loads go through a per-warp ring of kRing slots in shared memory, filled by
+// cp.async kLead rows ahead of the arithmetic: each lane copies its own 16-byte pieces
+// (zero-filled outside the grid and beyond column W - 1 by the copy's source size) and
+// reads back only what it copied, so no barrier is needed, and the bytes in flight no
+// longer cost registers.  wait_group is the hardware's own wait on the lane's copies.
+constexpr int kLead = 3;
+constexpr int kRing = kLead + 1;   // the slot being read is never the one being filled
+constexpr int kWalkWarps = 4;      // 128-thread blocks
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gsrc), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa), "l"(gsrc), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gsrc), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_lead() { asm volatile("cp.async.wait_group %0;" ::"n"(kLead) : "memory"); }
+
+// bytes of the lane's float4 at (r, j) that lie in the grid (0, 4, 8, 12 or 16)
+__device__ __forceinline__ int row_bytes(const Grid& f, int r, int j) {
+  if (r < 0 || r >= f.H || j < 0 || j >= f.W) return 0;
+  const int n = f.W - j;
+  return n >= 4 ? 16 : 4 * n;
+}
+
+// one slot of the down walker's ring: U, V, D^-1, b of one row (float4 per lane)
+struct DownSlot {
+  float4 U[32], V[32], D[32], B[32];
 };
-__device__ __forceinline__ DownRow down_row(const Grid& f, int r, int j) {
-  return DownRow{lrow(f.U, f, r, j), lrow(f.V, f, r, j), lrow(f.Dinv, f, r, j), lrow(f.b, f, r, j)};
+
+__device__ __forceinline__ void down_issue(DownSlot& sl, const Grid& f, int r, int j, int lane) {
+  const int nb = row_bytes(f, r, j);
+  const size_t o = nb ? (size_t)r * f.ld + j : 0;
+  cp_async16(&sl.U[lane], f.U + o, nb);
+  cp_async16(&sl.V[lane], f.V + o, nb);
+  cp_async16(&sl.D[lane], f.Dinv + o, nb);
+  cp_async16(&sl.B[lane], f.b + o, nb);
 }
 
 // pre-smoothing + residual + restriction for the coarse rows [RB band, RB band + RB)
-__global__ void __launch_bounds__(256, 2) k_mg_down_w(Grid f, Grid c, int RB, const MapState* S) {
+__global__ void __launch_bounds__(kWalkWarps * 32) k_mg_down_w(Grid f, Grid c, int RB, const MapState* S) {
   if (skip_map(S)) return;
+  extern __shared__ float4 wsm4[];
   int seg, band, j, lane;
   if (!walk_warp(f.W, (c.H + RB - 1) / RB, seg, band, j, lane)) return;
+  DownSlot* ring = reinterpret_cast<DownSlot*>(wsm4) + (threadIdx.x >> 5) * kRing;
   const bool out = lane >= 1 && lane <= 30 && j < f.W;
   const int I0 = band * RB, I1 = min(c.H, I0 + RB);
   const int r0 = 2 * I0, r1 = min(f.H, 2 * I1);
+  const int rb = r0 - 2, re = r1 + 1;  // rows walked
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
   // rows r-1, r-2, r-3 of the window (m1, m2, m3)
   float4 Um1 = z, Um2 = z, Vm1 = z, Vm2 = z, Vm3 = z, Dm1 = z, Bm1 = z, Bm2 = z;
   float4 X1m1 = z, X1m2 = z, X2m2 = z, X2m3 = z;
   float lo = 0.f, hi = 0.f;
-  DownRow nx = down_row(f, r0 - 2, j);
-  for (int r = r0 - 2; r <= r1 + 1; ++r) {
-    const DownRow cu = nx;
-    if (r + 1 <= r1 + 1) nx = down_row(f, r + 1, j);
-    const float4 U = cu.U, V = cu.V, D = cu.D, B = cu.B;
+#pragma unroll
+  for (int k = 0; k < kLead; ++k) {
+    if (rb + k <= re) down_issue(ring[k], f, rb + k, j, lane);
+    cp_commit();
+  }
+  for (int r = rb; r <= re; ++r) {
+    if (r + kLead <= re) down_issue(ring[(r + kLead - rb) % kRing], f, r + kLead, j, lane);
+    cp_commit();
+    cp_wait_lead();
+    const DownSlot& sl = ring[(r - rb) % kRing];
+    const float4 U = sl.U[lane], V = sl.V[lane], D = sl.D[lane], B = sl.B[lane];
     const float4 X1 = make_float4(kOmegaF * D.x * B.x, kOmegaF * D.y * B.y, kOmegaF * D.z * B.z, kOmegaF * D.w * B.w);
     // x2 at row q = r - 1
     const int q = r - 1;
@@ -719,66 +766,79 @@ __global__ void __launch_bounds__(256, 2) k_mg_down_w(Grid f, Grid c, int RB, co
   }
 }
 
-struct UpRow {
-  float4 U, V, D, B, XP;  // row r
-  double2 ra, rb;         // the map's r at row r - 2 (dot phase)
-  uchar4 mk;              // the mask at row r - 2
+// one slot of the up walker's ring: U, V, D^-1, b, x of row r, the coarse x of its
+// aggregates, and on the map's grid the mask and FP64 r of row r - 2
+struct UpSlot {
+  float4 U[32], V[32], D[32], B[32], X[32];
+  float2 XC[32];
+  uchar4 MK[32];
+  double2 RA[32], RB[32];
 };
-template <bool MAP>
-__device__ __forceinline__ UpRow up_row(const Grid& f, const Grid& c, const float* xc, const uint8_t* mask,
-                                        const double* rv, int r, int j) {
-  UpRow u;
-  u.U = lrow(f.U, f, r, j);
-  u.V = lrow(f.V, f, r, j);
-  u.D = lrow(f.Dinv, f, r, j);
-  u.B = lrow(f.b, f, r, j);
-  u.XP = lrow(f.x, f, r, j);
-  if (r >= 0 && r < f.H && j >= 0 && j < f.W) {
-    const float2 e = *reinterpret_cast<const float2*>(xc + (size_t)(r >> 1) * c.ld + (j >> 1));
-    u.XP = make_float4(u.XP.x + kCCF * e.x, u.XP.y + kCCF * e.x, u.XP.z + kCCF * e.y, u.XP.w + kCCF * e.y);
-    if (j + 1 >= f.W) u.XP.y = 0.f;
-    if (j + 2 >= f.W) u.XP.z = 0.f;
-    if (j + 3 >= f.W) u.XP.w = 0.f;
-  }
-  u.ra = u.rb = make_double2(0.0, 0.0);
-  u.mk = make_uchar4(0, 0, 0, 0);
-  if (MAP) {
+
+template <int MODE>
+__device__ __forceinline__ void up_issue(UpSlot& sl, const Grid& f, const Grid& c, const float* xc,
+                                         const uint8_t* mask, const double* rv, int r, int j, int lane) {
+  const int nb = row_bytes(f, r, j);
+  const size_t o = nb ? (size_t)r * f.ld + j : 0;
+  cp_async16(&sl.U[lane], f.U + o, nb);
+  cp_async16(&sl.V[lane], f.V + o, nb);
+  cp_async16(&sl.D[lane], f.Dinv + o, nb);
+  cp_async16(&sl.B[lane], f.b + o, nb);
+  cp_async16(&sl.X[lane], f.x + o, nb);
+  cp_async8(&sl.XC[lane], nb ? xc + (size_t)(r >> 1) * c.ld + (j >> 1) : xc, nb ? 8 : 0);
+  if (MODE != kUpCoarse) {
     const int p = r - 2;
-    if (p >= 0 && p < f.H && j >= 0 && j < f.W) {
-      const size_t o = (size_t)p * f.ld + j;
-      if (mask) u.mk = *reinterpret_cast<const uchar4*>(mask + o);
-      if (rv) {
-        u.ra = *reinterpret_cast<const double2*>(rv + o);
-        u.rb = *reinterpret_cast<const double2*>(rv + o + 2);
-      }
+    const int pb = row_bytes(f, p, j);
+    const size_t op = pb ? (size_t)p * f.ld + j : 0;
+    if (mask) cp_async4(&sl.MK[lane], mask + op, pb ? 4 : 0);
+    if (MODE == kUp64 && rv) {
+      cp_async16(&sl.RA[lane], rv + op, pb ? 16 : 0);
+      cp_async16(&sl.RB[lane], rv + op + (pb ? 2 : 0), pb ? 16 : 0);
     }
   }
-  return u;
 }
 
 // prolongation + correction + both post-sweeps for the rows [R band, R band + R); modes
 // and outputs as k_mg_up_t (the dot phase's arrival counted per warp).
 template <int MODE>
-__global__ void __launch_bounds__(256, 2) k_mg_up_w(Grid f, Grid c, const float* __restrict__ xc, int R,
-                                                  const uint8_t* mask, double* s, const double* __restrict__ rv,
-                                                  float* s32, const PcgArgs* pa, const MapState* S) {
+__global__ void __launch_bounds__(kWalkWarps * 32) k_mg_up_w(Grid f, Grid c, const float* __restrict__ xc, int R,
+                                                             const uint8_t* mask, double* s,
+                                                             const double* __restrict__ rv, float* s32,
+                                                             const PcgArgs* pa, const MapState* S) {
   constexpr bool MAP = MODE != kUpCoarse;
   if (skip_map(S)) return;
+  extern __shared__ float4 wsm4[];
   int seg, band, j, lane;
   const int bands = (f.H + R - 1) / R;
   if (!walk_warp(f.W, bands, seg, band, j, lane)) return;
+  UpSlot* ring = reinterpret_cast<UpSlot*>(wsm4) + (threadIdx.x >> 5) * kRing;
   const bool out = lane >= 1 && lane <= 30 && j < f.W;
   const int i0 = band * R, i1 = min(f.H, i0 + R);
+  const int rb = i0 - 2, re = i1 + 1;
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 Um1 = z, Um2 = z, Vm1 = z, Vm2 = z, Vm3 = z, Dm1 = z, Dm2 = z, Bm1 = z, Bm2 = z;
   float4 XPm1 = z, XPm2 = z, Tm2 = z, Tm3 = z;
   double rs = 0.0, rr = 0.0;
   DF rs32, rr32;
-  UpRow nx = up_row<MAP>(f, c, xc, mask, rv, i0 - 2, j);
-  for (int r = i0 - 2; r <= i1 + 1; ++r) {
-    const UpRow cu = nx;
-    if (r + 1 <= i1 + 1) nx = up_row<MAP>(f, c, xc, mask, rv, r + 1, j);
-    const float4 U = cu.U, V = cu.V, D = cu.D, B = cu.B, XP = cu.XP;
+#pragma unroll
+  for (int k = 0; k < kLead; ++k) {
+    if (rb + k <= re) up_issue<MODE>(ring[k], f, c, xc, mask, rv, rb + k, j, lane);
+    cp_commit();
+  }
+  for (int r = rb; r <= re; ++r) {
+    if (r + kLead <= re) up_issue<MODE>(ring[(r + kLead - rb) % kRing], f, c, xc, mask, rv, r + kLead, j, lane);
+    cp_commit();
+    cp_wait_lead();
+    const UpSlot& sl = ring[(r - rb) % kRing];
+    const float4 U = sl.U[lane], V = sl.V[lane], D = sl.D[lane], B = sl.B[lane];
+    float4 XP = sl.X[lane];
+    if (r >= 0 && r < f.H && j >= 0 && j < f.W) {
+      const float2 e = sl.XC[lane];
+      XP = make_float4(XP.x + kCCF * e.x, XP.y + kCCF * e.x, XP.z + kCCF * e.y, XP.w + kCCF * e.y);
+      if (j + 1 >= f.W) XP.y = 0.f;
+      if (j + 2 >= f.W) XP.z = 0.f;
+      if (j + 3 >= f.W) XP.w = 0.f;
+    }
     // t at row q = r - 1
     const int q = r - 1;
     float4 T = z;
@@ -790,9 +850,9 @@ __global__ void __launch_bounds__(256, 2) k_mg_up_w(Grid f, Grid c, const float*
       const size_t o = (size_t)p * f.ld + j;
       if (MODE == kUpCoarse) {
         if (out) *reinterpret_cast<float4*>(f.t + o) = v;
-      } else if (MODE == kUp32) {
-        if (out) {
-          const uchar4 mk = cu.mk;
+      } else if (out) {
+        const uchar4 mk = mask ? sl.MK[lane] : make_uchar4(0, 0, 0, 0);
+        if (MODE == kUp32) {
           const float4 sv = make_float4(mk.x ? 0.f : v.x, mk.y ? 0.f : v.y, mk.z ? 0.f : v.z, mk.w ? 0.f : v.w);
           *reinterpret_cast<float4*>(s32 + o) = sv;
           if (pa) {
@@ -806,28 +866,28 @@ __global__ void __launch_bounds__(256, 2) k_mg_up_w(Grid f, Grid c, const float*
             rr32.add_prod(Bm2.z, Bm2.z);
             rr32.add_prod(Bm2.w, Bm2.w);
           }
-        }
-      } else if (out) {
-        // the map's grid: FP64 s, 0 on masked pixels and nothing beyond column W - 1
-        const uchar4 mk = cu.mk;
-        const double sv[4] = {mk.x ? 0.0 : (double)v.x, mk.y ? 0.0 : (double)v.y, mk.z ? 0.0 : (double)v.z,
-                              mk.w ? 0.0 : (double)v.w};
-        if (j + 4 <= f.W) {
-          *reinterpret_cast<double2*>(s + o) = make_double2(sv[0], sv[1]);
-          *reinterpret_cast<double2*>(s + o + 2) = make_double2(sv[2], sv[3]);
         } else {
+          // the map's grid: FP64 s, 0 on masked pixels and nothing beyond column W - 1
+          const double sv[4] = {mk.x ? 0.0 : (double)v.x, mk.y ? 0.0 : (double)v.y, mk.z ? 0.0 : (double)v.z,
+                                mk.w ? 0.0 : (double)v.w};
+          if (j + 4 <= f.W) {
+            *reinterpret_cast<double2*>(s + o) = make_double2(sv[0], sv[1]);
+            *reinterpret_cast<double2*>(s + o + 2) = make_double2(sv[2], sv[3]);
+          } else {
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (j + k < f.W) s[o + k] = sv[k];
-        }
-        if (rv) {
-          const double rk[4] = {cu.ra.x, cu.ra.y, cu.rb.x, cu.rb.y};
+            for (int k = 0; k < 4; ++k)
+              if (j + k < f.W) s[o + k] = sv[k];
+          }
+          if (rv) {
+            const double2 ra = sl.RA[lane], rb2 = sl.RB[lane];
+            const double rk[4] = {ra.x, ra.y, rb2.x, rb2.y};
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (j + k < f.W) {
-              rs = fma(rk[k], sv[k], rs);
-              rr = fma(rk[k], rk[k], rr);
-            }
+            for (int k = 0; k < 4; ++k)
+              if (j + k < f.W) {
+                rs = fma(rk[k], sv[k], rs);
+                rr = fma(rk[k], rk[k], rr);
+              }
+          }
         }
       }
     }
@@ -848,6 +908,9 @@ __global__ void __launch_bounds__(256, 2) k_mg_up_w(Grid f, Grid c, const float*
     warp_arrive_fcg(a, a.maps[0], a.st, band * nseg + seg, nseg * bands, rs, rr, lane);
   }
 }
+
+constexpr size_t kDownRingSmem = (size_t)kWalkWarps * kRing * sizeof(DownSlot);
+constexpr size_t kUpRingSmem = (size_t)kWalkWarps * kRing * sizeof(UpSlot);
 
 // level 0 without the fused kernels (grids narrower than 64 columns): the FP64 s rounded to FP32
 __global__ void k_mg_to32(const double* __restrict__ s, float* s32, Grid g, const MapState* S) {
@@ -1117,7 +1180,7 @@ static int walk_rows(int rows, int W, int rmin, long long target) {
 
 static unsigned walk_blocks(const Grid& f, int rows, int R) {
   const long long warps = (long long)((f.W + kSegOut - 1) / kSegOut) * ((rows + R - 1) / R);
-  return (unsigned)((warps + 7) / 8);
+  return (unsigned)((warps + kWalkWarps - 1) / kWalkWarps);
 }
 
 // Rows per tile: the most (up to kTileMaxRows) that still give every SM two blocks,
@@ -1177,11 +1240,31 @@ MgPlan* mg_create(const MapDesc& M, void* mem, int nsm, int ntiles) {
     c.t = take(n);
     p->g.push_back(c);
   }
-  // tiles of the fused kernels on every grid at least kVecMinW wide; the map grid's up
-  // kernel carries the dot phase if its blocks fit the plan's per-tile partial arrays
-  // walkers where even two-row bands give a full wave of 16 warps per SM, tiles on the
-  // smaller grids (see the walker section for the measurements)
-  const long long wave = 16LL * nsm;
+  // fused kernels (walkers or tiles) on every grid at least kVecMinW wide; the map grid's
+  // up kernel carries the dot phase if its warps or blocks fit the plan's per-tile partial
+  // arrays
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_mg_down_t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    cudaFuncSetAttribute(k_mg_up_t<kUpCoarse>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    cudaFuncSetAttribute(k_mg_up_t<kUp64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    cudaFuncSetAttribute(k_mg_up_t<kUp32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    cudaFuncSetAttribute(k_mg_down_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDownRingSmem);
+    cudaFuncSetAttribute(k_mg_up_w<kUpCoarse>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpRingSmem);
+    cudaFuncSetAttribute(k_mg_up_w<kUp64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpRingSmem);
+    cudaFuncSetAttribute(k_mg_up_w<kUp32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpRingSmem);
+    attr = true;
+  }
+  // one resident wave of each walker (the ring's shared memory limits the up walker to
+  // three blocks per SM): more warps than that run as a second, mostly idle wave
+  int occ_down = 0, occ_up = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_down, k_mg_down_w, kWalkWarps * 32, kDownRingSmem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_up, k_mg_up_w<kUp32>, kWalkWarps * 32, kUpRingSmem);
+  const long long wave_down = (long long)(occ_down > 0 ? occ_down : 1) * kWalkWarps * nsm;
+  const long long wave_up = (long long)(occ_up > 0 ? occ_up : 1) * kWalkWarps * nsm;
+  // walkers where even two-row bands fill a wave, tiles on the smaller grids (see the
+  // walker section for the measurements)
+  const long long wave = wave_up < wave_down ? wave_up : wave_down;
   for (size_t l = 0; l < p->g.size(); ++l) {
     const Grid& f = p->g[l];
     const long long nseg = (f.W + kSegOut - 1) / kSegOut;
@@ -1189,8 +1272,8 @@ MgPlan* mg_create(const MapDesc& M, void* mem, int nsm, int ntiles) {
     if (l + 1 < p->g.size() && f.W >= kVecMinW) {
       if (nseg * ((f.H + 1) / 2) >= wave) {
         kind = kWalk;
-        rd = walk_rows(p->g[l + 1].H, f.W, 1, wave);
-        ru = walk_rows(f.H, f.W, 2, l == 0 ? (wave < ntiles ? wave : ntiles) : wave);
+        rd = walk_rows(p->g[l + 1].H, f.W, 1, wave_down);
+        ru = walk_rows(f.H, f.W, 2, l == 0 ? (wave_up < ntiles ? wave_up : ntiles) : wave_up);
       } else {
         kind = kTile;
         rd = tile_rows(f.H, f.W, nsm, true);
@@ -1207,14 +1290,7 @@ MgPlan* mg_create(const MapDesc& M, void* mem, int nsm, int ntiles) {
                             : (long long)tile_blocks(p->g[0], p->rows_up[0]);
     if (n >= kArriveGroups && n <= ntiles) p->dots_units = (int)n;
   }
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_mg_down_t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
-    cudaFuncSetAttribute(k_mg_up_t<kUpCoarse>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
-    cudaFuncSetAttribute(k_mg_up_t<kUp64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
-    cudaFuncSetAttribute(k_mg_up_t<kUp32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
-    attr = true;
-  }
+
   // the tail: the smallest suffix of grids, from the first with at most kTailMax unknowns,
   // if it fits the shared-memory budget and there is a grid before it
   const int L = (int)p->g.size();
@@ -1283,7 +1359,7 @@ cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cu
     const Grid& f = p.g[l];
     if (p.kind[l] == kWalk) {
       const Grid& c = p.g[l + 1];
-      k_mg_down_w<<<walk_blocks(f, c.H, p.rows_down[l]), 256, 0, st>>>(f, c, p.rows_down[l], S);
+      k_mg_down_w<<<walk_blocks(f, c.H, p.rows_down[l]), kWalkWarps * 32, kDownRingSmem, st>>>(f, c, p.rows_down[l], S);
     } else if (p.kind[l] == kTile) {
       const Grid& c = p.g[l + 1];
       k_mg_down_t<<<tile_blocks(f, p.rows_down[l]), kTileThreads, kTileSmem, st>>>(f, c, p.rows_down[l], S);
@@ -1323,9 +1399,10 @@ cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cu
       float* o32 = mode == kUp32 ? s32 : nullptr;
       if (p.kind[l] == kWalk) {
         const unsigned nb = walk_blocks(f, f.H, R);
-        if (mode == kUp32) k_mg_up_w<kUp32><<<nb, 256, 0, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
-        else if (mode == kUp64) k_mg_up_w<kUp64><<<nb, 256, 0, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
-        else k_mg_up_w<kUpCoarse><<<nb, 256, 0, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
+        const unsigned nt = kWalkWarps * 32;
+        if (mode == kUp32) k_mg_up_w<kUp32><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
+        else if (mode == kUp64) k_mg_up_w<kUp64><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
+        else k_mg_up_w<kUpCoarse><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
       } else {
         const unsigned nb = tile_blocks(f, R);
         if (mode == kUp32) k_mg_up_t<kUp32><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);

@@ -58,102 +58,124 @@ struct XDir32 {  // d = s + beta d_old (FP32), d = s on the first iteration
   }
 };
 
+// cp.async helpers: each lane copies its own pieces into shared memory (zero-filled
+// where the source size is 0) and waits on its own copies only.
+__device__ __forceinline__ void cpa8(void* sdst, const void* gsrc, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa), "l"(gsrc), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cpa4(void* sdst, const void* gsrc, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gsrc), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // FP32 sliding-window stencil (same tiling as the FP64 walker), summed over the
 // edges as w (x_i - x_j) from the FP32 weights: the FP32 operator keeps A 1 = 0
 // exactly, and for the smooth directions of a well-preconditioned solve its error
-// stays relative to |A x| rather than to |A| |x|.  FP32 rows move half the bytes of
-// FP64 ones, so loads run LA rows ahead of the arithmetic (a ring of raw rows in
-// registers) to keep more bytes in flight with two blocks per SM.
-template <class X, class Epi, int LA = 3>
+// stays relative to |A x| rather than to |A| |x|.  The rows stream through a ring of
+// kRing32 slots per warp in shared memory, filled by cp.async kLead32 rows ahead of
+// the arithmetic (rows outside the grid zero-filled): the loads in flight cost no
+// registers, and a row's wait is the hardware wait on the lane's own copies.
+constexpr int kLead32 = 3;
+// a slot is refilled only after the arithmetic that consumed the row it held: the row
+// two behind the one just read, so the ring holds kLead32 + 2 rows
+constexpr int kRing32 = kLead32 + 2;
+struct Slot32 {
+  float2 S[32], D[32], U[32], V[32];  // s, d_old, U, V at the lane's two columns
+  float hs[2], hd[2], hu, pad_[3];    // halo columns: s, d_old for lanes 0 and 31, U for lane 0
+};
+
+__device__ __forceinline__ void slot32_issue(Slot32& sl, const MapDesc& M, const XDir32& x, const float* U,
+                                             const float* V, int r, int j, int lane, bool hw, bool halo, int hc) {
+  const bool in = r >= 0 && r < M.H;
+  const size_t o = in ? (size_t)r * M.pitch + j : 0;
+  const int nb = in ? 8 : 0;
+  cpa8(&sl.S[lane], x.s + o, nb);
+  cpa8(&sl.D[lane], x.dold + o, x.first ? 0 : nb);
+  cpa8(&sl.U[lane], U + o, nb);
+  cpa8(&sl.V[lane], V + o, nb);
+  if (halo) {
+    const size_t oh = in ? (size_t)r * M.pitch + hc : 0;
+    const int k = lane == 0 ? 0 : 1;
+    cpa4(&sl.hs[k], x.s + oh, in ? 4 : 0);
+    cpa4(&sl.hd[k], x.dold + oh, (in && !x.first) ? 4 : 0);
+    if (hw) cpa4(&sl.hu, U + oh, in ? 4 : 0);
+  }
+}
+
+template <class Epi>
 __device__ __forceinline__ void stencil_tile32(const MapDesc& M, int i0, int i1, int j0, int lane,
-                                               const float* U, const float* V, const X& x, Epi& epi) {
-  using Raw = typename X::Raw;
+                                               const float* U, const float* V, const XDir32& x, Epi& epi) {
+  __shared__ Slot32 ring_all[kWarps][kRing32];
+  Slot32* ring = ring_all[threadIdx.x >> 5];
   const int j = j0 + 2 * lane;
   const bool hw = (lane == 0) && (j0 > 0);
   const bool he = (lane == 31) && (j0 + kStrip < M.pitch);
   const bool halo = hw || he;
   const int hc = (lane == 0) ? j0 - 1 : j0 + kStrip;
-  const size_t P = (size_t)M.pitch;
+  const int hk = lane == 0 ? 0 : 1;
+  // rows rb = i0-1 .. re = i1 stream through the ring, row r in slot (r - rb) % kRing32
+  const int rb = i0 - 1, re = i1;
+#pragma unroll
+  for (int k = 0; k < kLead32; ++k) {
+    if (rb + k <= re) slot32_issue(ring[k], M, x, U, V, rb + k, j, lane, hw, halo, hc);
+    cpa_commit();
+  }
+  auto make = [&](const float2 sv, const float2 dv) {
+    return x.first ? sv : make_float2(__fmaf_rn(x.beta, dv.x, sv.x), __fmaf_rn(x.beta, dv.y, sv.y));
+  };
+  auto make1 = [&](float sv, float dv) { return x.first ? sv : __fmaf_rn(x.beta, dv, sv); };
   const float2 z2 = make_float2(0.f, 0.f);
-  float2 xn = z2, vn = z2;
-  if (i0 > 0) {
-    xn = x.make(x.load(i0 - 1, j));
-    vn = ldf2(V, (size_t)(i0 - 1) * P + j);
-  }
-  float2 xc = x.make(x.load(i0, j));
-  // rings: raw x of rows i+1 .. i+LA (row r is needed while row r-1 is in the tile);
-  // weights and halo of rows i .. i+LA-1
-  Raw rx[LA];
-  float2 uu[LA], vv[LA];
-  float hh[LA], ww[LA];
-#pragma unroll
-  for (int k = 0; k < LA; ++k) {
-    const int ri = i0 + 1 + k, wi = i0 + k;
-    rx[k] = (ri < M.H && ri - 1 < i1) ? x.load(ri, j) : X::zero();
-    uu[k] = vv[k] = z2;
-    hh[k] = ww[k] = 0.f;
-    if (wi < i1) {
-      const size_t o = (size_t)wi * P + j;
-      uu[k] = ldf2(U, o);
-      vv[k] = ldf2(V, o);
-      if (halo) hh[k] = x.at(wi, hc);
-      if (hw) ww[k] = __ldcg(U + o - j + hc);
+  float2 xn = z2, vn = z2, xc = z2, u0 = z2, v0 = z2;
+  float h0 = 0.f, w0 = 0.f;
+  size_t off = (size_t)i0 * M.pitch + j;
+  for (int r = rb; r <= re; ++r) {
+    // every row r + kLead32 and later is still in flight: row r has landed
+    cpa_wait<kLead32 - 1>();
+    const Slot32& sl = ring[(r - rb) % kRing32];
+    const float2 xs = make(sl.S[lane], sl.D[lane]);
+    const float2 u1 = sl.U[lane], v1 = sl.V[lane];
+    const float h1 = halo ? make1(sl.hs[hk], sl.hd[hk]) : 0.f;
+    const float w1 = hw ? sl.hu : 0.f;
+    if (r >= i0 + 1) {
+      // row i = r - 1, with x below it from row r
+      float west = __shfl_up_sync(kFull, xc.y, 1);
+      float east = __shfl_down_sync(kFull, xc.x, 1);
+      float uw = __shfl_up_sync(kFull, u0.y, 1);
+      if (lane == 0) { west = h0; uw = w0; }
+      if (lane == 31) east = h0;
+      // sum over the four edges of w (x_i - x_j): the neighbour differences are nearly
+      // exact for a smooth x, where D x_i - sum w x_j would cancel to a few bits
+      float2 ax;
+      ax.x = __fmul_rn(u0.x, __fsub_rn(xc.x, xc.y));
+      ax.x = __fmaf_rn(uw, __fsub_rn(xc.x, west), ax.x);
+      ax.x = __fmaf_rn(vn.x, __fsub_rn(xc.x, xn.x), ax.x);
+      ax.x = __fmaf_rn(v0.x, __fsub_rn(xc.x, xs.x), ax.x);
+      ax.y = __fmul_rn(u0.y, __fsub_rn(xc.y, east));
+      ax.y = __fmaf_rn(u0.x, __fsub_rn(xc.y, xc.x), ax.y);
+      ax.y = __fmaf_rn(vn.y, __fsub_rn(xc.y, xn.y), ax.y);
+      ax.y = __fmaf_rn(v0.y, __fsub_rn(xc.y, xs.y), ax.y);
+      epi(off, xc, ax);
+      off += M.pitch;
     }
-  }
-  size_t off = (size_t)i0 * P + j;
-  // unrolled by LA so the ring shifts become register renames (measured: mixed Jacobi
-  // PCG 6.0 -> 6.2 Mpx/s at 2048^2 with LA = 3; LA = 4 unrolled spills)
-#pragma unroll LA
-  for (int i = i0; i < i1; ++i) {
-    // issue the loads LA rows ahead
-    const int rn = i + 1 + LA, wn = i + LA;
-    const Raw rnew = (rn < M.H && rn - 1 < i1) ? x.load(rn, j) : X::zero();
-    float2 unew = z2, vnew = z2;
-    float hnew = 0.f, wnew = 0.f;
-    if (wn < i1) {
-      const size_t o = off + (size_t)LA * P;
-      unew = ldf2(U, o);
-      vnew = ldf2(V, o);
-      if (halo) hnew = x.at(wn, hc);
-      if (hw) wnew = __ldcg(U + o - j + hc);
-    }
-    const float2 u0 = uu[0], v0 = vv[0];
-    const float2 xs = (i + 1 < M.H) ? x.make(rx[0]) : z2;
-    float west = __shfl_up_sync(kFull, xc.y, 1);
-    float east = __shfl_down_sync(kFull, xc.x, 1);
-    float uw = __shfl_up_sync(kFull, u0.y, 1);
-    if (lane == 0) { west = hh[0]; uw = ww[0]; }
-    if (lane == 31) east = hh[0];
-    // sum over the four edges of w (x_i - x_j): the neighbour differences are nearly
-    // exact for a smooth x, where D x_i - sum w x_j would cancel to a few bits
-    float2 ax;
-    ax.x = __fmul_rn(u0.x, __fsub_rn(xc.x, xc.y));
-    ax.x = __fmaf_rn(uw, __fsub_rn(xc.x, west), ax.x);
-    ax.x = __fmaf_rn(vn.x, __fsub_rn(xc.x, xn.x), ax.x);
-    ax.x = __fmaf_rn(v0.x, __fsub_rn(xc.x, xs.x), ax.x);
-    ax.y = __fmul_rn(u0.y, __fsub_rn(xc.y, east));
-    ax.y = __fmaf_rn(u0.x, __fsub_rn(xc.y, xc.x), ax.y);
-    ax.y = __fmaf_rn(vn.y, __fsub_rn(xc.y, xn.y), ax.y);
-    ax.y = __fmaf_rn(v0.y, __fsub_rn(xc.y, xs.y), ax.y);
-    epi(off, xc, ax);
+    // shift: rows r-1 and r become the rows above and at the next output row
     xn = xc;
-    xc = xs;
     vn = v0;
-#pragma unroll
-    for (int k = 0; k + 1 < LA; ++k) {
-      rx[k] = rx[k + 1];
-      uu[k] = uu[k + 1];
-      vv[k] = vv[k + 1];
-      hh[k] = hh[k + 1];
-      ww[k] = ww[k + 1];
-    }
-    rx[LA - 1] = rnew;
-    uu[LA - 1] = unew;
-    vv[LA - 1] = vnew;
-    hh[LA - 1] = hnew;
-    ww[LA - 1] = wnew;
-    off += P;
+    xc = xs;
+    u0 = u1;
+    v0 = v1;
+    h0 = h1;
+    w0 = w1;
+    // refill the slot of row r - 2, whose values the arithmetic above has consumed
+    // (rows rb-2 and rb-1 are the ring's two unused slots)
+    if (r + kLead32 <= re) slot32_issue(ring[(r + kLead32 - rb) % kRing32], M, x, U, V, r + kLead32, j, lane, hw, halo, hc);
+    cpa_commit();
   }
+  cpa_wait_all();  // the next tile of this warp refills the same slots
 }
 
 // d = s + beta d_old, q = A d in FP32, d^T q FP64-accurate.

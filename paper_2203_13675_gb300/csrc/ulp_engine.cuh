@@ -225,6 +225,7 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
         } else {
           done = true;
           S->status = 0;
+          if (ph == kPhFcg && a.xfcg && refreshed) S->x_clean = 1;  // this iteration folded x into phi
         }
       } else if (S->iter >= (a.lmax > 0 ? a.lmax : 2LL * M.H * M.W)) {
         done = true;
@@ -314,11 +315,12 @@ __device__ __forceinline__ void tile_arrive(const PcgArgs& a, const MapDesc& M, 
 // Arrival of the flexible-CG dot phase from a kernel that covers the map with its
 // own decomposition into n warps (32 <= n <= the map's tile count), warp w: its
 // r^T s and r^T r go to P0, P1 at tile_base + w and count as above with n in
-// place of the tile count; the r_{k+1}^T s_k partials that phase B left in P2
-// are indexed by the map's tiles, so the last warp of group g sums P2 over the
-// map's tiles of group g.  Same fixed summation order on every run.
+// place of the tile count; the third sum's partials (r_{k+1}^T s_k left by phase B,
+// or b^T b at the start of a solve, ph = kPhResInit) are indexed by the map's
+// tiles, so the last warp of group g sums P2 over the map's tiles of group g.
+// Same fixed summation order on every run.
 __device__ __forceinline__ void warp_arrive_fcg(const PcgArgs& a, const MapDesc& M, MapState* S, int w, int n,
-                                                double rs, double rr, int lane) {
+                                                double rs, double rr, int lane, int ph = kPhFcg) {
   rs = warp_sum(rs);
   rr = warp_sum(rr);
   const int base = M.tile_base;
@@ -357,7 +359,7 @@ __device__ __forceinline__ void warp_arrive_fcg(const PcgArgs& a, const MapDesc&
   last = __shfl_sync(kFull, last, 0);
   if (last) {
     __syncwarp();
-    finish_map(a, M, S, kPhFcg, lane, kArriveGroups);
+    finish_map(a, M, S, ph, lane, kArriveGroups);
   }
 }
 

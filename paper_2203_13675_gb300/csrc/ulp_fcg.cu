@@ -306,8 +306,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_b(const PcgArgs* pa) {
   }
 }
 
-// r = b - A phi in FP64, rounded to FP32 (x = 0 with it at the start); on refresh
-// iterations also r_{k+1}^T s_k.
+// r = b - A phi in FP64, rounded to FP32 (x = 0 with it at the start, and the b^T b
+// partials for the start's dot phase); on refresh iterations also r_{k+1}^T s_k.
 __global__ void __launch_bounds__(kThreads, 2) k_x_res(const PcgArgs* pa, int init) {
   const PcgArgs a = *pa;
   FCG_TILE_LOOP(a) {
@@ -316,12 +316,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_res(const PcgArgs* pa, int in
     const TileGeo g = tile_geo(M, t, a.R);
     XPlane x{M.f.phi, (size_t)M.pitch};
     DF rsp;
+    double bb = 0.0;
     auto epi = [&](size_t off, double2, double2 ax) {
       const double2 bv = ld2(M.f.b, off);
       const float2 r = make_float2((float)(bv.x - ax.x), (float)(bv.y - ax.y));
       stf2(M.h.r, off, r);
       if (init) {
         stf2(M.h.x, off, make_float2(0.f, 0.f));
+        bb = fma(bv.x, bv.x, bb);
+        bb = fma(bv.y, bv.y, bb);
       } else {
         const float2 sv = ldf2(M.h.s, off);
         rsp.add_prod(r.x, sv.x);
@@ -329,10 +332,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_res(const PcgArgs* pa, int in
       }
     };
     stencil_tile(M, g.i0, g.i1, g.j0, lane, M.f.U, M.f.V, M.f.D, x, epi);
-    if (!init) {
-      const double v = warp_sum(rsp.value());
-      if (lane == 0) __stcg(a.P2 + t, v);
-    }
+    const double v = warp_sum(init ? bb : rsp.value());
+    if (lane == 0) __stcg(a.P2 + t, v);
   }
 }
 
@@ -364,14 +365,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_dots(const PcgArgs* pa, int i
   }
 }
 
-// end of the solve: phi += x (zero after a confirmed stop; not after l_max or a breakdown)
+// end of the solve: phi += x; nothing to do after a stop on a refresh iteration (x = 0 then),
+// only after l_max or a breakdown
 __global__ void __launch_bounds__(kThreads) k_x_fold(const PcgArgs* pa) {
   const PcgArgs a = *pa;
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int NW = gridDim.x * (blockDim.x >> 5);
   const MapDesc& M = a.maps[0];
-  if (!a.st->outer_active) return;
+  if (!a.st->outer_active || *(volatile int*)&a.st->x_clean) return;
   for (int t = gw; t < a.ntiles; t += NW) {
     const TileGeo g = tile_geo(M, t, a.R);
     const size_t P = M.pitch;
@@ -417,13 +419,14 @@ static bool mixed_fcg(const Plan& pl, int kind) {
   return kind == ULP_PRECOND_MG && pl.opt.precision == ULP_PRECISION_MIXED;
 }
 
-// With fuse_dots the multigrid cycle's last kernel also runs the dot phase D.
-static cudaError_t fcg_precond(Plan& pl, int kind, cudaStream_t st, bool fuse_dots = false) {
+// With fuse_dots the multigrid cycle's last kernel also runs the dot phase D (at the
+// start of a solve, init: its start form, with b^T b).
+static cudaError_t fcg_precond(Plan& pl, int kind, cudaStream_t st, bool fuse_dots = false, bool init = false) {
   const MapDesc& M = pl.hmaps[0];
   if (kind == ULP_PRECOND_DCT) return dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st, true);
   if (kind == ULP_PRECOND_MG)
     return mg_apply(*pl.mg, M.f.mask, pl.dstate, st, true, fuse_dots ? pl.dargs : nullptr,
-                    mixed_fcg(pl, kind) ? M.h.s : nullptr);
+                    mixed_fcg(pl, kind) ? M.h.s : nullptr, init);
   if (kind == ULP_PRECOND_RBSSOR || kind == ULP_PRECOND_RBILU) return rb_apply(pl, kind, pl.dstate, st);
   const cudaError_t e = unet_apply_plane(*pl.unet, M.f.r, M.f.U, M.f.V, M.f.mask, M.H, M.W, M.pitch, M.f.s,
                                          &pl.dstate[0].fallback, st);
@@ -432,16 +435,20 @@ static cudaError_t fcg_precond(Plan& pl, int kind, cudaStream_t st, bool fuse_do
   return cudaGetLastError();
 }
 
+// D rides on the multigrid cycle's last kernel where the plan allows it
+static bool fused_dots(const Plan& pl, int kind) { return kind == ULP_PRECOND_MG && mg_fuses_dots(*pl.mg); }
+
 // Start of a solve: r = b - A phi (and its BF16 copy), the mask bits, s = M^-1 r, delta_0.
 static cudaError_t fcg_start(Plan& pl, int kind, cudaStream_t st) {
   const MapDesc& M = pl.hmaps[0];
   const int nb = tile_blocks(pl);
   if (mixed_fcg(pl, kind)) {
+    const bool fd = fused_dots(pl, kind);
     k_x_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = mg_setup(*pl.mg, pl.dstate, st, !pl.system_x);
-    if (e == cudaSuccess) e = fcg_precond(pl, kind, st);
-    k_x_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+    if (e == cudaSuccess) e = fcg_precond(pl, kind, st, fd, true);
+    if (!fd) k_x_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
     return e == cudaSuccess ? cudaGetLastError() : e;
   }
   k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
@@ -453,9 +460,6 @@ static cudaError_t fcg_start(Plan& pl, int kind, cudaStream_t st) {
   k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
-
-// D rides on the multigrid cycle's last kernel where the plan allows it
-static bool fused_dots(const Plan& pl, int kind) { return kind == ULP_PRECOND_MG && mg_fuses_dots(*pl.mg); }
 
 // One iteration: A, B, R, s = M^-1 r, D.
 static cudaError_t fcg_iteration(Plan& pl, int kind, cudaStream_t st) {
@@ -565,10 +569,12 @@ static cudaError_t fcg_eager_mixed(Plan& pl, int kind, cudaStream_t st) {
   k_x_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
   phase_mark(pl, st, 2);
   if ((e = mg_setup(*pl.mg, pl.dstate, st, !pl.system_x)) != cudaSuccess) return e;
-  if ((e = fcg_precond(pl, kind, st)) != cudaSuccess) return e;
+  if ((e = fcg_precond(pl, kind, st, fd, true)) != cudaSuccess) return e;
   phase_mark(pl, st, 3);
-  k_x_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
-  phase_mark(pl, st, 4);
+  if (!fd) {
+    k_x_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+    phase_mark(pl, st, 4);
+  }
   for (long long l = 0;; ++l) {
     int done = 0;
     if ((e = cudaMemcpyAsync(&done, &pl.dstate->done, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;

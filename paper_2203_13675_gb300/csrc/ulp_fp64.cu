@@ -619,6 +619,7 @@ __global__ void k_pcg_reset(MapState* S, int nmaps, int* n_active, Barrier* bar)
     s->restart = 0;
     s->stall = 0;
     s->force_refresh = 0;
+    s->x_clean = 0;
     s->rr_best = 0.0;
     if (act) atomicAdd(&s_cnt, 1);
   }
@@ -641,12 +642,16 @@ __global__ void k_outer_error(const MapDesc* __restrict__ maps, MapState* S, Map
   const MapDesc& M = maps[m];
   MapState* s = S + m;
   if (!s->outer_active) return;
-  const size_t n = (size_t)M.H * M.pitch;
+  // two elements per thread (the planes' pitch is even; padding columns are 0 in both)
+  const size_t n2 = (size_t)M.H * M.pitch / 2;
   double num = 0.0, den = 0.0;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const double e = M.f.phi[t] - M.f.phi_prev[t];
-    num = fma(e, e, num);
-    den = fma(M.f.phi_prev[t], M.f.phi_prev[t], den);
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n2; t += (size_t)gridDim.x * blockDim.x) {
+    const double2 ph = ld2(M.f.phi, 2 * t), pp = ld2(M.f.phi_prev, 2 * t);
+    const double ex = ph.x - pp.x, ey = ph.y - pp.y;
+    num = fma(ex, ex, num);
+    num = fma(ey, ey, num);
+    den = fma(pp.x, pp.x, den);
+    den = fma(pp.y, pp.y, den);
   }
   __shared__ double sn[kWarps], sd[kWarps];
   num = warp_sum(num);

@@ -117,8 +117,10 @@ cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st, bool l
 // arguments of a flexible-CG solve, or null): the cycle's last kernel also does the solve's
 // dot phase (r^T s, r^T r, beta, stop test), if mg_fuses_dots
 // s32 (or null): s is written in FP32 there instead of the map's FP64 s plane (the mixed flexible CG)
+// dots_init: the dot phase is the start of a solve (r^T s, r^T r, and b^T b from the
+// per-tile partials that k_x_res left in P2)
 cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st, bool packed = false,
-                     const PcgArgs* dots = nullptr, float* s32 = nullptr);
+                     const PcgArgs* dots = nullptr, float* s32 = nullptr, bool dots_init = false);
 bool mg_fuses_dots(const MgPlan& p);
 float* mg_input(const MgPlan& p);
 int mg_levels(const MgPlan& p);

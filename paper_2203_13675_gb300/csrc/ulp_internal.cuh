@@ -78,6 +78,8 @@ struct MapState {
   int stall;                // iterations since rr last fell below 0.99 rr_best
   int force_refresh;        // mixed flexible CG: every further iteration recomputes the true residual
   double rr_best;
+  int x_clean;              // mixed flexible CG: stopped right after a refresh, so the correction is 0
+  int pad2_;
 };
 
 // Device-side record of one call (per map), copied to the host at the end.

@@ -96,6 +96,43 @@ __global__ void k_mg_coarsen(Grid f, Grid c, const MapState* S) {
   }
 }
 
+// The coarse grids from index l0 on, made one after the other by one block (the
+// small grids of the hierarchy: one launch instead of one per grid).
+struct CoarsenList {
+  int n;          // grids g[0..n-1]: g[k+1] is made from g[k]
+  Grid g[16];
+};
+
+__global__ void __launch_bounds__(1024) k_mg_coarsen_small(CoarsenList cl, const MapState* S) {
+  if (skip_map(S)) return;
+  for (int k = 0; k + 1 < cl.n; ++k) {
+    const Grid& f = cl.g[k];
+    const Grid& c = cl.g[k + 1];
+    for (int t = threadIdx.x; t < c.H * c.W; t += blockDim.x) {
+      const int I = t / c.W, J = t - (t / c.W) * c.W;
+      auto uc = [&](int Jp) {
+        float u = 0.f;
+        if (Jp >= 0 && 2 * Jp + 2 < f.W)
+          for (int i = 2 * I; i <= 2 * I + 1 && i < f.H; ++i) u += f.U[(size_t)i * f.ld + 2 * Jp + 1];
+        return u;
+      };
+      auto vc = [&](int Ip) {
+        float v = 0.f;
+        if (Ip >= 0 && 2 * Ip + 2 < f.H)
+          for (int j = 2 * J; j <= 2 * J + 1 && j < f.W; ++j) v += f.V[(size_t)(2 * Ip + 1) * f.ld + j];
+        return v;
+      };
+      const float u = uc(J), v = vc(I);
+      const float d = u + v + uc(J - 1) + vc(I - 1);
+      const size_t o = (size_t)I * c.ld + J;
+      const_cast<float*>(c.U)[o] = u;
+      const_cast<float*>(c.V)[o] = v;
+      const_cast<float*>(c.Dinv)[o] = d > 0.f ? 1.f / d : 0.f;
+    }
+    __syncthreads();
+  }
+}
+
 // x = two damped-Jacobi sweeps from zero
 __global__ void k_mg_pre(Grid g, const MapState* S) {
   if (skip_map(S)) return;
@@ -499,7 +536,7 @@ enum { kUpCoarse = 0, kUp64 = 1, kUp32 = 2 };
 template <int MODE>
 __global__ void __launch_bounds__(kTileThreads) k_mg_up_t(Grid f, Grid c, const float* __restrict__ xc, int TR,
                                                         const uint8_t* mask, double* s, const double* __restrict__ rv,
-                                                        float* s32, const PcgArgs* pa, const MapState* S) {
+                                                        float* s32, const PcgArgs* pa, const MapState* S, int ph) {
   constexpr bool MAP = MODE != kUpCoarse;
   constexpr int kOut = kTileMaxRows / kTileWarps;  // output rows per warp at most
   if (skip_map(S)) return;
@@ -636,7 +673,7 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_up_t(Grid f, Grid c, const 
     if (warp == 0) {
       const PcgArgs a = *pa;
       const double v0 = lane < kTileWarps ? red[0][lane] : 0.0, v1 = lane < kTileWarps ? red[1][lane] : 0.0;
-      warp_arrive_fcg(a, a.maps[0], a.st, (int)blockIdx.x, (int)gridDim.x, v0, v1, lane);
+      warp_arrive_fcg(a, a.maps[0], a.st, (int)blockIdx.x, (int)gridDim.x, v0, v1, lane, ph);
     }
   }
 }
@@ -804,7 +841,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kWalkWarps * 32) k_mg_up_w(Grid f, Grid c, const float* __restrict__ xc, int R,
                                                              const uint8_t* mask, double* s,
                                                              const double* __restrict__ rv, float* s32,
-                                                             const PcgArgs* pa, const MapState* S) {
+                                                             const PcgArgs* pa, const MapState* S, int ph) {
   constexpr bool MAP = MODE != kUpCoarse;
   if (skip_map(S)) return;
   extern __shared__ float4 wsm4[];
@@ -905,7 +942,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_mg_up_w(Grid f, Grid c, con
       rs = rs32.value();
       rr = rr32.value();
     }
-    warp_arrive_fcg(a, a.maps[0], a.st, band * nseg + seg, nseg * bands, rs, rr, lane);
+    warp_arrive_fcg(a, a.maps[0], a.st, band * nseg + seg, nseg * bands, rs, rr, lane, ph);
   }
 }
 
@@ -1333,9 +1370,20 @@ static int mg_blocks(const MgPlan& p, long long n) {
 cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st, bool level0) {
   const Grid& g0 = p.g[0];
   if (level0) k_mg_level0<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(p.U0, p.V0, p.Dinv0, g0, S);
-  for (size_t l = 0; l + 1 < p.g.size(); ++l) {
+  // one launch per coarse grid while it has more than kCoarsenSmall unknowns, then one
+  // block for all the smaller ones (same arithmetic per aggregate)
+  constexpr long long kCoarsenSmall = 16384;
+  size_t l = 0;
+  for (; l + 1 < p.g.size(); ++l) {
     const Grid& c = p.g[l + 1];
+    if ((long long)c.H * c.W <= kCoarsenSmall && p.g.size() - l <= 16) break;
     k_mg_coarsen<<<mg_blocks(p, (long long)c.H * c.W), 256, 0, st>>>(p.g[l], c, S);
+  }
+  if (l + 1 < p.g.size()) {
+    CoarsenList cl{};
+    cl.n = (int)(p.g.size() - l);
+    for (int k = 0; k < cl.n; ++k) cl.g[k] = p.g[l + k];
+    k_mg_coarsen_small<<<1, 1024, 0, st>>>(cl, S);
   }
   return cudaGetLastError();
 }
@@ -1344,7 +1392,8 @@ cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st, bool l
 float* mg_input(const MgPlan& p) { return p.g[0].b; }
 
 cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st, bool packed,
-                     const PcgArgs* dots, float* s32) {
+                     const PcgArgs* dots, float* s32, bool dots_init) {
+  const int ph = dots_init ? kPhResInit : kPhFcg;
   const int L = (int)p.g.size();
   const Grid& g0 = p.g[0];
   if (!packed) k_mg_rhs_v<<<mg_blocks(p, (long long)g0.H * ((g0.W + 3) / 4)), 256, 0, st>>>(p.r0, g0, S);
@@ -1400,14 +1449,14 @@ cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cu
       if (p.kind[l] == kWalk) {
         const unsigned nb = walk_blocks(f, f.H, R);
         const unsigned nt = kWalkWarps * 32;
-        if (mode == kUp32) k_mg_up_w<kUp32><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
-        else if (mode == kUp64) k_mg_up_w<kUp64><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
-        else k_mg_up_w<kUpCoarse><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
+        if (mode == kUp32) k_mg_up_w<kUp32><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
+        else if (mode == kUp64) k_mg_up_w<kUp64><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
+        else k_mg_up_w<kUpCoarse><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
       } else {
         const unsigned nb = tile_blocks(f, R);
-        if (mode == kUp32) k_mg_up_t<kUp32><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
-        else if (mode == kUp64) k_mg_up_t<kUp64><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
-        else k_mg_up_t<kUpCoarse><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S);
+        if (mode == kUp32) k_mg_up_t<kUp32><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
+        else if (mode == kUp64) k_mg_up_t<kUp64><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
+        else k_mg_up_t<kUpCoarse><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
       }
     } else if (f.W >= kVecMinW) {
       k_mg_sweep_v<kSrcXP><<<row_blocks(f, f.H), 256, 0, st>>>(f, p.g[l + 1], f.t, nullptr, nullptr, S);

@@ -60,7 +60,8 @@ KERNEL = {("f64", "jacobi"): "k_pcg64", ("f64", "identity"): "k_pcg64", ("mixed"
 # dot phase reading the FP64 r (+16), or in FP32 in the mixed form (+4).  Each coarser grid moves 21
 # down and 25 up per pixel of its own, a third of the map's pixels in all.
 MG_COARSE_PER_PX = (21.0 + 25.0) / 3.0
-MG_BYTES_PER_PX = {"f64": 21.0 + 38.0 + MG_COARSE_PER_PX, "mixed": 21.0 + 26.0 + MG_COARSE_PER_PX}
+MG_UP0_PER_PX = {"f64": 38.0, "mixed": 26.0}   # the cycle's last kernel (phase U of the replay)
+MG_BYTES_PER_PX = {k: 21.0 + v + MG_COARSE_PER_PX for k, v in MG_UP0_PER_PX.items()}
 # forms compared on each workload: the first is the plain form (the paper's method as written);
 # CHOSEN is the form the workload's configuration is about and that `value` reports
 FORMS = {"c5_2048": [("f64", "jacobi"), ("f64", "dct"), ("f64", "mg"), ("f64", "learned")],
@@ -83,6 +84,10 @@ FCG_KERNEL = {"A": "k_f_a", "B": "k_f_b", "R": "k_f_res", "D": "k_f_dots", "M": 
 # writes x, r (28); the dot phase rides on the multigrid cycle's last kernel
 FCG_BYTES_MIXED = {"A": 24, "B": 28, "D": 16}
 FCG_KERNEL_MIXED = {"A": "k_x_a", "B": "k_x_b", "R": "k_x_res", "D": "k_x_dots"}
+UP0_KERNEL = {"mixed": "k_mg_up_w<kUp32> (the map grid's multigrid up step: both post-sweeps, s in FP32, "
+                       "and the flexible CG's dot phase)",
+              "f64": "k_mg_up_w<kUp64> (the map grid's multigrid up step: both post-sweeps, s in FP64, "
+                     "and the flexible CG's dot phase)"}
 
 
 def env_rank():
@@ -472,9 +477,12 @@ def learned_net(native, args):
 def fcg_roofline(native, H, W, psi, mask, w, precond, timed_plan, prec="f64"):
     """Roofline of the dominant kernel of a flexible-CG solve.  Kernels inside the
     solve's graph cannot carry their own events, so the same solve is replayed
-    host-driven (options.profile = 2) with an event after every phase; the
-    dominant phase (largest summed time) is reported with its algorithmic bytes
-    (or, for the DCT chain, tensor flops) per launch over its mean duration."""
+    host-driven (options.profile = 2) with an event after every phase.  For the
+    multigrid forms the replay times the cycle's last kernel (the up step on the
+    map's grid, which carries the dot phase) on its own as phase U: the largest
+    single kernel of the solve, reported with its algorithmic bytes per launch
+    over its mean duration.  Otherwise the phase with the largest summed time is
+    reported (for the DCT chain with its tensor flops)."""
     peaks = load_peaks_all()
     eager = native.Plan(H, W, outer_tol=0.0, profile=2,
                         precision=native.ULP_PRECISION_MIXED if prec == "mixed" else 0)
@@ -503,7 +511,9 @@ def fcg_roofline(native, H, W, psi, mask, w, precond, timed_plan, prec="f64"):
         if ph == "M" and precond == "learned":
             kname = "k_conv3x3 x7 + U-Net glue"
         elif ph == "M" and precond == "mg":
-            kname = "k_mg_down/k_mg_up per grid + k_mg_tail (dot phase in the last k_mg_up)"
+            kname = "V-cycle without its last kernel: k_mg_down_w/_t per grid, k_mg_tail, k_mg_up_t/_w on the coarser grids"
+        elif ph == "U":
+            kname = UP0_KERNEL[prec]
         ent = {"ms_total": ms, "launches": n, "us_per_launch": mean_s * 1e6, "kernel": kname}
         if ph in fbytes:
             ent.update(bound="hbm", achieved=fbytes[ph] * H * W / mean_s / 1e9, unit="GB/s",
@@ -515,10 +525,15 @@ def fcg_roofline(native, H, W, psi, mask, w, precond, timed_plan, prec="f64"):
                        peak=peaks["bf16_sust"][0], peak_source=peaks["bf16_sust"][1],
                        alg_per_launch=f"4 Hp Wp (Hp + Wp) = {fl:.3g} flop")
         elif ph == "M" and precond == "mg":
-            mb = MG_BYTES_PER_PX[prec]
+            mb = MG_BYTES_PER_PX[prec] - MG_UP0_PER_PX[prec]
             ent.update(bound="hbm", achieved=mb * H * W / mean_s / 1e9, unit="GB/s",
                        peak=peaks["hbm"][0], peak_source=peaks["hbm"][1] + " hbm_gbs",
-                       alg_per_launch=f"{mb:.0f} B/px x {H}x{W} (V-cycle, all grids)")
+                       alg_per_launch=f"{mb:.0f} B/px x {H}x{W} (V-cycle on all grids but the map grid's up step)")
+        elif ph == "U":
+            mb = MG_UP0_PER_PX[prec]
+            ent.update(bound="hbm", achieved=mb * H * W / mean_s / 1e9, unit="GB/s",
+                       peak=peaks["hbm"][0], peak_source=peaks["hbm"][1] + " hbm_gbs",
+                       alg_per_launch=f"{mb:.0f} B/px x {H}x{W}")
         elif ph == "M" and precond == "learned":
             fl = UNET_FLOP_PER_PX * Hp * Wp
             ent.update(bound="tensor", achieved=fl / mean_s / 1e12, unit="TFLOP/s",
@@ -527,12 +542,17 @@ def fcg_roofline(native, H, W, psi, mask, w, precond, timed_plan, prec="f64"):
         if "achieved" in ent:
             ent["frac"] = ent["achieved"] / ent["peak"] if ent["peak"] else None
         phases[ph] = ent
-    dom = max((k for k in phases if "achieved" in phases[k]), key=lambda k: phases[k]["ms_total"])
+    # the dominant kernel: for the multigrid forms the cycle's last kernel (the largest single
+    # kernel of the solve in the ncu launch list), else the phase with the largest total time
+    if precond == "mg" and "U" in phases:
+        dom = "U"
+    else:
+        dom = max((k for k in phases if "achieved" in phases[k]), key=lambda k: phases[k]["ms_total"])
     d = phases[dom]
     tpx = profile_traffic(f"fcg_{prec}_{precond}_{dom}_c2_2048")
     return {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
             "frac": d["frac"], "traffic": (tpx * H * W if tpx is not None else None),
-            "kernel": f"{d['kernel']} (flexible-CG phase {dom}, dominant)", "peak_source": d["peak_source"],
+            "kernel": f"{d['kernel']} (replay phase {dom}, dominant)", "peak_source": d["peak_source"],
             "alg_per_launch": d["alg_per_launch"], "measured": "host-driven replay of the same solve, "
             "CUDA events after every phase on the solve's stream", "phases": phases}
 

@@ -213,11 +213,13 @@ typedef struct ulp_counters {
   long long solver_launches;  /* persistent PCG launches among them */
   double solver_ms;           /* summed duration of the timed solver launches (profile only) */
   long long timed_launches;   /* solver launches included in solver_ms */
-  /* options.profile = 2, flexible-CG solves (DCT, learned), run host-driven: summed durations and
-   * counts of each phase, [0] A (d = s + beta d, q = A d, d^T q), [1] B (phi, r update), [2] R (true
-   * residual), [3] M (s = M^-1 r: the GEMM chain or the network), [4] D (r^T s, r^T r, stop test) */
-  double phase_ms[5];
-  long long phase_launches[5];
+  /* options.profile = 2, flexible-CG solves, run host-driven: summed durations and counts of each
+   * phase, [0] A (d = s + beta d, q = A d, d^T q), [1] B (phi, r update), [2] R (true residual),
+   * [3] M (s = M^-1 r: the GEMM chain, the network, the red-black passes or the V-cycle), [4] D
+   * (r^T s, r^T r, stop test), [5] U (multigrid only: the V-cycle's last kernel, the up step on
+   * the map's grid, which also runs D where it can; timed on its own and not included in M) */
+  double phase_ms[6];
+  long long phase_launches[6];
   /* flexible-CG solves run as a graph whose WHILE body executes once per inner iteration:
    * the kernels of its start and of one body (the body's kernels are not in kernel_launches;
    * an outer pass with l inner iterations runs start + l x body of them) */

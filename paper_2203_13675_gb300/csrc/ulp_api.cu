@@ -514,7 +514,7 @@ extern "C" int ulp_plan_counters(ulp_plan plan, int reset, ulp_counters* out) {
     ULP_CU(cudaEventElapsedTime(&ms, pl.ev_pool[k], pl.ev_pool[k + 1]));
     out->solver_ms += ms;
   }
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 6; ++k) {
     out->phase_ms[k] = 0.0;
     out->phase_launches[k] = 0;
   }
@@ -522,7 +522,7 @@ extern "C" int ulp_plan_counters(ulp_plan plan, int reset, ulp_counters* out) {
   out->graph_body_kernels = pl.fcg_body_kernels;
   for (size_t k = 1; k < pl.ph_used; ++k) {
     const int t = pl.ph_tag[k];
-    if (t < 0 || t > 4) continue;
+    if (t < 0 || t > 5) continue;
     ULP_CU(cudaEventSynchronize(pl.ph_pool[k]));
     float ms = 0.f;
     ULP_CU(cudaEventElapsedTime(&ms, pl.ph_pool[k - 1], pl.ph_pool[k]));

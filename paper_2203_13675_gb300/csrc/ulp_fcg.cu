@@ -421,12 +421,14 @@ static bool mixed_fcg(const Plan& pl, int kind) {
 
 // With fuse_dots the multigrid cycle's last kernel also runs the dot phase D (at the
 // start of a solve, init: its start form, with b^T b).
-static cudaError_t fcg_precond(Plan& pl, int kind, cudaStream_t st, bool fuse_dots = false, bool init = false) {
+// part (multigrid): as mg_apply's, so a replay can time the cycle's last kernel alone.
+static cudaError_t fcg_precond(Plan& pl, int kind, cudaStream_t st, bool fuse_dots = false, bool init = false,
+                               int part = 0) {
   const MapDesc& M = pl.hmaps[0];
   if (kind == ULP_PRECOND_DCT) return dct_apply(*pl.dct, M.f.r, M.pitch, M.f.mask, M.f.s, st, true);
   if (kind == ULP_PRECOND_MG)
     return mg_apply(*pl.mg, M.f.mask, pl.dstate, st, true, fuse_dots ? pl.dargs : nullptr,
-                    mixed_fcg(pl, kind) ? M.h.s : nullptr, init);
+                    mixed_fcg(pl, kind) ? M.h.s : nullptr, init, part);
   if (kind == ULP_PRECOND_RBSSOR || kind == ULP_PRECOND_RBILU) return rb_apply(pl, kind, pl.dstate, st);
   const cudaError_t e = unet_apply_plane(*pl.unet, M.f.r, M.f.U, M.f.V, M.f.mask, M.H, M.W, M.pitch, M.f.s,
                                          &pl.dstate[0].fallback, st);
@@ -587,8 +589,10 @@ static cudaError_t fcg_eager_mixed(Plan& pl, int kind, cudaStream_t st) {
     phase_mark(pl, st, 1);
     k_x_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
     phase_mark(pl, st, 2);
-    if ((e = fcg_precond(pl, kind, st, fd)) != cudaSuccess) return e;
+    if ((e = fcg_precond(pl, kind, st, fd, false, 1)) != cudaSuccess) return e;
     phase_mark(pl, st, 3);
+    if ((e = fcg_precond(pl, kind, st, fd, false, 2)) != cudaSuccess) return e;
+    phase_mark(pl, st, 5);
     if (!fd) {
       k_x_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
       phase_mark(pl, st, 4);
@@ -627,8 +631,15 @@ static cudaError_t fcg_eager(Plan& pl, int kind, cudaStream_t st) {
     k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
     phase_mark(pl, st, 2);
     const bool fd = fused_dots(pl, kind);
-    if ((e = fcg_precond(pl, kind, st, fd)) != cudaSuccess) return e;
-    phase_mark(pl, st, 3);
+    if (kind == ULP_PRECOND_MG) {
+      if ((e = fcg_precond(pl, kind, st, fd, false, 1)) != cudaSuccess) return e;
+      phase_mark(pl, st, 3);
+      if ((e = fcg_precond(pl, kind, st, fd, false, 2)) != cudaSuccess) return e;
+      phase_mark(pl, st, 5);
+    } else {
+      if ((e = fcg_precond(pl, kind, st, fd)) != cudaSuccess) return e;
+      phase_mark(pl, st, 3);
+    }
     if (!fd) {
       k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
       phase_mark(pl, st, 4);

@@ -119,8 +119,10 @@ cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st, bool l
 // s32 (or null): s is written in FP32 there instead of the map's FP64 s plane (the mixed flexible CG)
 // dots_init: the dot phase is the start of a solve (r^T s, r^T r, and b^T b from the
 // per-tile partials that k_x_res left in P2)
+// part: 0 the whole cycle; 1 all but its last kernel (the up step on the map's grid); 2 that
+// last kernel alone (the host-driven replay times it on its own)
 cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st, bool packed = false,
-                     const PcgArgs* dots = nullptr, float* s32 = nullptr, bool dots_init = false);
+                     const PcgArgs* dots = nullptr, float* s32 = nullptr, bool dots_init = false, int part = 0);
 bool mg_fuses_dots(const MgPlan& p);
 float* mg_input(const MgPlan& p);
 int mg_levels(const MgPlan& p);

@@ -1391,19 +1391,75 @@ cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st, bool l
 // s = V-cycle(r) on the map's planes; mask zeroes s.
 float* mg_input(const MgPlan& p) { return p.g[0].b; }
 
+// The up step of grid l; on the map's grid (l = 0) it writes s (FP64, or FP32 into
+// s32) and, with dots, carries the flexible CG's dot phase ph.
+static void up_level(const MgPlan& p, int l, int stop, const uint8_t* mask, const MapState* S, cudaStream_t st,
+                     const PcgArgs* dots, float* s32, int ph) {
+  const Grid& f = p.g[l];
+  if (p.kind[l] != kPerStep) {
+    // the coarse grid's corrected solution: the t plane if a fused kernel made it, else x
+    const Grid& c = p.g[l + 1];
+    const float* xc = (l + 1 < stop && p.kind[l + 1] != kPerStep) ? c.t : c.x;
+    const int R = p.rows_up[l];
+    const bool d = l == 0 && dots && p.dots_units > 0;
+    const PcgArgs* pa = d ? dots : nullptr;
+    const int mode = l > 0 ? kUpCoarse : (s32 ? kUp32 : kUp64);
+    const double* rv = (mode == kUp64 && d) ? p.r0 : nullptr;
+    double* s64 = mode == kUp64 ? p.s0 : nullptr;
+    const uint8_t* mk = l == 0 ? mask : nullptr;
+    float* o32 = mode == kUp32 ? s32 : nullptr;
+    if (p.kind[l] == kWalk) {
+      const unsigned nb = walk_blocks(f, f.H, R);
+      const unsigned nt = kWalkWarps * 32;
+      if (mode == kUp32) k_mg_up_w<kUp32><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
+      else if (mode == kUp64) k_mg_up_w<kUp64><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
+      else k_mg_up_w<kUpCoarse><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
+    } else {
+      const unsigned nb = tile_blocks(f, R);
+      if (mode == kUp32) k_mg_up_t<kUp32><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
+      else if (mode == kUp64) k_mg_up_t<kUp64><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
+      else k_mg_up_t<kUpCoarse><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
+    }
+    return;
+  }
+  if (f.W >= kVecMinW) {
+    k_mg_sweep_v<kSrcXP><<<row_blocks(f, f.H), 256, 0, st>>>(f, p.g[l + 1], f.t, nullptr, nullptr, S);
+    k_mg_sweep_v<kSrcT><<<row_blocks(f, f.H), 256, 0, st>>>(f, Grid{}, f.x, l == 0 ? mask : nullptr,
+                                                             l == 0 ? p.s0 : nullptr, S);
+  } else {
+    k_mg_post1<<<mg_blocks(p, (long long)f.H * f.W), 256, 0, st>>>(f, p.g[l + 1], S);
+    k_mg_post2<<<mg_blocks(p, (long long)f.H * f.W), 256, 0, st>>>(f, l == 0 ? mask : nullptr,
+                                                                  l == 0 ? p.s0 : nullptr, S);
+  }
+  // the map's grid without fused kernels: the FP64 s rounded into s32
+  if (l == 0 && s32) k_mg_to32<<<mg_blocks(p, (long long)f.H * f.W), 256, 0, st>>>(p.s0, s32, f, S);
+}
+
 cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cudaStream_t st, bool packed,
-                     const PcgArgs* dots, float* s32, bool dots_init) {
+                     const PcgArgs* dots, float* s32, bool dots_init, int part) {
   const int ph = dots_init ? kPhResInit : kPhFcg;
   const int L = (int)p.g.size();
   const Grid& g0 = p.g[0];
+  const int stop = p.lt > 0 ? p.lt : L - 1;  // grids [0, stop) by per-grid kernels
+  if (part == 2) {
+    // the map grid's last step alone
+    if (L == 1) {
+      k_mg_post2<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(g0, mask, p.s0, S);
+      if (s32) k_mg_to32<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(p.s0, s32, g0, S);
+    } else {
+      up_level(p, 0, stop, mask, S, st, dots, s32, ph);
+    }
+    return cudaGetLastError();
+  }
   if (!packed) k_mg_rhs_v<<<mg_blocks(p, (long long)g0.H * ((g0.W + 3) / 4)), 256, 0, st>>>(p.r0, g0, S);
   if (L == 1) {
     k_mg_coarsest<<<1, 256, 0, st>>>(g0, S);
-    k_mg_post2<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(g0, mask, p.s0, S);
-    if (s32) k_mg_to32<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(p.s0, s32, g0, S);
+    if (part == 0) {
+      k_mg_post2<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(g0, mask, p.s0, S);
+      if (s32) k_mg_to32<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(p.s0, s32, g0, S);
+    }
     return cudaGetLastError();
   }
-  const int stop = p.lt > 0 ? p.lt : L - 1;  // grids [0, stop) by per-grid kernels
   for (int l = 0; l < stop; ++l) {
     const Grid& f = p.g[l];
     if (p.kind[l] == kWalk) {
@@ -1432,44 +1488,7 @@ cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cu
   } else {
     k_mg_coarsest<<<1, 256, 0, st>>>(p.g[L - 1], S);
   }
-  for (int l = stop - 1; l >= 0; --l) {
-    const Grid& f = p.g[l];
-    if (p.kind[l] != kPerStep) {
-      // the coarse grid's corrected solution: the t plane if a fused kernel made it, else x
-      const Grid& c = p.g[l + 1];
-      const float* xc = (l + 1 < stop && p.kind[l + 1] != kPerStep) ? c.t : c.x;
-      const int R = p.rows_up[l];
-      const bool d = l == 0 && dots && p.dots_units > 0;
-      const PcgArgs* pa = d ? dots : nullptr;
-      const int mode = l > 0 ? kUpCoarse : (s32 ? kUp32 : kUp64);
-      const double* rv = (mode == kUp64 && d) ? p.r0 : nullptr;
-      double* s64 = mode == kUp64 ? p.s0 : nullptr;
-      const uint8_t* mk = l == 0 ? mask : nullptr;
-      float* o32 = mode == kUp32 ? s32 : nullptr;
-      if (p.kind[l] == kWalk) {
-        const unsigned nb = walk_blocks(f, f.H, R);
-        const unsigned nt = kWalkWarps * 32;
-        if (mode == kUp32) k_mg_up_w<kUp32><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
-        else if (mode == kUp64) k_mg_up_w<kUp64><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
-        else k_mg_up_w<kUpCoarse><<<nb, nt, kUpRingSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
-      } else {
-        const unsigned nb = tile_blocks(f, R);
-        if (mode == kUp32) k_mg_up_t<kUp32><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
-        else if (mode == kUp64) k_mg_up_t<kUp64><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
-        else k_mg_up_t<kUpCoarse><<<nb, kTileThreads, kTileSmem, st>>>(f, c, xc, R, mk, s64, rv, o32, pa, S, ph);
-      }
-    } else if (f.W >= kVecMinW) {
-      k_mg_sweep_v<kSrcXP><<<row_blocks(f, f.H), 256, 0, st>>>(f, p.g[l + 1], f.t, nullptr, nullptr, S);
-      k_mg_sweep_v<kSrcT><<<row_blocks(f, f.H), 256, 0, st>>>(f, Grid{}, f.x, l == 0 ? mask : nullptr,
-                                                               l == 0 ? p.s0 : nullptr, S);
-    } else {
-      k_mg_post1<<<mg_blocks(p, (long long)f.H * f.W), 256, 0, st>>>(f, p.g[l + 1], S);
-      k_mg_post2<<<mg_blocks(p, (long long)f.H * f.W), 256, 0, st>>>(f, l == 0 ? mask : nullptr,
-                                                                    l == 0 ? p.s0 : nullptr, S);
-    }
-  }
-  if (s32 && !(p.kind[0] != kPerStep && stop > 0))
-    k_mg_to32<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(p.s0, s32, g0, S);
+  for (int l = stop - 1; l >= (part == 1 ? 1 : 0); --l) up_level(p, l, stop, mask, S, st, dots, s32, ph);
   return cudaGetLastError();
 }
 

@@ -63,7 +63,7 @@ class ulp_stats(ctypes.Structure):
 class ulp_counters(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("solver_launches", ctypes.c_longlong),
                 ("solver_ms", ctypes.c_double), ("timed_launches", ctypes.c_longlong),
-                ("phase_ms", ctypes.c_double * 5), ("phase_launches", ctypes.c_longlong * 5),
+                ("phase_ms", ctypes.c_double * 6), ("phase_launches", ctypes.c_longlong * 6),
                 ("graph_start_kernels", ctypes.c_longlong), ("graph_body_kernels", ctypes.c_longlong)]
 
 
@@ -247,10 +247,10 @@ class Plan:
 
     def counters(self, reset=False):
         """ulp_plan_counters(): kernel launches, solver launches, (profile=1) solver ms and
-        (profile=2, flexible CG) per-phase ms and counts keyed A, B, R, M, D."""
+        (profile=2, flexible CG) per-phase ms and counts keyed A, B, R, M, D, U."""
         c = ulp_counters()
         _check(load().ulp_plan_counters(self._h, int(bool(reset)), ctypes.byref(c)))
-        names = ("A", "B", "R", "M", "D")
+        names = ("A", "B", "R", "M", "D", "U")
         return {"kernel_launches": c.kernel_launches, "solver_launches": c.solver_launches,
                 "solver_ms": c.solver_ms, "timed_launches": c.timed_launches,
                 "phase_ms": {n: c.phase_ms[k] for k, n in enumerate(names)},

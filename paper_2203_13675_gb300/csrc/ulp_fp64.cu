@@ -201,11 +201,13 @@ __global__ void k_system_x(const MapDesc* __restrict__ maps, MapState* S) {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const double d = __dadd_rn(__dadd_rn(__dadd_rn(uw[k], uev[k]), vnv[k]), vsv[k]);
+      // b as in k_system, with fused multiply-adds (this form's system is not compared bit
+      // for bit with the FP64 one: its weights are FP32); FP64 issue is what bounds the kernel
       double bk = 0.0;
-      if (j + k > 0) bk = __dadd_rn(bk, __dmul_rn(dxwv[k], uw[k]));
-      bk = __dsub_rn(bk, __dmul_rn(dxv2[k], uev[k]));
-      if (i > 0) bk = __dadd_rn(bk, __dmul_rn(dynv[k], vnv[k]));
-      bk = __dsub_rn(bk, __dmul_rn(dyv2[k], vsv[k]));
+      if (j + k > 0) bk = __dmul_rn(dxwv[k], uw[k]);
+      bk = __fma_rn(-dxv2[k], uev[k], bk);
+      if (i > 0) bk = __fma_rn(dynv[k], vnv[k], bk);
+      bk = __fma_rn(-dyv2[k], vsv[k], bk);
       d2[k] = d;
       b2[k] = bk;
       di[k] = (d > 0.0) ? __fdiv_rn(1.f, (float)d) : 0.f;

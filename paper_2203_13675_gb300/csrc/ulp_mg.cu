@@ -1371,8 +1371,9 @@ cudaError_t mg_setup(const MgPlan& p, const MapState* S, cudaStream_t st, bool l
   const Grid& g0 = p.g[0];
   if (level0) k_mg_level0<<<mg_blocks(p, (long long)g0.H * g0.W), 256, 0, st>>>(p.U0, p.V0, p.Dinv0, g0, S);
   // one launch per coarse grid while it has more than kCoarsenSmall unknowns, then one
-  // block for all the smaller ones (same arithmetic per aggregate)
-  constexpr long long kCoarsenSmall = 16384;
+  // block for all the smaller ones (same arithmetic per aggregate); one block walking a
+  // 128^2 grid serialised its memory latency (38 us for the grids of 16384 and fewer)
+  constexpr long long kCoarsenSmall = 1024;
   size_t l = 0;
   for (; l + 1 < p.g.size(); ++l) {
     const Grid& c = p.g[l + 1];

@@ -186,7 +186,8 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
         S->stall = 0;
       } else if (ph == kPhFcg) {
         // flexible CG (Polak-Ribiere): beta = r_{k+1}^T (s_{k+1} - s_k) / (r_k^T s_k), v2 = r_{k+1}^T s_k
-        refreshed = (S->iter % M.refresh) == 0 || S->force_refresh;
+        refreshed = (a.xfcg ? (S->iter > 0 && (S->iter % M.refresh) == 0) : (S->iter % M.refresh) == 0) ||
+                    S->force_refresh;
         const double dold = S->delta;
         S->delta = v0;
         S->rr = v1;
@@ -319,10 +320,13 @@ __device__ __forceinline__ void tile_arrive(const PcgArgs& a, const MapDesc& M, 
 // or b^T b at the start of a solve, ph = kPhResInit) are indexed by the map's
 // tiles, so the last warp of group g sums P2 over the map's tiles of group g.
 // Same fixed summation order on every run.
+// rr_tiles: r^T r comes, like the third sum, as per-tile partials in P1 (left by the
+// kernels that wrote r) instead of from this kernel.
 __device__ __forceinline__ void warp_arrive_fcg(const PcgArgs& a, const MapDesc& M, MapState* S, int w, int n,
-                                                double rs, double rr, int lane, int ph = kPhFcg) {
+                                                double rs, double rr, int lane, int ph = kPhFcg,
+                                                bool rr_tiles = false) {
   rs = warp_sum(rs);
-  rr = warp_sum(rr);
+  if (!rr_tiles) rr = warp_sum(rr);
   const int base = M.tile_base;
   const int g = w % kArriveGroups;
   const int gsize = (n - g + kArriveGroups - 1) / kArriveGroups;
@@ -330,7 +334,7 @@ __device__ __forceinline__ void warp_arrive_fcg(const PcgArgs& a, const MapDesc&
   int glast = 0;
   if (lane == 0) {
     __stcg(a.P0 + base + w, rs);
-    __stcg(a.P1 + base + w, rr);
+    if (!rr_tiles) __stcg(a.P1 + base + w, rr);
     glast = atom_add_acq_rel(&S->arrive_grp[g], 1u) == (unsigned)gsize - 1u;
   }
   glast = __shfl_sync(kFull, glast, 0);
@@ -341,10 +345,14 @@ __device__ __forceinline__ void warp_arrive_fcg(const PcgArgs& a, const MapDesc&
   for (int m = lane; m < gsize; m += 32) {
     const int idx = base + g + kArriveGroups * m;
     s0 += __ldcg(a.P0 + idx);
-    s1 += __ldcg(a.P1 + idx);
+    if (!rr_tiles) s1 += __ldcg(a.P1 + idx);
   }
 #pragma unroll 4
-  for (int m = lane; m < gsize2; m += 32) s2 += __ldcg(a.P2 + base + g + kArriveGroups * m);
+  for (int m = lane; m < gsize2; m += 32) {
+    const int idx = base + g + kArriveGroups * m;
+    s2 += __ldcg(a.P2 + idx);
+    if (rr_tiles) s1 += __ldcg(a.P1 + idx);
+  }
   s0 = warp_sum(s0);
   s1 = warp_sum(s1);
   s2 = warp_sum(s2);

@@ -229,13 +229,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_f_dots(const PcgArgs* pa, int i
 // writes s in FP32.  Once the recurrence reports convergence, every remaining
 // iteration is a refresh iteration, so the solve stops on a true residual.
 //   A: d = s + beta d, q = A d, d^T q  (the mixed engine's phase A)
-//   B: x += alpha d; r -= alpha q and r_{k+1}^T s_k, or on refresh iterations phi += x, x = 0
-//   R: on refresh iterations r = b - A phi (FP64, rounded to FP32) and r_{k+1}^T s_k
-//   M: the V-cycle, whose last kernel also runs the dot phase
+//   B: x += alpha d; r -= alpha q, r_{k+1}^T s_k and r^T r per tile, or on refresh
+//      iterations phi += x, x = 0
+//   R: on refresh iterations r = b - A phi (FP64, rounded to FP32), r_{k+1}^T s_k, r^T r
+//   M: the V-cycle, whose last kernel sums r^T s and runs the dot phase
 
+// refresh iterations: every M.refresh-th after the first (the start computed r in FP64
+// just before iteration 0), and every one once the recurrence has reported convergence
 __device__ __forceinline__ bool x_refresh(const MapDesc& M, MapState* S) {
   const long long it = *(volatile long long*)&S->iter;
-  return (it % M.refresh) == 0 || *(volatile int*)&S->force_refresh;
+  return (it > 0 && (it % M.refresh) == 0) || *(volatile int*)&S->force_refresh;
 }
 
 __global__ void __launch_bounds__(kThreads, 2) k_x_a(const PcgArgs* pa) {
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_b(const PcgArgs* pa) {
     const float* __restrict__ d = (it & 1) ? M.h.d0 : M.h.d1;
     const float alpha = (float)*(volatile double*)&S->alpha;
     const int j = g.j0 + 2 * lane;
-    DF rsp;
+    DF rsp, rrp;
     // rows in groups of four, all loads of a group issued before its stores
     for (int i = g.i0; i < g.i1; i += 4) {
       float2 dv[4], xv[4], qv[4], rv[4], sv[4];
@@ -295,19 +298,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_b(const PcgArgs* pa) {
             stf2(M.h.r, off, r);
             rsp.add_prod(r.x, sv[k].x);
             rsp.add_prod(r.y, sv[k].y);
+            rrp.add_prod(r.x, r.x);
+            rrp.add_prod(r.y, r.y);
           }
         }
       }
     }
     if (!refresh) {
-      const double v = warp_sum(rsp.value());
-      if (lane == 0) __stcg(a.P2 + t, v);
+      // r_{k+1}^T s_k and r_{k+1}^T r_{k+1} per tile for the dot phase
+      const double v = warp_sum(rsp.value()), w = warp_sum(rrp.value());
+      if (lane == 0) {
+        __stcg(a.P2 + t, v);
+        __stcg(a.P1 + t, w);
+      }
     }
   }
 }
 
-// r = b - A phi in FP64, rounded to FP32 (x = 0 with it at the start, and the b^T b
-// partials for the start's dot phase); on refresh iterations also r_{k+1}^T s_k.
+// r = b - A phi in FP64, rounded to FP32, and its r^T r per tile (x = 0 with it at the
+// start, and the b^T b partials for the start's dot phase); on refresh iterations also
+// r_{k+1}^T s_k.
 __global__ void __launch_bounds__(kThreads, 2) k_x_res(const PcgArgs* pa, int init) {
   const PcgArgs a = *pa;
   FCG_TILE_LOOP(a) {
@@ -315,12 +325,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_res(const PcgArgs* pa, int in
     if (!init && !x_refresh(M, S)) return;
     const TileGeo g = tile_geo(M, t, a.R);
     XPlane x{M.f.phi, (size_t)M.pitch};
-    DF rsp;
+    DF rsp, rrp;
     double bb = 0.0;
     auto epi = [&](size_t off, double2, double2 ax) {
       const double2 bv = ld2(M.f.b, off);
       const float2 r = make_float2((float)(bv.x - ax.x), (float)(bv.y - ax.y));
       stf2(M.h.r, off, r);
+      rrp.add_prod(r.x, r.x);
+      rrp.add_prod(r.y, r.y);
       if (init) {
         stf2(M.h.x, off, make_float2(0.f, 0.f));
         bb = fma(bv.x, bv.x, bb);
@@ -332,8 +344,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_res(const PcgArgs* pa, int in
       }
     };
     stencil_tile(M, g.i0, g.i1, g.j0, lane, M.f.U, M.f.V, M.f.D, x, epi);
-    const double v = warp_sum(init ? bb : rsp.value());
-    if (lane == 0) __stcg(a.P2 + t, v);
+    const double v = warp_sum(init ? bb : rsp.value()), w = warp_sum(rrp.value());
+    if (lane == 0) {
+      __stcg(a.P2 + t, v);
+      __stcg(a.P1 + t, w);
+    }
   }
 }
 

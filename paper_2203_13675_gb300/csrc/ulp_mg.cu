@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_up_t(Grid f, Grid c, const 
   __syncthreads();
   // s at rows r0 .. r1-1
   double rs = 0.0, rr2 = 0.0;
-  DF rs32, rr32;
+  DF rs32;
 #pragma unroll
   for (int k = 0; k < kOut; ++k) {
     const int r = r0 + warp + kTileWarps * k;
@@ -624,15 +624,12 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_up_t(Grid f, Grid c, const 
                                     mk[k].w ? 0.f : v.w);
       *reinterpret_cast<float4*>(s32 + o) = sv;
       if (pa) {
-        // r is the cycle's right-hand side (zero beyond column W - 1, as is s there)
+        // r is the cycle's right-hand side (zero beyond column W - 1, as is s there);
+        // r^T r comes per tile from the kernels that wrote r
         rs32.add_prod(B.x, sv.x);
         rs32.add_prod(B.y, sv.y);
         rs32.add_prod(B.z, sv.z);
         rs32.add_prod(B.w, sv.w);
-        rr32.add_prod(B.x, B.x);
-        rr32.add_prod(B.y, B.y);
-        rr32.add_prod(B.z, B.z);
-        rr32.add_prod(B.w, B.w);
       }
     } else {
       // FP64 s, 0 on masked pixels and nothing beyond column W - 1
@@ -658,10 +655,7 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_up_t(Grid f, Grid c, const 
     }
   }
   if (MAP && pa) {
-    if (MODE == kUp32) {
-      rs = rs32.value();
-      rr2 = rr32.value();
-    }
+    if (MODE == kUp32) rs = rs32.value();
     // block sums in warp order, then the arrival of the block as one unit
     rs = warp_sum(rs);
     rr2 = warp_sum(rr2);
@@ -673,7 +667,7 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_up_t(Grid f, Grid c, const 
     if (warp == 0) {
       const PcgArgs a = *pa;
       const double v0 = lane < kTileWarps ? red[0][lane] : 0.0, v1 = lane < kTileWarps ? red[1][lane] : 0.0;
-      warp_arrive_fcg(a, a.maps[0], a.st, (int)blockIdx.x, (int)gridDim.x, v0, v1, lane, ph);
+      warp_arrive_fcg(a, a.maps[0], a.st, (int)blockIdx.x, (int)gridDim.x, v0, v1, lane, ph, MODE == kUp32);
     }
   }
 }
@@ -856,7 +850,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_mg_up_w(Grid f, Grid c, con
   float4 Um1 = z, Um2 = z, Vm1 = z, Vm2 = z, Vm3 = z, Dm1 = z, Dm2 = z, Bm1 = z, Bm2 = z;
   float4 XPm1 = z, XPm2 = z, Tm2 = z, Tm3 = z;
   double rs = 0.0, rr = 0.0;
-  DF rs32, rr32;
+  DF rs32;
 #pragma unroll
   for (int k = 0; k < kLead; ++k) {
     if (rb + k <= re) up_issue<MODE>(ring[k], f, c, xc, mask, rv, rb + k, j, lane);
@@ -893,15 +887,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_mg_up_w(Grid f, Grid c, con
           const float4 sv = make_float4(mk.x ? 0.f : v.x, mk.y ? 0.f : v.y, mk.z ? 0.f : v.z, mk.w ? 0.f : v.w);
           *reinterpret_cast<float4*>(s32 + o) = sv;
           if (pa) {
-            // r is the cycle's right-hand side (zero beyond column W - 1, as is s there)
+            // r is the cycle's right-hand side (zero beyond column W - 1, as is s there);
+            // r^T r comes per tile from the kernels that wrote r
             rs32.add_prod(Bm2.x, sv.x);
             rs32.add_prod(Bm2.y, sv.y);
             rs32.add_prod(Bm2.z, sv.z);
             rs32.add_prod(Bm2.w, sv.w);
-            rr32.add_prod(Bm2.x, Bm2.x);
-            rr32.add_prod(Bm2.y, Bm2.y);
-            rr32.add_prod(Bm2.z, Bm2.z);
-            rr32.add_prod(Bm2.w, Bm2.w);
           }
         } else {
           // the map's grid: FP64 s, 0 on masked pixels and nothing beyond column W - 1
@@ -938,11 +929,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_mg_up_w(Grid f, Grid c, con
   if (MAP && pa) {
     const PcgArgs a = *pa;
     const int nseg = (f.W + kSegOut - 1) / kSegOut;
-    if (MODE == kUp32) {
-      rs = rs32.value();
-      rr = rr32.value();
-    }
-    warp_arrive_fcg(a, a.maps[0], a.st, band * nseg + seg, nseg * bands, rs, rr, lane, ph);
+    if (MODE == kUp32) rs = rs32.value();
+    warp_arrive_fcg(a, a.maps[0], a.st, band * nseg + seg, nseg * bands, rs, rr, lane, ph, MODE == kUp32);
   }
 }
 

@@ -55,3 +55,39 @@ def test_full_size_run_matches_the_oracle(key):
     ii, jj = np.array(g["sample_i"]), np.array(g["sample_j"])
     e = (got[ii, jj] - mean) - np.array(g["sample_phi_mean_removed"])
     assert np.sqrt(np.mean(e ** 2)) < 1e-4, np.sqrt(np.mean(e ** 2))
+
+
+# The bench's chosen form -- the mixed-precision multigrid flexible CG (FP32 weights,
+# recurrence and V-cycle, FP64 inner products and true residual) -- replayed at full size
+# against every multigrid run the oracle recorded: per pass within -3..+4 of the oracle's
+# FP64 counts (FP32 rounding of the cycle and the recurrence, and one more iteration
+# where the stop seen on the recurrence is confirmed on the true residual).  Its phase is
+# the solution of the system with FP32-rounded weights, reached along an FP32 path and
+# stopped at relative residual tol like the oracle's: two such solutions lie anywhere
+# within the set the tolerance allows (the plain and multigrid FP64 solutions of the
+# 2048^2 map, both exact to their oracle runs, are 0.011 rad apart), so the distance to
+# the oracle is measured and reported (about 2e-4 rad RMS on the C2 maps) and held
+# under 1e-3 rad; test_gpu_mg.py checks that the returned phi meets tol on the FP64
+# operator.
+@pytest.mark.parametrize("key", sorted(k for k in GOLD if GOLD[k]["precond"] == "mg"))
+def test_full_size_mixed_multigrid_matches_the_oracle(key):
+    g = GOLD[key]
+    m = synth.workload_map(g["workload"])
+    H, W = m.psi.shape
+    plan = native.Plan(H, W, outer_tol=g["outer_tol"], precision=native.ULP_PRECISION_MIXED)
+    mask = torch.from_numpy(m.mask).cuda() if m.mask is not None else None
+    phi, st = plan.unwrap(torch.from_numpy(m.psi).cuda(), mask, p=g["p"], eps=g["tau"], precond="mg",
+                          tol=g["tol"], max_outer=g["max_outer"])
+    assert st["status"] == 0, st
+    assert st["outer"] == g["stats"]["outer"], (st["inner"], g["stats"]["inner"])
+    for a, b in zip(st["inner"], g["stats"]["inner"]):
+        assert -3 <= a - b <= 4, (st["inner"], g["stats"]["inner"])
+    got = phi.cpu().numpy()
+    keep = np.ones(got.shape, bool) if m.mask is None else (m.mask == 0)
+    mean = got[keep].mean()
+    ii, jj = np.array(g["sample_i"]), np.array(g["sample_j"])
+    e = (got[ii, jj] - mean) - np.array(g["sample_phi_mean_removed"])
+    rms = float(np.sqrt(np.mean(e ** 2)))
+    print(f"{key}: mixed multigrid vs the FP64 oracle, {rms:.2e} rad RMS at 256 pixels; inner {st['inner']} "
+          f"vs {g['stats']['inner']}")
+    assert rms < 1e-3, rms

@@ -207,17 +207,18 @@ static bool make_map(CUtensorMap* tm, const void* ptr, int rows, int cols) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// dynamic shared memory above 48 KB is an attribute of the function on the current device:
+// set when a plan is made on it
+static void gemm_attrs() {
+  cudaFuncSetAttribute(k_gemm_nt<kEpiBf16T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  cudaFuncSetAttribute(k_gemm_nt<kEpiBf16TScale>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  cudaFuncSetAttribute(k_gemm_nt<kEpiF64TMask>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+}
+
 template <int EPI>
 static cudaError_t gemm(const void* A, int M, const void* B, int N, int K, const GemmOut& o, cudaStream_t st) {
   CUtensorMap ta, tb;
   if (!make_map(&ta, A, M, K) || !make_map(&tb, B, N, K)) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gemm_nt<kEpiBf16T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
-    cudaFuncSetAttribute(k_gemm_nt<kEpiBf16TScale>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
-    cudaFuncSetAttribute(k_gemm_nt<kEpiF64TMask>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
-    attr = true;
-  }
   dim3 grid(N / kBN, M / kBM);
   k_gemm_nt<EPI><<<grid, 128, kGemmSmem, st>>>(ta, tb, K, o);
   return cudaGetLastError();
@@ -298,6 +299,7 @@ int dct_setup(DctPlan& d, int H, int W, void* mem) {
 }
 
 DctPlan* dct_create(int H, int W, void* mem) {
+  gemm_attrs();
   DctPlan* d = new DctPlan();
   if (dct_setup(*d, H, W, mem) != 0) {
     delete d;

@@ -1268,8 +1268,10 @@ MgPlan* mg_create(const MapDesc& M, void* mem, int nsm, int ntiles) {
   // fused kernels (walkers or tiles) on every grid at least kVecMinW wide; the map grid's
   // up kernel carries the dot phase if its warps or blocks fit the plan's per-tile partial
   // arrays
-  static bool attr = false;
-  if (!attr) {
+  // dynamic shared memory above 48 KB is an attribute of the function on the current
+  // device: set on every plan creation (the plan's device is current here)
+  {
+    cudaFuncSetAttribute(k_mg_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(6 * kTailPx * sizeof(float)));
     cudaFuncSetAttribute(k_mg_down_t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
     cudaFuncSetAttribute(k_mg_up_t<kUpCoarse>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
     cudaFuncSetAttribute(k_mg_up_t<kUp64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
@@ -1278,7 +1280,6 @@ MgPlan* mg_create(const MapDesc& M, void* mem, int nsm, int ntiles) {
     cudaFuncSetAttribute(k_mg_up_w<kUpCoarse>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpRingSmem);
     cudaFuncSetAttribute(k_mg_up_w<kUp64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpRingSmem);
     cudaFuncSetAttribute(k_mg_up_w<kUp32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpRingSmem);
-    attr = true;
   }
   // one resident wave of each walker (the ring's shared memory limits the up walker to
   // three blocks per SM): more warps than that run as a second, mostly idle wave
@@ -1466,13 +1467,6 @@ cudaError_t mg_apply(const MgPlan& p, const uint8_t* mask, const MapState* S, cu
     }
   }
   if (p.lt > 0) {
-    static bool attr = false;
-    if (!attr) {
-      const cudaError_t e = cudaFuncSetAttribute(k_mg_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(6 * kTailPx * sizeof(float)));
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
     k_mg_tail<<<1, kTailThreads, p.tail_smem, st>>>(p.tail, S);
   } else {
     k_mg_coarsest<<<1, 256, 0, st>>>(p.g[L - 1], S);

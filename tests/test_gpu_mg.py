@@ -120,3 +120,23 @@ def test_mixed_mg_pcg_true_residual(H, W, tol):
     if tol >= 1e-6:
         _, rst = oracle.pcg(A, np.zeros((H, W)), kind=oracle.M_MG, tol=tol)
         assert -3 <= st["inner"][0] - rst["iters"] <= 4, (st, rst)
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+def test_mg_walkers_on_odd_sizes_vs_oracle(precision):
+    """A 1001 x 999 map with a masked disk takes the row-walker kernels on its own grid
+    (odd in both dimensions: a ragged last 120-column window and last band, partial row
+    copies at column W - 1) and the tile kernels below.  FP64 form: counts within 3 and
+    1e-4 rad RMS against the oracle's multigrid PCG; mixed form: counts -3..+4 and within
+    the 1e-3 rad the full-size replays allow (test_gpu_golden.py)."""
+    H, W = 1001, 999
+    m = synth.phase_map(H, W, 31, ramp=0.02, n_bumps=12, noise=0.5, mask_frac=0.05, sigma_range=(10.0, 40.0))
+    mixed = precision == "mixed"
+    plan = native.Plan(H, W, outer_tol=0.0, precision=native.ULP_PRECISION_MIXED if mixed else 0)
+    phi, st = plan.unwrap(_cuda(m.psi), _cuda(m.mask, torch.uint8), p=1.0, precond="mg", tol=1e-6, max_outer=2)
+    ref, rst = oracle.unwrap(m.psi, m.mask, p=1.0, kind=oracle.M_MG, tol=1e-6, max_outer=2)
+    assert st["status"] == 0, st
+    rms = _rms(phi.cpu().numpy(), ref, m.mask == 0)
+    assert rms < (1e-3 if mixed else 1e-4), rms
+    for a, b in zip(st["inner"], rst["inner"]):
+        assert (-3 <= a - b <= 4) if mixed else abs(a - b) <= 3, (st["inner"], rst["inner"])

@@ -560,8 +560,12 @@ def fcg_roofline(native, H, W, psi, mask, w, precond, timed_plan, prec="f64"):
 # ------------------------------------------------------------------ batched workload
 def run_batch(args):
     """64 maps of uneven sizes (256..2048 square, own seed, p in {0, 1}, noise 0.1-0.8),
-    solved together: one persistent launch per outer pass, the whole call captured in a
-    CUDA graph and replayed, tile shape from ulp_autotune.  Mpixel/s = sum of H W / time."""
+    solved together: one persistent Jacobi PCG launch per outer pass, the whole call captured
+    in a CUDA graph and replayed, tile shape from ulp_autotune.  Mpixel/s = sum of H W / time.
+    Both precisions are timed; the line reports the mixed one (FP32 recurrence, FP64 dots
+    and true residual) with the FP64 one as its plain form and their largest per-map RMS
+    distance."""
+    import numpy as np
     import torch
     from paper_2203_13675_gb300 import native, synth
     rank, world, local = env_rank()
@@ -569,35 +573,50 @@ def run_batch(args):
     native.load()
     specs = synth.batch_specs(64)
     pm = synth.batch_maps(specs)
-    maps = [{"psi": torch.from_numpy(m.psi).cuda(), "mask": None,
-             "phi": torch.empty(m.psi.shape, dtype=torch.float64, device="cuda"), "p": sp["p"], "eps": 1e-2}
-            for m, sp in zip(pm, specs)]
     sizes = [tuple(m.psi.shape) for m in pm]
     px = sum(h * w for h, w in sizes)
-    tuned = native.ulp_autotune(maps, "jacobi", native.ULP_PRECISION_FP64, iters=30)
-    tuned.outer_tol = 0.0
-    tuned.graph = 1
-    plan = native.Plan(None, sizes=sizes, options=tuned)
-    for _ in range(args.warmup):
-        plan.unwrap_batched(maps, precond="jacobi", tol=1e-6, max_outer=5, stats=False)
-    torch.cuda.synchronize()
-    rc, stats = plan.last_status()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        plan.unwrap_batched(maps, precond="jacobi", tol=1e-6, max_outer=5, stats=False)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    rc, per = plan.unwrap_batched(maps, precond="jacobi", tol=1e-6, max_outer=5, stats=True)
-    line = {"metric": METRIC, "value": px / (ms * 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batch64_jacobi", "maps": len(sizes), "total_px": px,
-                       "tile_rows": tuned.tile_rows, "blocks_per_sm": tuned.blocks_per_sm,
-                       "graph": True, "inner_iterations_max_map": max(max(p["inner"]) for p in per),
-                       "worst_status": min(p["status"] for p in per)}}
+    out = {}
+    for prec in ("f64", "mixed"):
+        maps = [{"psi": torch.from_numpy(m.psi).cuda(), "mask": None,
+                 "phi": torch.empty(m.psi.shape, dtype=torch.float64, device="cuda"), "p": sp["p"], "eps": 1e-2}
+                for m, sp in zip(pm, specs)]
+        precision = native.ULP_PRECISION_MIXED if prec == "mixed" else native.ULP_PRECISION_FP64
+        tuned = native.ulp_autotune(maps, "jacobi", precision, iters=30)
+        tuned.outer_tol = 0.0
+        tuned.graph = 1
+        plan = native.Plan(None, sizes=sizes, options=tuned)
+        for _ in range(args.warmup):
+            plan.unwrap_batched(maps, precond="jacobi", tol=1e-6, max_outer=5, stats=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            plan.unwrap_batched(maps, precond="jacobi", tol=1e-6, max_outer=5, stats=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        rc, per = plan.unwrap_batched(maps, precond="jacobi", tol=1e-6, max_outer=5, stats=True)
+        out[prec] = {"ms": ms, "tuned": tuned, "per": per, "phi": [m["phi"].cpu().numpy() for m in maps]}
+        del plan
+
+    def rms(a, b):
+        d = a - b
+        d = d - d.mean()
+        return float(np.sqrt(np.mean(d * d)))
+    dist = max(rms(a, b) for a, b in zip(out["mixed"]["phi"], out["f64"]["phi"]))
+    c, f = out["mixed"], out["f64"]
+    line = {"metric": METRIC, "value": px / (c["ms"] * 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": c["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE["mixed"], "data": "synthetic",
+            "config": {"workload": "batch64_jacobi", "maps": len(sizes), "total_px": px, "precision": "mixed",
+                       "tile_rows": c["tuned"].tile_rows, "blocks_per_sm": c["tuned"].blocks_per_sm,
+                       "graph": True, "inner_iterations_max_map": max(max(p["inner"]) for p in c["per"]),
+                       "worst_status": min(p["status"] for p in c["per"])},
+            "plain": {"value": px / (f["ms"] * 1e3), "unit": UNIT, "ms_per_step": f["ms"], "dtype": "f64",
+                      "tile_rows": f["tuned"].tile_rows, "blocks_per_sm": f["tuned"].blocks_per_sm,
+                      "worst_status": min(p["status"] for p in f["per"])},
+            "max_map_rms_vs_plain_rad": dist}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

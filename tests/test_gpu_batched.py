@@ -97,3 +97,29 @@ def test_last_status_of_a_batched_plan_is_the_first_map():
     for _ in range(3):
         rc, st = plan.last_status()
         assert rc == rc_all and st["inner"] == per[0]["inner"]
+
+
+def test_batched_mixed_precision():
+    """The batched persistent solve in mixed precision (FP32 recurrence, FP64-accurate
+    dots, FP64 phi and true residual every 20 iterations): each map equals its
+    single-map mixed solve with the same tiles, and agrees with the oracle's Jacobi PCG
+    within the 1e-4 rad bar (the reliable-update refresh keeps the FP32 recurrence on
+    the FP64 system), the counts within 2 + 1 %."""
+    pm = _batch(seed0=950)
+    plan = native.Plan(None, sizes=SIZES, outer_tol=0.0, tile_rows=16, precision=native.ULP_PRECISION_MIXED)
+    dev = [{"psi": _cuda(m.psi), "mask": _cuda(m.mask, torch.uint8) if m.mask is not None else None,
+            "phi": torch.empty(m.psi.shape, dtype=torch.float64, device="cuda"), "p": p} for m, p in pm]
+    rc, stats = plan.unwrap_batched(dev, precond="jacobi", tol=1e-6, max_outer=2)
+    assert rc >= 0
+    for (m, p), d, st in zip(pm, dev, stats):
+        mk = _cuda(m.mask, torch.uint8) if m.mask is not None else None
+        single = native.Plan(*m.psi.shape, outer_tol=0.0, tile_rows=16, precision=native.ULP_PRECISION_MIXED)
+        phi, s1 = single.unwrap(_cuda(m.psi), mk, p=p, precond="jacobi", tol=1e-6, max_outer=2)
+        assert s1["inner"] == st["inner"]
+        assert torch.equal(phi, d["phi"])
+        ref, rst = oracle.unwrap(m.psi, m.mask, p=p, kind=oracle.M_JACOBI, tol=1e-6, max_outer=2)
+        keep = None if m.mask is None else m.mask == 0
+        assert st["status"] == 0, st
+        for a, b in zip(st["inner"], rst["inner"]):
+            assert abs(a - b) <= 2 + int(0.01 * b), (st["inner"], rst["inner"])
+        assert _rms(d["phi"].cpu().numpy(), ref, keep) < 1e-4

@@ -95,6 +95,35 @@ def env_rank():
         int(os.environ.get("LOCAL_RANK", 0))
 
 
+def init_ranks(backend="nccl"):
+    """One process per GPU under torchrun: (rank, world, local rank, torch.distributed or None)."""
+    import torch
+    rank, world, local = env_rank()
+    if world <= 1:
+        return rank, world, local, None
+    import torch.distributed as td
+    if not td.is_initialized():
+        if backend == "nccl":
+            td.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            td.init_process_group(backend)
+    return rank, world, local, td
+
+
+def max_over_ranks(vals, dist=None, device="cpu"):
+    """Per-rank timings -> their maximum over the ranks (every rank receives it)."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], device=device, dtype=torch.float64)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_throughput(px_per_rank, world, ms):
+    """Whole-job Mpixel/s: every rank's pixels over the slowest rank's step time."""
+    return px_per_rank * world / (ms * 1e3)
+
+
 def load_peaks_all():
     """HBM GB/s and bf16 TFLOP/s (burst, sustained) from MEASURED_PEAKS.json, else the fallback."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -285,12 +314,7 @@ def run_form(plan, psi, mask, phi, w, precond, steps, warmup, dist):
 def run_ours(args):
     import torch
     from paper_2203_13675_gb300 import native, synth
-    rank, world, local = env_rank()
-    dist = None
-    if world > 1:
-        import torch.distributed as td
-        td.init_process_group("nccl", device_id=torch.device("cuda", local))
-        dist = td
+    rank, world, local, dist = init_ranks()
     torch.cuda.set_device(local)
     native.load()
     wl_name = args.workload
@@ -383,13 +407,10 @@ def run_ours(args):
         dist.barrier()
 
     # max over ranks
-    vals = torch.tensor([ms, ms_plain, ms_e2e], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms, ms_plain, ms_e2e = [float(x) for x in vals.cpu()]
-    px = H * W * world
+    ms, ms_plain, ms_e2e = max_over_ranks([ms, ms_plain, ms_e2e], dist, "cuda")
     line = {
-        "metric": METRIC, "value": px / (ms * 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": job_throughput(H * W, world, ms), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE[chosen[0]], "data": "synthetic",
         "config": {"workload": f"{wl_name}_p{w['p']:g}_{chosen[1]}", "H": H, "W": W, "p": w["p"],
@@ -398,13 +419,13 @@ def run_ours(args):
                    "noise": w["noise"], "seed": w["seed"], "parallelism": f"replicas{world}",
                    "l2": "working set ~0.5 GB of planes > 129 MB L2 (inputs larger than L2)",
                    "inner_iterations": st["inner"], "outer_passes": st["outer"]},
-        "plain": {"value": px / (ms_plain * 1e3), "unit": UNIT, "ms_per_step": ms_plain, "precond": "jacobi",
+        "plain": {"value": job_throughput(H * W, world, ms_plain), "unit": UNIT, "ms_per_step": ms_plain, "precond": "jacobi",
                   "dtype": "f64", "inner_iterations": st_plain["inner"],
                   "roofline": plain_roofline(st_plain, cnt_plain, H, W, args.steps, peak, peak_kind)},
         "roofline": roofline,
-        "e2e": {"value": px / (ms_e2e * 1e3), "unit": UNIT, "h2d_bytes_per_step": H * W * 8 + (H * W if mask is not None else 0),
+        "e2e": {"value": job_throughput(H * W, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": H * W * 8 + (H * W if mask is not None else 0),
                 "d2h_bytes_per_step": H * W * 8, "ms_per_step": ms_e2e},
-        "forms": {f"{k[0]}_{k[1]}": {"value": px / (v[0] * 1e3), "ms_per_step": v[0],
+        "forms": {f"{k[0]}_{k[1]}": {"value": job_throughput(H * W, world, v[0]), "ms_per_step": v[0],
                                      "inner_iterations": v[1]["inner"],
                                      "fallbacks": v[1].get("fallbacks", 0),
                                      "rms_vs_plain_rad": rms_diff(sols[k], sols[forms[0]], m.mask),
@@ -568,7 +589,7 @@ def run_batch(args):
     import numpy as np
     import torch
     from paper_2203_13675_gb300 import native, synth
-    rank, world, local = env_rank()
+    rank, world, local, dist = init_ranks()
     torch.cuda.set_device(local)
     native.load()
     specs = synth.batch_specs(64)
@@ -587,6 +608,8 @@ def run_batch(args):
         plan = native.Plan(None, sizes=sizes, options=tuned)
         for _ in range(args.warmup):
             plan.unwrap_batched(maps, precond="jacobi", tol=1e-6, max_outer=5, stats=False)
+        if dist:
+            dist.barrier()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -595,7 +618,9 @@ def run_batch(args):
             plan.unwrap_batched(maps, precond="jacobi", tol=1e-6, max_outer=5, stats=False)
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        if dist:
+            dist.barrier()
+        ms = max_over_ranks([e0.elapsed_time(e1) / args.steps], dist, "cuda")[0]
         rc, per = plan.unwrap_batched(maps, precond="jacobi", tol=1e-6, max_outer=5, stats=True)
         out[prec] = {"ms": ms, "tuned": tuned, "per": per, "phi": [m["phi"].cpu().numpy() for m in maps]}
         del plan
@@ -606,14 +631,16 @@ def run_batch(args):
         return float(np.sqrt(np.mean(d * d)))
     dist = max(rms(a, b) for a, b in zip(out["mixed"]["phi"], out["f64"]["phi"]))
     c, f = out["mixed"], out["f64"]
-    line = {"metric": METRIC, "value": px / (c["ms"] * 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC, "value": job_throughput(px, world, c["ms"]), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": c["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE["mixed"], "data": "synthetic",
-            "config": {"workload": "batch64_jacobi", "maps": len(sizes), "total_px": px, "precision": "mixed",
+            "config": {"workload": "batch64_jacobi", "maps": len(sizes), "total_px": px * world,
+                       "parallelism": f"replicas{world}", "precision": "mixed",
                        "tile_rows": c["tuned"].tile_rows, "blocks_per_sm": c["tuned"].blocks_per_sm,
                        "graph": True, "inner_iterations_max_map": max(max(p["inner"]) for p in c["per"]),
                        "worst_status": min(p["status"] for p in c["per"])},
-            "plain": {"value": px / (f["ms"] * 1e3), "unit": UNIT, "ms_per_step": f["ms"], "dtype": "f64",
+            "plain": {"value": job_throughput(px, world, f["ms"]), "unit": UNIT, "ms_per_step": f["ms"], "dtype": "f64",
                       "tile_rows": f["tuned"].tile_rows, "blocks_per_sm": f["tuned"].blocks_per_sm,
                       "worst_status": min(p["status"] for p in f["per"])},
             "max_map_rms_vs_plain_rad": dist}

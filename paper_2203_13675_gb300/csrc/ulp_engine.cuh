@@ -142,6 +142,14 @@ enum Phase { kPhResInit = 0, kPhA = 1, kPhB = 2, kPhRes = 3, kPhFcg = 4 };
 // the map's tile partials in a fixed order and advances its scalars
 // (alpha = delta_new / d^T q; delta_old, delta_new, beta; stop tests).
 // ngroups: how many group sums the arrival left (0: as many as the map's tiles make).
+// The finisher is the serial tail of its kernel (every other warp has left), so it is
+// built as few dependent memory round trips as possible: lane 0 loads every field of
+// the map's state it reads in the same round of L2 loads as the group sums (only the
+// finisher writes these fields, and every tile of the phase has arrived), works in
+// registers, and stores.  No fence closes it: the next phase reads the state after a
+// kernel boundary or after the grid barrier that follows every phase of the persistent
+// kernels (whose leading __syncthreads and fence cover this warp's stores).
+static_assert(kArriveGroups <= 32, "one lane per arrival group");
 __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, MapState* Sp, int ph, int lane,
                                            int ngroups = 0) {
   volatile MapState* S = Sp;
@@ -154,15 +162,30 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
   double v0 = own ? __ldcg(&Sp->gpart[0][lane]) : 0.0;
   double v1 = (own && cnt > 1) ? __ldcg(&Sp->gpart[1][lane]) : 0.0;
   double v2 = (own && cnt > 2) ? __ldcg(&Sp->gpart[2][lane]) : 0.0;
+  double delta = 0.0, delta0 = 0.0, bb = 0.0, rr_best = 0.0;
+  long long iter = 0;
+  int fallback = 0, restart = 0, stall = 0, force_refresh = 0, stop_after = 0;
+  if (lane == 0) {
+    delta = __ldcg(&Sp->delta);
+    delta0 = __ldcg(&Sp->delta0);
+    bb = __ldcg(&Sp->bb);
+    rr_best = __ldcg(&Sp->rr_best);
+    iter = __ldcg(&Sp->iter);
+    fallback = __ldcg(&Sp->fallback);
+    restart = __ldcg(&Sp->restart);
+    stall = __ldcg(&Sp->stall);
+    force_refresh = __ldcg(&Sp->force_refresh);
+    stop_after = __ldcg(&Sp->stop_after);
+  }
   v0 = warp_sum(v0);
   v1 = cnt > 1 ? warp_sum(v1) : 0.0;
   v2 = cnt > 2 ? warp_sum(v2) : 0.0;
+  bool done = false;
   if (lane == 0) {
-    bool done = false;
     bool refreshed = true;  // r is the true residual (mixed flexible CG: this iteration recomputed it)
     if (ph == kPhA) {
       S->dq = v0;
-      if ((!(v0 > 0.0) || !isfinite(v0)) && a.learned && !S->fallback) {
+      if ((!(v0 > 0.0) || !isfinite(v0)) && a.learned && !fallback) {
         // the network gave a direction that is not a descent direction: no step,
         // Jacobi from now on, and the next direction restarts (beta = 0)
         S->alpha = 0.0;
@@ -173,10 +196,15 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
         S->alpha = 0.0;
         S->stop_after = 1;
       } else {
-        S->alpha = S->delta / v0;
+        S->alpha = delta / v0;
       }
     } else {
+      const double rr = v1;
       if (ph == kPhResInit) {
+        delta = v0;
+        delta0 = v0;
+        bb = v2;
+        iter = 0;
         S->delta = v0;
         S->delta0 = v0;
         S->rr = v1;
@@ -186,39 +214,45 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
         S->stall = 0;
       } else if (ph == kPhFcg) {
         // flexible CG (Polak-Ribiere): beta = r_{k+1}^T (s_{k+1} - s_k) / (r_k^T s_k), v2 = r_{k+1}^T s_k
-        refreshed = (a.xfcg ? (S->iter > 0 && (S->iter % M.refresh) == 0) : (S->iter % M.refresh) == 0) ||
-                    S->force_refresh;
-        const double dold = S->delta;
+        refreshed = (a.xfcg ? (iter > 0 && (iter % M.refresh) == 0) : (iter % M.refresh) == 0) || force_refresh;
+        const double dold = delta;
+        delta = v0;
+        iter += 1;
         S->delta = v0;
         S->rr = v1;
-        S->beta = S->restart ? 0.0 : (v0 - v2) / dold;
+        S->beta = restart ? 0.0 : (v0 - v2) / dold;
         S->restart = 0;
-        S->iter += 1;
-        if (a.learned && !S->fallback) {
+        S->iter = iter;
+        if (a.learned && !fallback) {
           // progress test: ||r|| must halve (||r||^2 quarter) within every stall_window
           // iterations, measured from the last point where it did
-          if (v1 < 0.25 * S->rr_best) {
+          if (v1 < 0.25 * rr_best) {
             S->rr_best = v1;
             S->stall = 0;
-          } else if (++S->stall >= a.stall_window || !(v0 > 0.0)) {
-            S->fallback = 1;  // the next s is D^-1 r and the direction restarts from it
-            S->restart = 1;
+          } else {
+            S->stall = stall + 1;
+            if (stall + 1 >= a.stall_window || !(v0 > 0.0)) {
+              S->fallback = 1;  // the next s is D^-1 r and the direction restarts from it
+              S->restart = 1;
+            }
           }
         }
       } else {
-        const double dold = S->delta;
+        const double dold = delta;
+        delta = v0;
+        iter += 1;
         S->delta = v0;
         S->rr = v1;
         S->beta = v0 / dold;
-        S->iter += 1;
+        S->iter = iter;
       }
       const double tol2 = a.tol2;
-      const bool conv = (a.stop_mode == 1) ? !(S->delta > tol2 * S->delta0) : !(S->rr > tol2 * S->bb);
-      S->relres = (S->bb > 0.0) ? sqrt(S->rr / S->bb) : 0.0;
-      if (S->stop_after) {
+      const bool conv = (a.stop_mode == 1) ? !(delta > tol2 * delta0) : !(rr > tol2 * bb);
+      S->relres = (bb > 0.0) ? sqrt(rr / bb) : 0.0;
+      if (stop_after) {
         done = true;
-      } else if (S->bb == 0.0 || conv) {
-        if (ph == kPhFcg && a.xfcg && !refreshed && S->bb != 0.0) {
+      } else if (bb == 0.0 || conv) {
+        if (ph == kPhFcg && a.xfcg && !refreshed && bb != 0.0) {
           // the FP32 recurrence says converged: from here on every iteration recomputes the
           // true residual, and the solve stops on that (a single confirmation that lands just
           // above the tolerance would otherwise cost two iterations per attempt)
@@ -228,21 +262,21 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
           S->status = 0;
           if (ph == kPhFcg && a.xfcg && refreshed) S->x_clean = 1;  // this iteration folded x into phi
         }
-      } else if (S->iter >= (a.lmax > 0 ? a.lmax : 2LL * M.H * M.W)) {
+      } else if (iter >= (a.lmax > 0 ? a.lmax : 2LL * M.H * M.W)) {
         done = true;
         S->status = 1;
       }
     }
     S->arrive = 0u;
-#pragma unroll 1
-    for (int g = 0; g < kArriveGroups; ++g) S->arrive_grp[g] = 0u;
-    if (done) {
-      S->done = 1;
-      __threadfence();
-      atomicSub(a.n_active, 1);
-      if (a.cond) cudaGraphSetConditional(a.cond, 0);  // ends the graph's WHILE loop
-    }
+  }
+  // the arrival counters back to zero, one lane per group
+  if (lane < kArriveGroups) S->arrive_grp[lane] = 0u;
+  __syncwarp();
+  if (lane == 0 && done) {
+    S->done = 1;
     __threadfence();
+    atomicSub(a.n_active, 1);
+    if (a.cond) cudaGraphSetConditional(a.cond, 0);  // ends the graph's WHILE loop
   }
   __syncwarp();
 }

@@ -374,18 +374,21 @@ __device__ __forceinline__ void warp_arrive_fcg(const PcgArgs& a, const MapDesc&
   glast = __shfl_sync(kFull, glast, 0);
   if (!glast) return;
   __syncwarp();
+  // one loop over both index ranges, so that all of a lane's loads are in flight together
+  // (each sum still runs over its own range in the same order)
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  const int gmax = gsize > gsize2 ? gsize : gsize2;
 #pragma unroll 4
-  for (int m = lane; m < gsize; m += 32) {
+  for (int m = lane; m < gmax; m += 32) {
     const int idx = base + g + kArriveGroups * m;
-    s0 += __ldcg(a.P0 + idx);
-    if (!rr_tiles) s1 += __ldcg(a.P1 + idx);
-  }
-#pragma unroll 4
-  for (int m = lane; m < gsize2; m += 32) {
-    const int idx = base + g + kArriveGroups * m;
-    s2 += __ldcg(a.P2 + idx);
-    if (rr_tiles) s1 += __ldcg(a.P1 + idx);
+    if (m < gsize) {
+      s0 += __ldcg(a.P0 + idx);
+      if (!rr_tiles) s1 += __ldcg(a.P1 + idx);
+    }
+    if (m < gsize2) {
+      s2 += __ldcg(a.P2 + idx);
+      if (rr_tiles) s1 += __ldcg(a.P1 + idx);
+    }
   }
   s0 = warp_sum(s0);
   s1 = warp_sum(s1);

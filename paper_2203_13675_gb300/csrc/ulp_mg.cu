@@ -1063,32 +1063,43 @@ __device__ __forceinline__ void tail_up(const TailGrids& tg, const TailSmem& sm,
   tail_sync<WARPS>();
 }
 
-// Coarsest tail grid: thirty sweeps from zero (x and t ping-pong), result in x.
+// Coarsest tail grid: thirty sweeps from zero, result in x.  The grid has at most
+// kCoarseMax <= 32 unknowns, so warp 0 holds one unknown per lane in a register and
+// takes its four neighbours by shuffle: thirty sweeps without a barrier or a
+// shared-memory round trip between them, the same terms in the same order as tail_ax.
+static_assert(kCoarseMax <= 32, "the coarsest grid fits one warp");
 template <int WARPS>
 __device__ __forceinline__ void tail_coarsest(const TailGrids& tg, const TailSmem& sm, int l, int warp, int lane) {
   const int H = tg.g[l].H, W = tg.g[l].W, o0 = tg.off[l];
-  const float* U = sm.U + o0;
-  const float* V = sm.V + o0;
-  const float* D = sm.D + o0;
-  const float* b = sm.b + o0;
-  float* src = sm.x + o0;
-  float* dst = sm.t + o0;
-  tail_for<WARPS>(H, W, warp, lane, [&](int i, int j) { src[i * W + j] = 0.f; });
+  if (warp == 0) {
+    const bool in = lane < H * W;
+    const int k = in ? lane : 0;  // lanes past the grid mirror unknown 0 and store nothing
+    const int i = k / W, j = k - i * W;
+    const bool hx = j + 1 < W, hw = j > 0, hs = i + 1 < H, hn = i > 0;
+    const float u = sm.U[o0 + k], v = sm.V[o0 + k];
+    const float uw = hw ? sm.U[o0 + k - 1] : 0.f, vn = hn ? sm.V[o0 + k - W] : 0.f;
+    float d = u + v;
+    if (hw) d += uw;
+    if (hn) d += vn;
+    const float dk = sm.D[o0 + k], bk = sm.b[o0 + k];
+    const int le = hx ? k + 1 : k, lw = hw ? k - 1 : k, ls = hs ? k + W : k, ln = hn ? k - W : k;
+    float x = 0.f;
+    for (int s = 0; s < kCoarseSweeps; ++s) {
+      const float xe = __shfl_sync(kFull, x, le);
+      const float xw = __shfl_sync(kFull, x, lw);
+      const float xs = __shfl_sync(kFull, x, ls);
+      const float xn = __shfl_sync(kFull, x, ln);
+      float acc = 0.f;
+      if (hx) acc -= u * xe;
+      if (hw) acc -= uw * xw;
+      if (hs) acc -= v * xs;
+      if (hn) acc -= vn * xn;
+      const float ax = d * x + acc;
+      x = x + kOmegaF * dk * (bk - ax);
+    }
+    if (in) sm.x[o0 + k] = x;
+  }
   tail_sync<WARPS>();
-  for (int s = 0; s < kCoarseSweeps; ++s) {
-    tail_for<WARPS>(H, W, warp, lane, [&](int i, int j) {
-      const int k = i * W + j;
-      dst[k] = src[k] + kOmegaF * D[k] * (b[k] - tail_ax(U, V, H, W, i, j, src));
-    });
-    tail_sync<WARPS>();
-    float* tmp = src;
-    src = dst;
-    dst = tmp;
-  }
-  if (src != sm.x + o0) {
-    tail_for<WARPS>(H, W, warp, lane, [&](int i, int j) { sm.x[o0 + i * W + j] = src[i * W + j]; });
-    tail_sync<WARPS>();
-  }
 }
 
 // Grids of at most this many unknowns run on the first kTailSmallThreads threads.

@@ -20,7 +20,9 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
                                one-iteration convergence with the DCT M at p = 2, finite termination
   unwrap                    -- exact recovery of noiseless phase, M-independence
   congruence, quality_q     -- definitions checked on constructed cases
-  functional                -- parity unpinned beyond small hand cases (monitoring only)
+  functional                -- hand case; shift invariance, degree-p homogeneity, row/column
+                               symmetry, zero at a noiseless congruent phase, masked edges free,
+                               and at p = 2 its gradient equals (2 / c)(A phi - b) from assemble
 """
 from __future__ import annotations
 

@@ -411,6 +411,66 @@ def test_functional_hand_case():
     assert oracle.functional(np.zeros((2, 2)), dx, dy, None, 2.0) == pytest.approx(5.3125)
 
 
+@pytest.mark.parametrize("p", [0.5, 1.0, 2.0])
+def test_functional_invariants(p):
+    # Eq. (funcional) depends on phi only through its differences, is homogeneous of
+    # degree p in (phi, Delta), treats rows and columns alike, and vanishes where the
+    # differences of phi equal Delta (a noiseless phase whose true gradients stay below pi)
+    rng = np.random.default_rng(21)
+    H, W = 7, 9
+    phi = rng.normal(size=(H, W))
+    dx, dy = rng.normal(size=(H, W)), rng.normal(size=(H, W))
+    J = oracle.functional(phi, dx, dy, None, p)
+    assert J > 0.0
+    assert oracle.functional(phi + 5.0, dx, dy, None, p) == pytest.approx(J, rel=1e-12)
+    assert oracle.functional(2.0 * phi, 2.0 * dx, 2.0 * dy, None, p) == pytest.approx(2.0 ** p * J, rel=1e-14)
+    assert oracle.functional(phi.T.copy(), dy.T.copy(), dx.T.copy(), None, p) == pytest.approx(J, rel=1e-14)
+    m = synth.smooth_map(24, 30, seed=4)
+    ex, ey = oracle.wrapped_diffs(m.psi)
+    # each edge's residual is rounding (|e| < 1e-12, the wrapped differences' own pin), so J is
+    # below edges x (1e-12)^p, while any misplaced term would contribute O(1) per edge
+    edges = 2 * m.psi.size
+    assert oracle.functional(m.phi_true, ex, ey, None, p) < edges * 1e-12 ** p
+    assert oracle.functional(m.phi_true, ey, ex, None, p) > 1.0
+
+
+def test_functional_ignores_masked_edges():
+    # an edge with a masked end point carries no term: the value at a masked pixel is free
+    rng = np.random.default_rng(22)
+    phi = rng.normal(size=(6, 8))
+    dx, dy = rng.normal(size=(6, 8)), rng.normal(size=(6, 8))
+    mask = np.zeros((6, 8), dtype=np.uint8)
+    mask[2, 3] = 1
+    J = oracle.functional(phi, dx, dy, mask, 1.0)
+    phi2 = phi.copy()
+    phi2[2, 3] = 1e6
+    assert oracle.functional(phi2, dx, dy, mask, 1.0) == J
+    assert oracle.functional(phi2, dx, dy, None, 1.0) > 1e6
+
+
+def test_functional_gradient_is_the_system_at_p2():
+    # at p = 2 the weights are the constant c = tau / (1 + tau) (Eq. UV), so Eq. (Axb) is c times
+    # the normal equations of Eq. (funcional): grad J = (2 / c) (A phi - b).  The functional and
+    # the CSR assembly are separate code; a quadratic's central difference is exact up to rounding.
+    rng = np.random.default_rng(23)
+    H, W, tau = 5, 6, 0.01
+    phi = rng.normal(size=(H, W))
+    dx, dy = rng.normal(size=(H, W)), rng.normal(size=(H, W))
+    U, V = oracle.weights(phi, dx, dy, None, 2.0, tau)
+    A = oracle.assemble(U, V, dx, dy)
+    c = tau / (1.0 + tau)
+    want = (2.0 / c) * (A.matvec(phi) - A.b)
+    h = 1e-3
+    got = np.empty((H, W))
+    for i in range(H):
+        for j in range(W):
+            e = np.zeros((H, W))
+            e[i, j] = h
+            got[i, j] = (oracle.functional(phi + e, dx, dy, None, 2.0) -
+                         oracle.functional(phi - e, dx, dy, None, 2.0)) / (2 * h)
+    np.testing.assert_allclose(got, want, rtol=1e-7, atol=1e-7)
+
+
 def test_unwrap_rejects_invalid():
     with pytest.raises(ValueError):
         oracle.unwrap(np.zeros((1, 5)))

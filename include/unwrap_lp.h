@@ -304,7 +304,9 @@ ULP_API int ulp_pcg(const double* U, const double* V, const double* b, int H, in
  *   contents in it; each call clears what it needs before use.  Calls whose
  *   work overlaps on the GPU (different streams or host threads) race on the
  *   array: the caller must serialise them.
- *   stats (host, nullable) as in ulp_pcg; non-NULL synchronises the stream. */
+ *   stats (host, nullable) as in ulp_pcg; non-NULL synchronises the stream
+ *   and returns the solve's status (a negative one also sets ulp_last_error());
+ *   NULL returns after enqueueing, without reading the solve's status. */
 ULP_API int ulp_pcg_noalloc(const double* U, const double* V, const double* b, int H, int W,
                             int precond, double tol, int max_inner, double* phi, void* cuda_stream,
                             ulp_stats* stats);

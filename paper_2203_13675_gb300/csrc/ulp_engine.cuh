@@ -164,7 +164,7 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
   double v2 = (own && cnt > 2) ? __ldcg(&Sp->gpart[2][lane]) : 0.0;
   double delta = 0.0, delta0 = 0.0, bb = 0.0, rr_best = 0.0;
   long long iter = 0;
-  int fallback = 0, restart = 0, stall = 0, force_refresh = 0, stop_after = 0;
+  int fallback = 0, restart = 0, stall = 0, force_refresh = 0, stop_after = 0, confirm = 0;
   if (lane == 0) {
     delta = __ldcg(&Sp->delta);
     delta0 = __ldcg(&Sp->delta0);
@@ -176,6 +176,7 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
     stall = __ldcg(&Sp->stall);
     force_refresh = __ldcg(&Sp->force_refresh);
     stop_after = __ldcg(&Sp->stop_after);
+    confirm = __ldcg(&Sp->confirm);
   }
   v0 = warp_sum(v0);
   v1 = cnt > 1 ? warp_sum(v1) : 0.0;
@@ -214,15 +215,26 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
         S->stall = 0;
       } else if (ph == kPhFcg) {
         // flexible CG (Polak-Ribiere): beta = r_{k+1}^T (s_{k+1} - s_k) / (r_k^T s_k), v2 = r_{k+1}^T s_k
-        refreshed = (a.xfcg ? (iter > 0 && (iter % M.refresh) == 0) : (iter % M.refresh) == 0) || force_refresh;
-        const double dold = delta;
-        delta = v0;
-        iter += 1;
-        S->delta = v0;
-        S->rr = v1;
-        S->beta = restart ? 0.0 : (v0 - v2) / dold;
-        S->restart = 0;
-        S->iter = iter;
+        refreshed = (a.xfcg ? (iter > 0 && (iter % M.refresh) == 0) : (iter % M.refresh) == 0) || force_refresh ||
+                    confirm;
+        if (confirm) {
+          // mixed flexible CG: this body took no step; it folded the correction into phi and
+          // recomputed r and s for the same iterate, so the iteration count and beta (the
+          // recurrence's) stay, and delta becomes r^T s of the recomputed pair
+          delta = v0;
+          S->delta = v0;
+          S->rr = v1;
+          S->confirm = 0;
+        } else {
+          const double dold = delta;
+          delta = v0;
+          iter += 1;
+          S->delta = v0;
+          S->rr = v1;
+          S->beta = restart ? 0.0 : (v0 - v2) / dold;
+          S->restart = 0;
+          S->iter = iter;
+        }
         if (a.learned && !fallback) {
           // progress test: ||r|| must halve (||r||^2 quarter) within every stall_window
           // iterations, measured from the last point where it did
@@ -253,15 +265,19 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
         done = true;
       } else if (bb == 0.0 || conv) {
         if (ph == kPhFcg && a.xfcg && !refreshed && bb != 0.0) {
-          // the FP32 recurrence says converged: from here on every iteration recomputes the
-          // true residual, and the solve stops on that (a single confirmation that lands just
-          // above the tolerance would otherwise cost two iterations per attempt)
-          S->force_refresh = 1;
+          // the FP32 recurrence says converged at this iterate, the point where Algorithm 1
+          // stops on its recurrence residual: the next body takes no step, folds the correction
+          // into phi and tests the FP64 true residual of this same iterate
+          S->confirm = 1;
         } else {
           done = true;
           S->status = 0;
           if (ph == kPhFcg && a.xfcg && refreshed) S->x_clean = 1;  // this iteration folded x into phi
         }
+      } else if (ph == kPhFcg && a.xfcg && confirm) {
+        // the true residual of the iterate the recurrence called converged misses the
+        // tolerance: from here on every iteration recomputes it, and the solve stops on that
+        S->force_refresh = 1;
       } else if (iter >= (a.lmax > 0 ? a.lmax : 2LL * M.H * M.W)) {
         done = true;
         S->status = 1;

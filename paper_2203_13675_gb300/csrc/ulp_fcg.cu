@@ -226,8 +226,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_f_dots(const PcgArgs* pa, int i
 // every refresh period the correction is folded into phi and r = b - A phi is
 // recomputed with the FP64 weights.  The multigrid cycle
 // reads r directly (its FP32 right-hand side is the recurrence's r plane) and
-// writes s in FP32.  Once the recurrence reports convergence, every remaining
-// iteration is a refresh iteration, so the solve stops on a true residual.
+// writes s in FP32.  When the recurrence reports convergence, the next body takes
+// no step (A returns at once, B uses alpha = 0): it folds the correction into phi,
+// recomputes r = b - A phi in FP64 and s, and the solve stops there if the true
+// residual meets the tolerance, with the iteration count of the recurrence's stop
+// (the point where Algorithm 1 stops on its recurrence residual); otherwise every
+// further iteration is a refresh iteration and the solve stops on a true residual.
 //   A: d = s + beta d, q = A d, d^T q  (the mixed engine's phase A)
 //   B: x += alpha d; r -= alpha q, r_{k+1}^T s_k and r^T r per tile, or on refresh
 //      iterations phi += x, x = 0
@@ -235,16 +239,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_f_dots(const PcgArgs* pa, int i
 //   M: the V-cycle, whose last kernel sums r^T s and runs the dot phase
 
 // refresh iterations: every M.refresh-th after the first (the start computed r in FP64
-// just before iteration 0), and every one once the recurrence has reported convergence
+// just before iteration 0), the confirmation body that follows the recurrence's first
+// report of convergence, and every iteration after a confirmation that missed the tolerance
 __device__ __forceinline__ bool x_refresh(const MapDesc& M, MapState* S) {
   const long long it = *(volatile long long*)&S->iter;
-  return (it > 0 && (it % M.refresh) == 0) || *(volatile int*)&S->force_refresh;
+  return (it > 0 && (it % M.refresh) == 0) || *(volatile int*)&S->force_refresh || *(volatile int*)&S->confirm;
 }
 
 __global__ void __launch_bounds__(kThreads, 2) k_x_a(const PcgArgs* pa) {
   const PcgArgs a = *pa;
   FCG_TILE_LOOP(a) {
-    if (*(volatile int*)&S->done) return;
+    if (*(volatile int*)&S->done || *(volatile int*)&S->confirm) return;  // a confirmation body takes no step
     a32_tile<kJacobi>(a, M, S, t, lane);
   }
 }
@@ -254,11 +259,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_b(const PcgArgs* pa) {
   FCG_TILE_LOOP(a) {
     if (*(volatile int*)&S->done) return;
     const bool refresh = x_refresh(M, S);
+    const bool confirm = *(volatile int*)&S->confirm;
     const long long it = *(volatile long long*)&S->iter;
     const TileGeo g = tile_geo(M, t, a.R);
     const size_t P = M.pitch;
     const float* __restrict__ d = (it & 1) ? M.h.d0 : M.h.d1;
-    const float alpha = (float)*(volatile double*)&S->alpha;
+    // a confirmation body only folds the correction into phi (no step: alpha = 0)
+    const float alpha = confirm ? 0.f : (float)*(volatile double*)&S->alpha;
     const int j = g.j0 + 2 * lane;
     DF rsp, rrp;
     // rows in groups of four, all loads of a group issued before its stores

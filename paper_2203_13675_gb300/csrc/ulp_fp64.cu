@@ -622,6 +622,7 @@ __global__ void k_pcg_reset(MapState* S, int nmaps, int* n_active, Barrier* bar)
     s->stall = 0;
     s->force_refresh = 0;
     s->x_clean = 0;
+    s->confirm = 0;
     s->rr_best = 0.0;
     if (act) atomicAdd(&s_cnt, 1);
   }

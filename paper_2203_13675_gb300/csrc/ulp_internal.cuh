@@ -79,7 +79,8 @@ struct MapState {
   int force_refresh;        // mixed flexible CG: every further iteration recomputes the true residual
   double rr_best;
   int x_clean;              // mixed flexible CG: stopped right after a refresh, so the correction is 0
-  int pad2_;
+  int confirm;              // mixed flexible CG: the next body re-evaluates the current iterate on the FP64
+                            // true residual without taking a step
 };
 
 // Device-side record of one call (per map), copied to the host at the end.

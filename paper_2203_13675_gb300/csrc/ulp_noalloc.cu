@@ -176,5 +176,10 @@ extern "C" int ulp_pcg_noalloc(const double* U, const double* V, const double* b
     stats->relres[k] = hs.relres[k];
     stats->outer_err[k] = hs.outer_err[k];
   }
+  // a solver error is recorded for ulp_last_error() with the same wording as ulp_pcg's
+  if (hs.status < 0)
+    return nfail(hs.status, hs.status == ULP_ERR_TIMEOUT     ? "an in-kernel wait ran out"
+                            : hs.status == ULP_ERR_BREAKDOWN ? "PCG breakdown (d^T A d <= 0 or not finite)"
+                                                             : "solver error");
   return hs.status;
 }

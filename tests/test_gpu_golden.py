@@ -10,7 +10,7 @@ dot-product blocking moves the stop point by at most that much); M = I within
 iterations their counts are not fixed to +-2 by FP64 arithmetic -- for M = I
 see test_gpu_fp64.py; for the sweeps the wavefront rounds each application
 slightly differently from the sequential sweep (2568 against 2561 on the
-2048^2 map); multigrid within 3 (the GPU cycle runs in FP32).
+2048^2 map); multigrid within 2.
 """
 import json
 import os
@@ -31,8 +31,6 @@ def _bar(precond, n):
         return max(2, int(0.01 * n))
     if precond in ("ilu0", "ic0", "ssor"):
         return max(2, int(0.005 * n))
-    if precond == "mg":
-        return 3
     return 2
 
 
@@ -59,16 +57,12 @@ def test_full_size_run_matches_the_oracle(key):
 
 # The bench's chosen form -- the mixed-precision multigrid flexible CG (FP32 weights,
 # recurrence and V-cycle, FP64 inner products and true residual) -- replayed at full size
-# against every multigrid run the oracle recorded: per pass within -3..+4 of the oracle's
-# FP64 counts (FP32 rounding of the cycle and the recurrence, and one more iteration
-# where the stop seen on the recurrence is confirmed on the true residual).  Its phase is
-# the solution of the system with FP32-rounded weights, reached along an FP32 path and
-# stopped at relative residual tol like the oracle's: two such solutions lie anywhere
-# within the set the tolerance allows (the plain and multigrid FP64 solutions of the
-# 2048^2 map, both exact to their oracle runs, are 0.011 rad apart), so the distance to
-# the oracle is measured and reported (about 2e-4 rad RMS on the C2 maps) and held
-# under 1e-3 rad; test_gpu_mg.py checks that the returned phi meets tol on the FP64
-# operator.
+# against every multigrid run the oracle recorded: per pass within 2 of the oracle's FP64
+# counts, and the phase within 1e-4 rad RMS.  The solve stops at the iterate where its
+# FP32 recurrence reports convergence once that iterate's FP64 true residual meets the
+# tolerance, as Algorithm 1 stops on its recurrence residual; the stop point is what
+# decides the distance here (one more multigrid iteration moves the C2 1024^2 solution
+# by 1.5e-4 rad RMS, while rounding the weights to FP32 moves it by 1e-10 rad).
 @pytest.mark.parametrize("key", sorted(k for k in GOLD if GOLD[k]["precond"] == "mg"))
 def test_full_size_mixed_multigrid_matches_the_oracle(key):
     g = GOLD[key]
@@ -81,7 +75,7 @@ def test_full_size_mixed_multigrid_matches_the_oracle(key):
     assert st["status"] == 0, st
     assert st["outer"] == g["stats"]["outer"], (st["inner"], g["stats"]["inner"])
     for a, b in zip(st["inner"], g["stats"]["inner"]):
-        assert -3 <= a - b <= 4, (st["inner"], g["stats"]["inner"])
+        assert abs(a - b) <= 2, (st["inner"], g["stats"]["inner"])
     got = phi.cpu().numpy()
     keep = np.ones(got.shape, bool) if m.mask is None else (m.mask == 0)
     mean = got[keep].mean()
@@ -90,4 +84,4 @@ def test_full_size_mixed_multigrid_matches_the_oracle(key):
     rms = float(np.sqrt(np.mean(e ** 2)))
     print(f"{key}: mixed multigrid vs the FP64 oracle, {rms:.2e} rad RMS at 256 pixels; inner {st['inner']} "
           f"vs {g['stats']['inner']}")
-    assert rms < 1e-3, rms
+    assert rms < 1e-4, rms

@@ -6,7 +6,7 @@ One application matches to FP32 rounding: the cycle is about 10 grids of a
 few sweeps each, so the bar is 2e-5 relative in the 2-norm.  With a fixed M,
 flexible CG (Polak-Ribiere beta) and PCG (Fletcher-Reeves beta) are the same
 iteration in exact arithmetic; an M that differs from the oracle's by FP32
-rounding moves the stop point by at most a few iterations: counts within 3,
+rounding moves the stop point by at most two iterations: counts within 2,
 solutions within the 1e-4 rad RMS bar.
 """
 import numpy as np
@@ -61,7 +61,7 @@ def test_mg_fcg_unwrap_vs_oracle(H, W, p, mask_frac):
     assert st["status"] == 0, st
     assert _rms(phi.cpu().numpy(), ref, keep) < 1e-4
     for a, b in zip(st["inner"], rst["inner"]):
-        assert abs(a - b) <= 3, (st["inner"], rst["inner"])
+        assert abs(a - b) <= 2, (st["inner"], rst["inner"])
 
 
 def test_mg_pcg_step_entry_point():
@@ -73,15 +73,15 @@ def test_mg_pcg_step_entry_point():
     phi = torch.zeros((H, W), dtype=torch.float64, device="cuda")
     _, st = native.ulp_pcg(_cuda(U), _cuda(V), _cuda(A.b), phi, precond="mg", tol=1e-8)
     ref, rst = oracle.pcg(A, np.zeros((H, W)), kind=oracle.M_MG, tol=1e-8)
-    assert abs(st["inner"][0] - rst["iters"]) <= 3, (st, rst)
+    assert abs(st["inner"][0] - rst["iters"]) <= 2, (st, rst)
     assert _rms(phi.cpu().numpy(), ref) < 1e-6
 
 
 # Mixed flexible CG with the multigrid cycle: FP32 recurrence and V-cycle, FP64
 # inner products, phi and true residual.  Its iterates follow the FP64 solve to
-# FP32 rounding, and a stop seen on the FP32 recurrence costs one more iteration
-# to confirm on the true residual, so each pass may take up to 3 + 1 iterations
-# more or 3 fewer than the oracle; the solution meets the same 1e-4 rad bar.
+# FP32 rounding, and a stop seen on the FP32 recurrence is confirmed on the true
+# residual of the same iterate without another step, so each pass takes the
+# oracle's count within 2; the solution meets the same 1e-4 rad bar.
 @pytest.mark.parametrize("H,W,p,mask_frac", [(128, 128, 1.0, 0.05), (200, 129, 0.0, 0.05), (96, 256, 2.0, 0.0),
                                              (256, 256, 0.5, 0.0), (40, 50, 1.0, 0.0)])
 def test_mixed_mg_fcg_unwrap_vs_oracle(H, W, p, mask_frac):
@@ -95,7 +95,7 @@ def test_mixed_mg_fcg_unwrap_vs_oracle(H, W, p, mask_frac):
     assert st["status"] == 0, st
     assert _rms(phi.cpu().numpy(), ref, keep) < 1e-4
     for a, b in zip(st["inner"], rst["inner"]):
-        assert -3 <= a - b <= 4, (st["inner"], rst["inner"])
+        assert abs(a - b) <= 2, (st["inner"], rst["inner"])
 
 
 @pytest.mark.parametrize("H,W", [(160, 96), (33, 70)])
@@ -119,7 +119,7 @@ def test_mixed_mg_pcg_true_residual(H, W, tol):
     assert res <= tol * (1 + 1e-3), res
     if tol >= 1e-6:
         _, rst = oracle.pcg(A, np.zeros((H, W)), kind=oracle.M_MG, tol=tol)
-        assert -3 <= st["inner"][0] - rst["iters"] <= 4, (st, rst)
+        assert abs(st["inner"][0] - rst["iters"]) <= 2, (st, rst)
 
 
 @pytest.mark.parametrize("precision", ["f64", "mixed"])
@@ -127,8 +127,7 @@ def test_mg_walkers_on_odd_sizes_vs_oracle(precision):
     """A 1001 x 999 map with a masked disk takes the row-walker kernels on its own grid
     (odd in both dimensions: a ragged last 120-column window and last band, partial row
     copies at column W - 1) and the tile kernels below.  FP64 form: counts within 3 and
-    1e-4 rad RMS against the oracle's multigrid PCG; mixed form: counts -3..+4 and within
-    the 1e-3 rad the full-size replays allow (test_gpu_golden.py)."""
+    1e-4 rad RMS against the oracle's multigrid PCG, in both forms."""
     H, W = 1001, 999
     m = synth.phase_map(H, W, 31, ramp=0.02, n_bumps=12, noise=0.5, mask_frac=0.05, sigma_range=(10.0, 40.0))
     mixed = precision == "mixed"
@@ -137,6 +136,6 @@ def test_mg_walkers_on_odd_sizes_vs_oracle(precision):
     ref, rst = oracle.unwrap(m.psi, m.mask, p=1.0, kind=oracle.M_MG, tol=1e-6, max_outer=2)
     assert st["status"] == 0, st
     rms = _rms(phi.cpu().numpy(), ref, m.mask == 0)
-    assert rms < (1e-3 if mixed else 1e-4), rms
+    assert rms < 1e-4, rms
     for a, b in zip(st["inner"], rst["inner"]):
-        assert (-3 <= a - b <= 4) if mixed else abs(a - b) <= 3, (st["inner"], rst["inner"])
+        assert abs(a - b) <= 2, (st["inner"], rst["inner"])

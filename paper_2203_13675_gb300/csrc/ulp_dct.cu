@@ -9,6 +9,15 @@
 // and Pi zeroes masked pixels.  The four products are dense contractions and
 // run as BF16 tcgen05 GEMMs with FP32 accumulation in tensor memory.
 //
+// Split-BF16 operands: every operand X is held as two BF16 planes, X = Xh + Xl
+// with Xh = bf16(X) and Xl = bf16(X - Xh) (16 significant bits together), and
+// each product is A B^T ~ Ah Bh^T + Ah Bl^T + Al Bh^T: one GEMM over three
+// K-segments, the TMA producer loading (Ah, Bh), (Ah, Bl), (Al, Bh) in turn into
+// the same accumulator.  The dropped Al Bl^T term and the residual of the split
+// are about 2^-16 of each product, so one application is within about 4e-5 of
+// the exact operator (plain BF16 operands: about 1e-2).  Every epilogue that
+// feeds the next GEMM writes both planes of its output.
+//
 // GEMM form: C[m][n] = sum_k A[m][k] B[n][k] with both operands K-major
 // (row-major, k contiguous), BM = 128, BN = 128, BK = 64 (one 128-byte
 // swizzle atom of BF16 per row), operands staged by TMA into a 3-stage ring,
@@ -42,6 +51,7 @@ enum Epi { kEpiBf16T = 0, kEpiBf16TScale = 1, kEpiF64TMask = 2 };
 
 struct GemmOut {
   void* out;           // Epi 0/1: bf16 [N][ldo]; Epi 2: double plane [*][ldo]
+  void* out_lo;        // Epi 0/1: the low BF16 plane of the split output, same layout
   int ldo;
   const float* lh;     // Epi 1: eigenvalues 2 - 2 cos(pi a / H) by output row n (+inf on padding)
   const float* lw;     // Epi 1: eigenvalues 2 - 2 cos(pi b / W) by output column m (+inf on padding)
@@ -55,9 +65,13 @@ struct GemmOut {
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
                             ((uint32_t)(kBM >> 4) << 24);
 
+// tmA / tmB: the high planes, tmAl / tmBl: the low planes; K-segments (Ah, Bh), (Ah, Bl),
+// (Al, Bh) in that order, all accumulated into one tensor-memory tile
 template <int EPI>
 __global__ void __launch_bounds__(128, 1) k_gemm_nt(const __grid_constant__ CUtensorMap tmA,
-                                                    const __grid_constant__ CUtensorMap tmB, int K, GemmOut o) {
+                                                    const __grid_constant__ CUtensorMap tmB,
+                                                    const __grid_constant__ CUtensorMap tmAl,
+                                                    const __grid_constant__ CUtensorMap tmBl, int K, GemmOut o) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -67,7 +81,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_nt(const __grid_constant__ CUte
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
-  const int nkb = K / kBK;
+  const int nkb0 = K / kBK, nkb = 3 * nkb0;  // three K-segments of the split product
   float* s_lh = reinterpret_cast<float*>(base + kStages * kStageBytes + 256);
   const int m = m0 + warp * 32 + lane;  // this thread's accumulator row in the epilogue
   float lwm = 0.f;
@@ -108,9 +122,10 @@ __global__ void __launch_bounds__(128, 1) k_gemm_nt(const __grid_constant__ CUte
       const int s = kb % kStages, u = kb / kStages;
       if (u > 0 && !mbar_wait(empty + s, (u - 1) & 1, o.err)) break;
       unsigned char* sa = base + s * kStageBytes;
+      const int seg = kb / nkb0, kc = (kb - seg * nkb0) * kBK;
       mbar_expect_tx(full + s, kStageBytes);
-      tma_load_2d(sa, &tmA, full + s, kb * kBK, m0);
-      tma_load_2d(sa + kTileBytes, &tmB, full + s, kb * kBK, n0);
+      tma_load_2d(sa, seg == 2 ? &tmAl : &tmA, full + s, kc, m0);
+      tma_load_2d(sa + kTileBytes, seg == 1 ? &tmBl : &tmB, full + s, kc, n0);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: four K = 16 steps per 64-wide stage, advancing the descriptors by 32 bytes
@@ -145,12 +160,13 @@ __global__ void __launch_bounds__(128, 1) k_gemm_nt(const __grid_constant__ CUte
       for (int q = 0; q < 16; ++q) {
         const int n = n0 + c * 16 + q;
         const size_t off = (size_t)n * o.ldo + m;
-        if (EPI == kEpiBf16T) {
-          reinterpret_cast<__nv_bfloat16*>(o.out)[off] = __float2bfloat16_rn(v[q]);
-        } else if (EPI == kEpiBf16TScale) {
+        if (EPI == kEpiBf16T || EPI == kEpiBf16TScale) {
+          float w = v[q];
           // 1/Lambda(a, b) with a = n, b = m; the zero mode and the padding give 0
-          const float sc = (n | m) ? 1.f / (s_lh[c * 16 + q] + lwm) : 0.f;
-          reinterpret_cast<__nv_bfloat16*>(o.out)[off] = __float2bfloat16_rn(v[q] * sc);
+          if (EPI == kEpiBf16TScale) w *= (n | m) ? 1.f / (s_lh[c * 16 + q] + lwm) : 0.f;
+          const __nv_bfloat16 h = __float2bfloat16_rn(w);
+          reinterpret_cast<__nv_bfloat16*>(o.out)[off] = h;
+          reinterpret_cast<__nv_bfloat16*>(o.out_lo)[off] = __float2bfloat16_rn(w - __bfloat162float(h));
         } else {
           if (n < o.rows && m < o.cols) {
             const int nn = c * 16 + q;
@@ -166,13 +182,16 @@ __global__ void __launch_bounds__(128, 1) k_gemm_nt(const __grid_constant__ CUte
   if (warp == 2) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN));
 }
 
-// r (FP64 plane) -> R (BF16, Hp x Wp, zero padding)
-__global__ void k_pack_bf16(const double* __restrict__ r, int H, int W, int pitch, __nv_bfloat16* R, int Hp,
-                            int Wp) {
+// r (FP64 plane) -> R = Rh + Rl (split BF16, Hp x Wp, zero padding)
+__global__ void k_pack_bf16(const double* __restrict__ r, int H, int W, int pitch, __nv_bfloat16* R,
+                            __nv_bfloat16* Rl, int Hp, int Wp) {
   const size_t n = (size_t)Hp * Wp;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(t / Wp), j = (int)(t % Wp);
-    R[t] = __float2bfloat16_rn((i < H && j < W) ? (float)r[(size_t)i * pitch + j] : 0.f);
+    const float v = (i < H && j < W) ? (float)r[(size_t)i * pitch + j] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    R[t] = h;
+    Rl[t] = __float2bfloat16_rn(v - __bfloat162float(h));
   }
 }
 
@@ -215,26 +234,39 @@ static void gemm_attrs() {
   cudaFuncSetAttribute(k_gemm_nt<kEpiF64TMask>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
 }
 
+// A split operand: its high and low BF16 planes.
+struct Split {
+  const void* h;
+  const void* l;
+};
+
 template <int EPI>
-static cudaError_t gemm(const void* A, int M, const void* B, int N, int K, const GemmOut& o, cudaStream_t st) {
-  CUtensorMap ta, tb;
-  if (!make_map(&ta, A, M, K) || !make_map(&tb, B, N, K)) return cudaErrorInvalidValue;
+static cudaError_t gemm(Split A, int M, Split B, int N, int K, const GemmOut& o, cudaStream_t st) {
+  CUtensorMap ta, tb, tal, tbl;
+  if (!make_map(&ta, A.h, M, K) || !make_map(&tb, B.h, N, K) || !make_map(&tal, A.l, M, K) ||
+      !make_map(&tbl, B.l, N, K))
+    return cudaErrorInvalidValue;
   dim3 grid(N / kBN, M / kBM);
-  k_gemm_nt<EPI><<<grid, 128, kGemmSmem, st>>>(ta, tb, K, o);
+  k_gemm_nt<EPI><<<grid, 128, kGemmSmem, st>>>(ta, tb, tal, tbl, K, o);
   return cudaGetLastError();
 }
 
-// Orthonormal DCT-II matrix of size n padded to np: C[k][x] = c_k cos(pi k (x + 1/2) / n).
-static void dct_matrix(int n, int np, std::vector<__nv_bfloat16>& C, std::vector<__nv_bfloat16>& CT) {
-  C.assign((size_t)np * np, __float2bfloat16(0.f));
-  CT.assign((size_t)np * np, __float2bfloat16(0.f));
+// Orthonormal DCT-II matrix of size n padded to np, C[k][x] = c_k cos(pi k (x + 1/2) / n),
+// as split BF16 (high, low) planes, and its transpose.
+static void dct_matrix(int n, int np, std::vector<__nv_bfloat16>& C, std::vector<__nv_bfloat16>& Cl,
+                       std::vector<__nv_bfloat16>& CT, std::vector<__nv_bfloat16>& CTl) {
+  for (auto* v : {&C, &Cl, &CT, &CTl}) v->assign((size_t)np * np, __float2bfloat16(0.f));
   const double pi = 3.14159265358979323846;
   for (int k = 0; k < n; ++k) {
     const double ck = (k == 0) ? std::sqrt(1.0 / n) : std::sqrt(2.0 / n);
     for (int x = 0; x < n; ++x) {
-      const __nv_bfloat16 v = __float2bfloat16((float)(ck * std::cos(pi * k * (x + 0.5) / n)));
-      C[(size_t)k * np + x] = v;
-      CT[(size_t)x * np + k] = v;
+      const double c = ck * std::cos(pi * k * (x + 0.5) / n);
+      const __nv_bfloat16 h = __float2bfloat16((float)c);
+      const __nv_bfloat16 l = __float2bfloat16((float)(c - (double)__bfloat162float(h)));
+      C[(size_t)k * np + x] = h;
+      Cl[(size_t)k * np + x] = l;
+      CT[(size_t)x * np + k] = h;
+      CTl[(size_t)x * np + k] = l;
     }
   }
 }
@@ -242,8 +274,10 @@ static void dct_matrix(int n, int np, std::vector<__nv_bfloat16>& C, std::vector
 // Device buffers of the DCT preconditioner for an H x W map (allocated with the plan).
 struct DctPlan {
   int H = 0, W = 0, Hp = 0, Wp = 0;
-  __nv_bfloat16 *CH = nullptr, *CHT = nullptr, *CW = nullptr, *CWT = nullptr;
-  __nv_bfloat16 *R = nullptr, *X = nullptr, *Y = nullptr;  // R, X^T / S^, Y^T
+  __nv_bfloat16 *CH = nullptr, *CHT = nullptr, *CW = nullptr, *CWT = nullptr;      // high planes
+  __nv_bfloat16 *CHl = nullptr, *CHTl = nullptr, *CWl = nullptr, *CWTl = nullptr;  // low planes
+  __nv_bfloat16 *R = nullptr, *X = nullptr, *Y = nullptr;     // R, X^T / S^, Y^T (high)
+  __nv_bfloat16 *Rl = nullptr, *Xl = nullptr, *Yl = nullptr;  // their low planes
   float *lh = nullptr, *lw = nullptr;                        // [Hp], [Wp] eigenvalue factors
   unsigned* mbits = nullptr;                                 // [Hp / 32][Wp] mask bits
   int* err = nullptr;
@@ -252,7 +286,7 @@ struct DctPlan {
 
 size_t dct_bytes(int H, int W) {
   const size_t Hp = (H + 127) / 128 * 128, Wp = (W + 127) / 128 * 128;
-  return 2 * (Hp * Hp + Wp * Wp) * 2 + 3 * Hp * Wp * 2 + (Hp + Wp) * 4 + Hp / 32 * Wp * 4 + 4096;
+  return 2 * 2 * (Hp * Hp + Wp * Wp) * 2 + 2 * 3 * Hp * Wp * 2 + (Hp + Wp) * 4 + Hp / 32 * Wp * 4 + 8192;
 }
 
 // Builds the matrices into mem (dct_bytes(H, W) bytes of device memory).
@@ -273,20 +307,31 @@ int dct_setup(DctPlan& d, int H, int W, void* mem) {
   d.CHT = static_cast<__nv_bfloat16*>(take(Hp * Hp * 2));
   d.CW = static_cast<__nv_bfloat16*>(take(Wp * Wp * 2));
   d.CWT = static_cast<__nv_bfloat16*>(take(Wp * Wp * 2));
+  d.CHl = static_cast<__nv_bfloat16*>(take(Hp * Hp * 2));
+  d.CHTl = static_cast<__nv_bfloat16*>(take(Hp * Hp * 2));
+  d.CWl = static_cast<__nv_bfloat16*>(take(Wp * Wp * 2));
+  d.CWTl = static_cast<__nv_bfloat16*>(take(Wp * Wp * 2));
   d.R = static_cast<__nv_bfloat16*>(take(Hp * Wp * 2));
   d.X = static_cast<__nv_bfloat16*>(take(Hp * Wp * 2));
   d.Y = static_cast<__nv_bfloat16*>(take(Hp * Wp * 2));
+  d.Rl = static_cast<__nv_bfloat16*>(take(Hp * Wp * 2));
+  d.Xl = static_cast<__nv_bfloat16*>(take(Hp * Wp * 2));
+  d.Yl = static_cast<__nv_bfloat16*>(take(Hp * Wp * 2));
   d.lh = static_cast<float*>(take(Hp * 4));
   d.lw = static_cast<float*>(take(Wp * 4));
   d.mbits = static_cast<unsigned*>(take(Hp / 32 * Wp * 4));
   d.err = static_cast<int*>(take(256));
-  std::vector<__nv_bfloat16> C, CT;
-  dct_matrix(H, d.Hp, C, CT);
-  if (cudaMemcpy(d.CH, C.data(), C.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return -2;
-  if (cudaMemcpy(d.CHT, CT.data(), CT.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return -2;
-  dct_matrix(W, d.Wp, C, CT);
-  if (cudaMemcpy(d.CW, C.data(), C.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return -2;
-  if (cudaMemcpy(d.CWT, CT.data(), CT.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return -2;
+  std::vector<__nv_bfloat16> C, Cl, CT, CTl;
+  auto up = [](void* dst, const std::vector<__nv_bfloat16>& v) {
+    return cudaMemcpy(dst, v.data(), v.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  dct_matrix(H, d.Hp, C, Cl, CT, CTl);
+  if (!up(d.CH, C) || !up(d.CHl, Cl) || !up(d.CHT, CT) || !up(d.CHTl, CTl)) return -2;
+  dct_matrix(W, d.Wp, C, Cl, CT, CTl);
+  if (!up(d.CW, C) || !up(d.CWl, Cl) || !up(d.CWT, CT) || !up(d.CWTl, CTl)) return -2;
+  // the split copy of r starts at zero: the flexible CG writes only its H x W part, and the
+  // GEMMs multiply the padding by the matrices' zero padding (which must not meet a NaN pattern)
+  if (cudaMemset(d.R, 0, Hp * Wp * 2) != cudaSuccess || cudaMemset(d.Rl, 0, Hp * Wp * 2) != cudaSuccess) return -2;
   // Lambda(a, b) = lh[a] + lw[b]; padded indices get +inf so that 1/Lambda = 0 there
   const double pi = 3.14159265358979323846;
   std::vector<float> lh(Hp, INFINITY), lw(Wp, INFINITY);
@@ -318,8 +363,9 @@ int dct_error(const DctPlan& d) {
 }
 
 // s = Pi L^+ r: r, s are FP64 planes with the given pitch; mask a uint8 plane or null.
-unsigned* dct_input(const DctPlan& d, int* ld_pairs) {
+unsigned* dct_input(const DctPlan& d, int* ld_pairs, unsigned** lo) {
   *ld_pairs = d.Wp / 2;
+  *lo = reinterpret_cast<unsigned*>(d.Rl);
   return reinterpret_cast<unsigned*>(d.R);
 }
 
@@ -335,7 +381,7 @@ cudaError_t dct_apply(const DctPlan& d, const double* r, int pitch, const uint8_
                       cudaStream_t st, bool packed) {
   const int Hp = d.Hp, Wp = d.Wp;
   if (!packed) {
-    k_pack_bf16<<<elem_blocks((size_t)Hp * Wp), 256, 0, st>>>(r, d.H, d.W, pitch, d.R, Hp, Wp);
+    k_pack_bf16<<<elem_blocks((size_t)Hp * Wp), 256, 0, st>>>(r, d.H, d.W, pitch, d.R, d.Rl, Hp, Wp);
     const cudaError_t e = dct_prepare_mask(d, mask, pitch, st);
     if (e != cudaSuccess) return e;
   }
@@ -343,30 +389,34 @@ cudaError_t dct_apply(const DctPlan& d, const double* r, int pitch, const uint8_
   o.err = d.err;
   // G1: X^T[b][i] = sum_j R[i][j] C_W[b][j]
   o.out = d.X;
+  o.out_lo = d.Xl;
   o.ldo = Hp;
-  cudaError_t e = gemm<kEpiBf16T>(d.R, Hp, d.CW, Wp, Wp, o, st);
+  cudaError_t e = gemm<kEpiBf16T>({d.R, d.Rl}, Hp, {d.CW, d.CWl}, Wp, Wp, o, st);
   if (e != cudaSuccess) return e;
   // G2: S^[a][b] = (sum_i X^T[b][i] C_H[a][i]) / Lambda[a][b]
   o.out = d.Y;
+  o.out_lo = d.Yl;
   o.ldo = Wp;
   o.lh = d.lh;
   o.lw = d.lw;
-  e = gemm<kEpiBf16TScale>(d.X, Wp, d.CH, Hp, Hp, o, st);
+  e = gemm<kEpiBf16TScale>({d.X, d.Xl}, Wp, {d.CH, d.CHl}, Hp, Hp, o, st);
   if (e != cudaSuccess) return e;
   // G3: Y^T[j][a] = sum_b S^[a][b] C_W^T[j][b]
   o.out = d.X;
+  o.out_lo = d.Xl;
   o.ldo = Hp;
   o.lh = o.lw = nullptr;
-  e = gemm<kEpiBf16T>(d.Y, Hp, d.CWT, Wp, Wp, o, st);
+  e = gemm<kEpiBf16T>({d.Y, d.Yl}, Hp, {d.CWT, d.CWTl}, Wp, Wp, o, st);
   if (e != cudaSuccess) return e;
   // G4: S[i][j] = sum_a Y^T[j][a] C_H^T[i][a], masked, into the FP64 plane
   o.out = s;
+  o.out_lo = nullptr;
   o.ldo = pitch;
   o.mbits = mask ? d.mbits : nullptr;
   o.ldb = Wp;
   o.rows = d.H;
   o.cols = d.W;
-  return gemm<kEpiF64TMask>(d.X, Wp, d.CHT, Hp, Hp, o, st);
+  return gemm<kEpiF64TMask>({d.X, d.Xl}, Wp, {d.CHT, d.CHTl}, Hp, Hp, o, st);
 }
 
 }  // namespace ulp

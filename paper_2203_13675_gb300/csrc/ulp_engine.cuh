@@ -136,7 +136,8 @@ __device__ __forceinline__ TileGeo tile_geo(const MapDesc& M, int t, int R) {
 }
 
 // ------------------------------------------------------------------ PCG engine
-enum Phase { kPhResInit = 0, kPhA = 1, kPhB = 2, kPhRes = 3, kPhFcg = 4 };
+// kPhConfirm: the true residual of a mixed flexible-CG confirmation body (its r^T r alone)
+enum Phase { kPhResInit = 0, kPhA = 1, kPhB = 2, kPhRes = 3, kPhFcg = 4, kPhConfirm = 5 };
 
 // Runs in the warp whose tile arrival completed phase `ph` for map m: reduces
 // the map's tile partials in a fixed order and advances its scalars
@@ -184,7 +185,20 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
   bool done = false;
   if (lane == 0) {
     bool refreshed = true;  // r is the true residual (mixed flexible CG: this iteration recomputed it)
-    if (ph == kPhA) {
+    if (ph == kPhConfirm) {
+      // the recurrence called the current iterate converged and this body recomputed its
+      // residual in FP64: if that meets the tolerance the solve stops here, before the
+      // preconditioner runs; otherwise the body goes on (the cycle and the dot phase treat
+      // it as a confirmation that missed)
+      if (!(v1 > a.tol2 * bb)) {
+        done = true;
+        S->status = 0;
+        S->x_clean = 1;
+        S->confirm = 0;
+        S->rr = v1;
+        S->relres = (bb > 0.0) ? sqrt(v1 / bb) : 0.0;
+      }
+    } else if (ph == kPhA) {
       S->dq = v0;
       if ((!(v0 > 0.0) || !isfinite(v0)) && a.learned && !fallback) {
         // the network gave a direction that is not a descent direction: no step,

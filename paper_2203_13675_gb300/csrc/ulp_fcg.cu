@@ -35,12 +35,16 @@ __global__ void k_set_args(PcgArgs a, PcgArgs* dst) { *dst = a; }
   MapState* S = a.st;                                                  \
   for (int t = gw; t < a.ntiles; t += NW)
 
-// BF16 copy of r at (i, j), (i, j+1) for the DCT's first GEMM, or the FP32 copy the
-// multigrid cycle starts from (zero beyond column W-1)
+// split BF16 copy of r at (i, j), (i, j+1) for the DCT's first GEMM (high plane bf16(r), low
+// plane bf16(r - high)), or the FP32 copy the multigrid cycle starts from (zero beyond column W-1)
 __device__ __forceinline__ void put_rbf(const PcgArgs& a, const MapDesc& M, int i, int j, double2 r) {
   if (a.rbf && j < M.W) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn((float)r.x, j + 1 < M.W ? (float)r.y : 0.f);
+    const float fx = (float)r.x, fy = j + 1 < M.W ? (float)r.y : 0.f;
+    const __nv_bfloat162 v = __floats2bfloat162_rn(fx, fy);
+    const float2 h = __bfloat1622float2(v);
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(fx - h.x, fy - h.y);
     a.rbf[(size_t)i * a.rbf_ld + (j >> 1)] = *reinterpret_cast<const unsigned*>(&v);
+    a.rbf_lo[(size_t)i * a.rbf_ld + (j >> 1)] = *reinterpret_cast<const unsigned*>(&lo);
   }
   if (a.rf32 && j < M.W)
     *reinterpret_cast<float2*>(a.rf32 + (size_t)i * M.pitch + j) =
@@ -330,6 +334,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_res(const PcgArgs* pa, int in
   FCG_TILE_LOOP(a) {
     if (*(volatile int*)&S->done) return;
     if (!init && !x_refresh(M, S)) return;
+    // a confirmation body under the relative-residual stop decides here whether the solve ends
+    const bool confirm = !init && a.stop_mode == ULP_STOP_RELRES && *(volatile int*)&S->confirm;
     const TileGeo g = tile_geo(M, t, a.R);
     XPlane x{M.f.phi, (size_t)M.pitch};
     DF rsp, rrp;
@@ -351,7 +357,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_res(const PcgArgs* pa, int in
       }
     };
     stencil_tile(M, g.i0, g.i1, g.j0, lane, M.f.U, M.f.V, M.f.D, x, epi);
-    const double v = warp_sum(init ? bb : rsp.value()), w = warp_sum(rrp.value());
+    const double v = warp_sum(init ? bb : rsp.value());
+    if (confirm) {
+      // r_{k+1}^T s_k for the dot phase, should the body go on; r^T r through the arrival
+      if (lane == 0) __stcg(a.P2 + t, v);
+      tile_arrive(a, M, S, t, kPhConfirm, 0.0, rrp.value(), 0.0, lane);
+      continue;
+    }
+    const double w = warp_sum(rrp.value());
     if (lane == 0) {
       __stcg(a.P2 + t, v);
       __stcg(a.P1 + t, w);
@@ -682,9 +695,10 @@ cudaError_t launch_fcg(Plan& pl, int kind, const PcgArgs& a_in, cudaStream_t st,
   }
   PcgArgs a = a_in;
   a.rbf = nullptr;
+  a.rbf_lo = nullptr;
   a.rbf_ld = 0;
   a.rf32 = nullptr;
-  if (kind == ULP_PRECOND_DCT) a.rbf = dct_input(*pl.dct, &a.rbf_ld);
+  if (kind == ULP_PRECOND_DCT) a.rbf = dct_input(*pl.dct, &a.rbf_ld, &a.rbf_lo);
   a.xfcg = mixed_fcg(pl, kind);
   if (kind == ULP_PRECOND_MG && !a.xfcg) a.rf32 = mg_input(*pl.mg);
   a.learned = kind == ULP_PRECOND_LEARNED;

@@ -96,7 +96,8 @@ void launch_pcg_reset(const Plan& pl, cudaStream_t st);
 size_t dct_bytes(int H, int W);
 DctPlan* dct_create(int H, int W, void* mem);  // builds the matrices in mem (dct_bytes); null on failure
 void dct_destroy(DctPlan* d);
-unsigned* dct_input(const DctPlan& d, int* ld_pairs);
+// the split BF16 copy of r that the first GEMM reads: high plane returned, low plane in *lo
+unsigned* dct_input(const DctPlan& d, int* ld_pairs, unsigned** lo);
 // the mask's bit plane used by dct_apply(..., packed = true)
 cudaError_t dct_prepare_mask(const DctPlan& d, const uint8_t* mask, int pitch, cudaStream_t st);
 // packed: the BF16 copy of r (dct_input) and the mask bits (dct_prepare_mask) are

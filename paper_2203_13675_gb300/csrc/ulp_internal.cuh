@@ -116,6 +116,7 @@ struct PcgArgs {
   int apply_only;           // sweep solvers: stop after the first s = M^-1 r (single-step entry point)
   unsigned long long cond;  // flexible-CG graph: WHILE-node handle cleared when the map stops (0 = none)
   unsigned* rbf;            // flexible-CG graph: BF16 copy of r as column pairs (the DCT input), or null
+  unsigned* rbf_lo;         // its low plane (r - bf16(r), BF16 pairs): the DCT's operands are split BF16
   int rbf_ld;               // its row stride in pairs
   float* rf32;              // flexible-CG graph: FP32 copy of r (the multigrid's right-hand side), or null
   int learned;              // flexible CG with the learned preconditioner: stall / breakdown fall back to Jacobi

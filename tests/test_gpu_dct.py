@@ -1,10 +1,12 @@
-"""DCT Poisson preconditioner (tcgen05 BF16 GEMMs, FP32 accumulation) against the oracle's
-FP64 explicit-cosine apply.
+"""DCT Poisson preconditioner (tcgen05 GEMMs on split-BF16 operands, FP32 accumulation)
+against the oracle's FP64 explicit-cosine apply.
 
-BF16 operands (8-bit mantissa) put one application within a few percent of the
-exact pseudo-inverse (about 1-4 % in a CPU emulation of the same rounding);
-the bar is 6 % relative in the 2-norm.  The solver uses it inside flexible CG,
-which tolerates such an inexact M.
+Each operand is the sum of two BF16 planes (16 significant bits) and each product
+keeps three of the four cross terms, so one application is within about 4e-5 of
+the exact pseudo-inverse in the 2-norm (3.9e-5 in a CPU emulation of the same
+rounding on the 200 x 129 case; plain BF16 operands gave 1.2e-2); the bar is
+1e-4.  The solver uses it inside flexible CG, whose iteration counts then follow
+the oracle's exact-M PCG within 2 (the emulation: 97 and 148 against 96 and 147).
 """
 import numpy as np
 import pytest
@@ -31,13 +33,13 @@ def test_dct_apply_vs_oracle(H, W, mask_frac):
     mk = _cuda(m.mask, torch.uint8) if m.mask is not None else None
     got = native.ulp_precond_apply("dct", _cuda(U), _cuda(V), _cuda(r), mask=mk).cpu().numpy()
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    assert err < 0.06, err
+    assert err < 1e-4, err
     if m.mask is not None:
         assert np.all(got[m.mask == 1] == 0.0)
 
 
 def test_dct_apply_inverts_the_laplacian_on_smooth_input():
-    # a single low-frequency cosine mode is an eigenvector: s = r / lambda exactly (to BF16)
+    # a single low-frequency cosine mode is an eigenvector: s = r / lambda (to the split's rounding)
     H, W = 128, 256
     i = np.arange(H)[:, None]
     j = np.arange(W)[None, :]
@@ -46,7 +48,7 @@ def test_dct_apply_inverts_the_laplacian_on_smooth_input():
     z = np.zeros((H, W))
     got = native.ulp_precond_apply("dct", _cuda(z), _cuda(z), _cuda(r)).cpu().numpy()
     err = np.linalg.norm(got - r / lam) / np.linalg.norm(r / lam)
-    assert err < 0.02, err
+    assert err < 1e-4, err
 
 
 def _rms(a, b, keep=None):
@@ -59,10 +61,8 @@ def _rms(a, b, keep=None):
 
 @pytest.mark.parametrize("H,W,p,mask_frac", [(128, 128, 1.0, 0.05), (200, 129, 0.0, 0.05), (96, 256, 2.0, 0.0)])
 def test_dct_fcg_unwrap_vs_oracle(H, W, p, mask_frac):
-    # the GPU runs flexible CG with a BF16 tensor-core M; the oracle standard PCG with the exact
-    # FP64 M: same solution (1e-4 rad RMS), iteration counts within 15 % + 5: a BF16 M is 1-4 %
-    # off the exact pseudo-inverse, so where the exact M needs 1 iteration (p = 2, no mask) the
-    # inexact one needs a handful
+    # the GPU runs flexible CG with the split-BF16 tensor-core M; the oracle standard PCG with the
+    # exact FP64 M: same solution (1e-4 rad RMS), iteration counts within 2
     m = synth.phase_map(H, W, 21, ramp=0.02, n_bumps=12, noise=0.5, mask_frac=mask_frac,
                         sigma_range=(5.0, 20.0))
     plan = native.Plan(H, W, outer_tol=0.0)
@@ -73,16 +73,16 @@ def test_dct_fcg_unwrap_vs_oracle(H, W, p, mask_frac):
     assert st["status"] == 0, st
     assert _rms(phi.cpu().numpy(), ref, keep) < 1e-4
     for a, b in zip(st["inner"], rst["inner"]):
-        assert abs(a - b) <= 5 + int(0.15 * b), (st["inner"], rst["inner"])
+        assert abs(a - b) <= 2, (st["inner"], rst["inner"])
 
 
 def test_dct_fcg_p2_unmasked_few_iterations():
-    # p = 2 without a mask: A = c L and M^-1 A is a projector; exact M converges in one
-    # iteration, the BF16 M in a handful
+    # p = 2 without a mask: A = c L and M^-1 A is a projector; the exact M converges in one
+    # iteration, the split-BF16 one (4e-5 off) in at most three
     m = synth.phase_map(128, 192, 8, noise=0.4)
     plan = native.Plan(128, 192, outer_tol=0.0)
     phi, st = plan.unwrap(_cuda(m.psi), None, p=2.0, precond="dct", tol=1e-6, max_outer=1, max_inner=200)
-    assert st["status"] == 0 and st["inner"][0] <= 6, st
+    assert st["status"] == 0 and st["inner"][0] <= 3, st
 
 
 @pytest.mark.slow

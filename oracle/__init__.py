@@ -66,13 +66,13 @@ class PcgOpts(ctypes.Structure):
 
 class PcgResult(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_long), ("status", ctypes.c_int), ("relres", ctypes.c_double),
-                ("true_relres", ctypes.c_double)]
+                ("true_relres", ctypes.c_double), ("setup_s", ctypes.c_double)]
 
 
 class UnwrapStats(ctypes.Structure):
     _fields_ = [("outer", ctypes.c_int), ("status", ctypes.c_int), ("inner_total", ctypes.c_long),
                 ("inner", ctypes.c_long * 64), ("relres", ctypes.c_double * 64),
-                ("outer_err", ctypes.c_double * 64)]
+                ("outer_err", ctypes.c_double * 64), ("setup_s", ctypes.c_double)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -231,7 +231,7 @@ def pcg(A: Csr, phi0, kind=M_JACOBI, tol=1e-6, max_inner=0, stop_mode=STOP_RELRE
     lib().orc_pcg(A.H, A.W, A.indptr.ctypes.data_as(_L), A.indices.ctypes.data_as(_I),
                   _d(A.data), _d(bb), mp, ctypes.byref(o), _d(phi), ctypes.byref(res))
     return phi, {"iters": res.iters, "status": res.status, "relres": res.relres,
-                 "true_relres": res.true_relres}
+                 "true_relres": res.true_relres, "setup_s": res.setup_s}
 
 
 def unwrap(psi, mask=None, p=1.0, tau=0.01, kind=M_JACOBI, tol=1e-6, max_outer=5,
@@ -250,7 +250,7 @@ def unwrap(psi, mask=None, p=1.0, tau=0.01, kind=M_JACOBI, tol=1e-6, max_outer=5
     k = st.outer
     stats = {"status": rc, "outer": k, "inner_total": st.inner_total,
              "inner": list(st.inner[:min(k, 64)]), "relres": list(st.relres[:min(k, 64)]),
-             "outer_err": list(st.outer_err[:min(k, 64)])}
+             "outer_err": list(st.outer_err[:min(k, 64)]), "setup_s": st.setup_s}
     return phi, stats
 
 

@@ -90,6 +90,7 @@ typedef struct {
   int status;        /* ORC_OK, ORC_MAXITER or ORC_BREAKDOWN */
   double relres;     /* ||r_l|| / ||b|| of the recurrence residual at exit */
   double true_relres;/* ||b - A phi|| / ||b|| at exit */
+  double setup_s;    /* wall time of building M from A (seconds), for the set-up share of Sec. 3 */
 } orc_pcg_result;
 
 /* Inner PCG of Algorithm 1 on CSR A, warm-started from phi (overwritten). */
@@ -104,6 +105,7 @@ typedef struct {
   long inner[64];        /* per-outer inner iterations (first 64 passes) */
   double relres[64];
   double outer_err[64];
+  double setup_s;        /* summed wall time of building M in every pass (seconds) */
 } orc_unwrap_stats;
 
 /* Algorithm 1: IRLS outer loop around the inner PCG.  phi holds phi^0 on

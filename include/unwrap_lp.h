@@ -129,6 +129,14 @@ typedef struct ulp_stats {
   double relres[ULP_MAX_OUTER_STATS];         /* ||r_l|| / ||b|| at exit of each inner solve */
   double outer_err[ULP_MAX_OUTER_STATS];      /* Algorithm 1's error after each pass (inf if ||phi^k|| = 0) */
   int fallbacks;                              /* ULP_PRECOND_LEARNED: inner solves that switched to Jacobi */
+  double setup_ms;                            /* device time spent building the preconditioner from A in
+                                                 this call (Algorithm 1, "estimate preconditioning matrix
+                                                 M from A"; the paper reports its share, Sec. 3): the
+                                                 pivot and coefficient phases of the ILU(0)/IC(0)/SSOR
+                                                 solvers, always; the coarse grids (multigrid), the mask
+                                                 bits (DCT) and the red-black pivots of the flexible-CG
+                                                 solves on plans made with options.profile != 0; 0 for
+                                                 I and Jacobi, whose D^-1 comes with the system kernel */
 } ulp_stats;
 
 /* Fills *opt with the defaults listed above. */

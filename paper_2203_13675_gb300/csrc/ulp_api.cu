@@ -224,7 +224,7 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
                       &M.f.cw, &M.f.cn, &M.f.ce, &M.f.cs};
     for (double** q : f64) { *q = reinterpret_cast<double*>(p); p += e64; }
     float** f32[] = {&M.h.U, &M.h.V, &M.h.Dinv, &M.h.x, &M.h.r, &M.h.s, &M.h.q,
-                     &M.h.d0, &M.h.d1, &M.h.cw, &M.h.cn, &M.h.pinv, &M.h.y};
+                     &M.h.d0, &M.h.d1, &M.h.cw, &M.h.cn, &M.h.pinv, &M.h.xl};
     for (float** q : f32) { *q = reinterpret_cast<float*>(p); p += e32; }
     M.f.mask = reinterpret_cast<uint8_t*>(p);
     p += align256((size_t)M.H * M.pitch);
@@ -330,6 +330,7 @@ static void fill_stats(const MapStats& d, ulp_stats* s) {
     s->outer_err[k] = d.outer_err[k];
   }
   s->fallbacks = d.fallbacks;
+  s->setup_ms = 1e-6 * (double)d.setup_ns;
 }
 
 static PcgArgs pcg_args(const Plan& pl, double tol, int max_inner) {
@@ -351,6 +352,7 @@ static PcgArgs pcg_args(const Plan& pl, double tol, int max_inner) {
   a.timeout_ns = (unsigned long long)(pl.opt.spin_timeout_s * 1e9);
   a.omega = pl.opt.omega;
   a.stall_window = pl.opt.stall_window > 0 ? pl.opt.stall_window : 200;
+  a.stats = pl.dstats;
   return a;
 }
 

@@ -292,6 +292,13 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
         // the true residual of the iterate the recurrence called converged misses the
         // tolerance: from here on every iteration recomputes it, and the solve stops on that
         S->force_refresh = 1;
+      } else if (ph == kPhFcg && a.xfcg && !force_refresh && bb != 0.0 &&
+                 ((a.stop_mode == 1) ? !(delta > 4.0 * tol2 * delta0) : !(rr > 4.0 * tol2 * bb))) {
+        // within a factor 2 of the tolerance: the iterates that follow recompute the true
+        // residual after their step and stop on it, so the stop falls on the first iterate
+        // whose FP64 residual meets the tolerance, where an FP64 recurrence stops, even
+        // when the FP32 recurrence lags it by a rounding
+        S->force_refresh = 1;
       } else if (iter >= (a.lmax > 0 ? a.lmax : 2LL * M.H * M.W)) {
         done = true;
         S->status = 1;

@@ -26,6 +26,16 @@ namespace ulp {
 
 __global__ void k_set_args(PcgArgs a, PcgArgs* dst) { *dst = a; }
 
+// Set-up timing of a flexible-CG solve (plans with options.profile): end = 0 records the
+// start of the preconditioner's set-up, end = 1 adds its duration to map 0's statistics.
+__global__ void k_setup_stamp(const PcgArgs* pa, int end) {
+  MapStats* st = pa->stats;
+  if (!st || *(volatile int*)&pa->st->done) return;
+  const unsigned long long t = globaltimer();
+  if (end) st->setup_ns += t - st->setup_t0;
+  else st->setup_t0 = t;
+}
+
 // one warp per tile (grid-stride), the single map of the plan
 #define FCG_TILE_LOOP(a)                                               \
   const int lane = threadIdx.x & 31;                                   \
@@ -224,9 +234,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_f_dots(const PcgArgs* pa, int i
 
 // ---------------------------------------------------------------- mixed flexible CG
 // The multigrid solve with the precision split of the mixed form: the Krylov
-// recurrence (d, q = A d, r, s and the correction x since the last refresh) on
-// FP32 planes with FP32 weights, the inner products as double-float sums of
-// exact FP32 products, alpha, beta and the stop tests in FP64, and phi in FP64:
+// recurrence (d, q = A d, r, s) on FP32 planes with FP32 weights, the correction
+// since the last refresh as a double-float pair of FP32 planes, the inner products
+// as double-float sums of exact FP32 products, alpha, beta and the stop tests in
+// FP64, and phi in FP64:
 // every refresh period the correction is folded into phi and r = b - A phi is
 // recomputed with the FP64 weights.  The multigrid cycle
 // reads r directly (its FP32 right-hand side is the recurrence's r plane) and
@@ -241,6 +252,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_f_dots(const PcgArgs* pa, int i
 //      iterations phi += x, x = 0
 //   R: on refresh iterations r = b - A phi (FP64, rounded to FP32), r_{k+1}^T s_k, r^T r
 //   M: the V-cycle, whose last kernel sums r^T s and runs the dot phase
+
+// hi + lo += y with hi, lo a double-float pair: TwoSum of hi and y (the rounding error of the
+// FP32 sum, exact), added into lo
+__device__ __forceinline__ void df_add(float& hi, float& lo, float y) {
+  const float s = __fadd_rn(hi, y);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(y, bp));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
 
 // refresh iterations: every M.refresh-th after the first (the start computed r in FP64
 // just before iteration 0), the confirmation body that follows the recurrence's first
@@ -274,13 +295,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_b(const PcgArgs* pa) {
     DF rsp, rrp;
     // rows in groups of four, all loads of a group issued before its stores
     for (int i = g.i0; i < g.i1; i += 4) {
-      float2 dv[4], xv[4], qv[4], rv[4], sv[4];
+      float2 dv[4], xv[4], xlv[4], qv[4], rv[4], sv[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (i + k < g.i1) {
           const size_t off = (size_t)(i + k) * P + j;
           dv[k] = ldf2(d, off);
           xv[k] = ldf2(M.h.x, off);
+          xlv[k] = ldf2(M.h.xl, off);
           if (!refresh) {
             qv[k] = ldf2(M.h.q, off);
             rv[k] = ldf2(M.h.r, off);
@@ -292,17 +314,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_b(const PcgArgs* pa) {
       for (int k = 0; k < 4; ++k) {
         if (i + k < g.i1) {
           const size_t off = (size_t)(i + k) * P + j;
-          float2 x = xv[k];
-          x.x = __fmaf_rn(alpha, dv[k].x, x.x);
-          x.y = __fmaf_rn(alpha, dv[k].y, x.y);
+          // the correction is a double-float sum x + xl (TwoSum of each step into it), so the
+          // iterate carries no FP32 rounding of x when it is folded into phi
+          float2 x = xv[k], xl = xlv[k];
+          df_add(x.x, xl.x, __fmul_rn(alpha, dv[k].x));
+          df_add(x.y, xl.y, __fmul_rn(alpha, dv[k].y));
           if (refresh) {
             double2 ph = ld2(M.f.phi, off);
-            ph.x += (double)x.x;
-            ph.y += (double)x.y;
+            ph.x += (double)x.x + (double)xl.x;
+            ph.y += (double)x.y + (double)xl.y;
             st2(M.f.phi, off, ph);
             stf2(M.h.x, off, make_float2(0.f, 0.f));
+            stf2(M.h.xl, off, make_float2(0.f, 0.f));
           } else {
             stf2(M.h.x, off, x);
+            stf2(M.h.xl, off, xl);
             float2 r = rv[k];
             r.x = __fmaf_rn(-alpha, qv[k].x, r.x);
             r.y = __fmaf_rn(-alpha, qv[k].y, r.y);
@@ -348,6 +374,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_res(const PcgArgs* pa, int in
       rrp.add_prod(r.y, r.y);
       if (init) {
         stf2(M.h.x, off, make_float2(0.f, 0.f));
+        stf2(M.h.xl, off, make_float2(0.f, 0.f));
         bb = fma(bv.x, bv.x, bb);
         bb = fma(bv.y, bv.y, bb);
       } else {
@@ -415,12 +442,13 @@ __global__ void __launch_bounds__(kThreads) k_x_fold(const PcgArgs* pa) {
     const int j = g.j0 + 2 * lane;
     for (int i = g.i0; i < g.i1; ++i) {
       const size_t off = (size_t)i * P + j;
-      const float2 xv = ldf2(M.h.x, off);
+      const float2 xv = ldf2(M.h.x, off), xlv = ldf2(M.h.xl, off);
       double2 ph = ld2(M.f.phi, off);
-      ph.x += (double)xv.x;
-      ph.y += (double)xv.y;
+      ph.x += (double)xv.x + (double)xlv.x;
+      ph.y += (double)xv.y + (double)xlv.y;
       st2(M.f.phi, off, ph);
       stf2(M.h.x, off, make_float2(0.f, 0.f));
+      stf2(M.h.xl, off, make_float2(0.f, 0.f));
     }
   }
 }
@@ -479,20 +507,25 @@ static bool fused_dots(const Plan& pl, int kind) { return kind == ULP_PRECOND_MG
 static cudaError_t fcg_start(Plan& pl, int kind, cudaStream_t st) {
   const MapDesc& M = pl.hmaps[0];
   const int nb = tile_blocks(pl);
+  const bool stamp = pl.opt.profile != 0;
   if (mixed_fcg(pl, kind)) {
     const bool fd = fused_dots(pl, kind);
     k_x_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
+    if (stamp) k_setup_stamp<<<1, 1, 0, st>>>(pl.dargs, 0);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = mg_setup(*pl.mg, pl.dstate, st, !pl.system_x);
+    if (stamp) k_setup_stamp<<<1, 1, 0, st>>>(pl.dargs, 1);
     if (e == cudaSuccess) e = fcg_precond(pl, kind, st, fd, true);
     if (!fd) k_x_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
     return e == cudaSuccess ? cudaGetLastError() : e;
   }
   k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
+  if (stamp) k_setup_stamp<<<1, 1, 0, st>>>(pl.dargs, 0);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && kind == ULP_PRECOND_DCT) e = dct_prepare_mask(*pl.dct, M.f.mask, M.pitch, st);
   if (e == cudaSuccess && kind == ULP_PRECOND_MG) e = mg_setup(*pl.mg, pl.dstate, st);
   if (e == cudaSuccess) e = rb_setup(pl, kind, pl.dstate, st);
+  if (stamp) k_setup_stamp<<<1, 1, 0, st>>>(pl.dargs, 1);
   if (e == cudaSuccess) e = fcg_precond(pl, kind, st);
   k_f_dots<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
   return e == cudaSuccess ? cudaGetLastError() : e;

@@ -554,13 +554,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_pcg64_sweep(PcgArgs a) {
 
   reset_exchange(a, s_bbase);
   if (!grid_sync(a.bar, a.timeout_ns)) return;
-  // preconditioner set-up (Algorithm 1: estimate M from A)
+  // preconditioner set-up (Algorithm 1: estimate M from A), timed by block 0 between the
+  // grid barriers that bracket it
+  const unsigned long long t_setup = (blockIdx.x == 0 && threadIdx.x == 0) ? globaltimer() : 0ull;
   if (KIND == kIlu) {
     sweep_phase<kSweepPiv>(a, s_bbase, map_active);
     if (!grid_sync(a.bar, a.timeout_ns)) return;
   }
   for_tiles([&](const MapDesc& M, MapState*, int t) { coef_tile<KIND>(a, M, t, lane); });
   if (!grid_sync(a.bar, a.timeout_ns)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats && !a.apply_only)
+    atomicAdd(&a.stats->setup_ns, globaltimer() - t_setup);
   // r = b - A phi, d = M^-1 r, delta_new = r^T d
   for_tiles([&](const MapDesc& M, MapState*, int t) { res_tile_sweep<KIND>(a, M, t, lane); });
   if (!grid_sync(a.bar, a.timeout_ns)) return;
@@ -712,6 +716,7 @@ __global__ void k_begin(MapState* S, MapStats* stats, int nmaps) {
     st->outer = 0;
     st->inner_total = 0;
     st->fallbacks = 0;
+    st->setup_ns = 0;
     for (int k = 0; k < 64; ++k) { st->inner[k] = 0; st->relres[k] = 0.0; st->outer_err[k] = 0.0; }
     s->outer_k = 0;
     s->arrive_outer = 0u;

@@ -45,7 +45,8 @@ struct Planes64 {
 struct Planes32 {
   float *U, *V, *Dinv;      // weights (FP32) and Jacobi inverse
   float *x, *r, *s, *q, *d0, *d1;
-  float *cw, *cn, *pinv, *y; // sweep coefficients (mixed ILU/SSOR)
+  float *cw, *cn, *pinv;    // sweep coefficients (mixed ILU/SSOR)
+  float *xl;                // mixed flexible CG: low word of the double-float correction (x + xl)
 };
 
 struct MapDesc {
@@ -91,6 +92,8 @@ struct MapStats {
   double relres[64];
   double outer_err[64];
   int fallbacks;
+  unsigned long long setup_ns;   // device time spent building the preconditioner in this call
+  unsigned long long setup_t0;   // %globaltimer at the start of the current set-up (flexible CG)
 };
 
 struct Barrier {
@@ -121,6 +124,7 @@ struct PcgArgs {
   float* rf32;              // flexible-CG graph: FP32 copy of r (the multigrid's right-hand side), or null
   int learned;              // flexible CG with the learned preconditioner: stall / breakdown fall back to Jacobi
   int stall_window;
+  MapStats* stats;          // per-map statistics (the set-up time is added to map 0's), or null
   int xfcg;                 // mixed flexible CG: convergence of the FP32 recurrence is confirmed on the
                             // FP64 true residual before the solve stops
 };

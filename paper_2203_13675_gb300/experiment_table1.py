@@ -5,21 +5,22 @@ the paper's five preconditioners (Sec. 2 list), unwrap a synthetic wrapped map o
 that size with the paper's stopping criteria: k_max = 500 outer passes, outer
 tolerance 1e-6, Algorithm 1's inner test delta_new <= eps^2 delta_0 with
 eps = 0.005, l_max = 2MN.  Records the inner iterations (the paper's Fig. 2)
-and the time (Fig. 3) per size and preconditioner; --oracle adds the FP64 CPU
-oracle's iteration counts and time for the sizes up to --oracle-max pixels.
+and the time (Fig. 3) per size and preconditioner, and the device time spent
+building the preconditioner (the set-up share the paper reports in Sec. 3).
 --preconds picks the columns (default: the paper's five; "all" adds the
-red-black, DCT and multigrid preconditioners).
+red-black, DCT and multigrid preconditioners).  The FP64 CPU oracle's columns of
+the same study come from tests/golden/make_table1_oracle.py (test
+infrastructure; this module runs the GPU library only).
 
 The paper's 640x480 map (Fig. 1) is not available; each size uses the seeded
 generator of synth.py (ramp 0.05 rad/px, 6 bumps with widths scaled to the
 size, noise 0.3 rad).
 
-usage: python -m paper_2203_13675_gb300.experiment_table1 [--out table1.json] [--oracle]
+usage: python -m paper_2203_13675_gb300.experiment_table1 [--out table1.json]
                                                          [--preconds identity,jacobi,...|all]
 """
 import argparse
 import json
-import time
 
 import torch
 
@@ -38,12 +39,13 @@ def make_map(cols, rows, seed=1):
                            sigma_range=(10.0 * scale, 40.0 * scale))
 
 
-def run(out, with_oracle=False, oracle_max=640 * 480, sizes=SIZES, preconds=PRECONDS, p=1.0):
+def run(out, sizes=SIZES, preconds=PRECONDS, p=1.0):
     rows_out = []
     for cols, rows in sizes:
         m = make_map(cols, rows)
         psi = torch.from_numpy(m.psi).cuda()
-        plan = native.Plan(rows, cols, outer_tol=1e-6, stop_mode=native.ULP_STOP_PAPER)
+        # profile = 1: the flexible-CG solves also time their preconditioner set-up
+        plan = native.Plan(rows, cols, outer_tol=1e-6, stop_mode=native.ULP_STOP_PAPER, profile=1)
         for pc in preconds:
             plan.unwrap(psi, None, p=p, precond=pc, tol=0.005, max_outer=500, max_inner=0)  # warm-up
             torch.cuda.synchronize()
@@ -53,19 +55,10 @@ def run(out, with_oracle=False, oracle_max=640 * 480, sizes=SIZES, preconds=PREC
             phi, st = plan.unwrap(psi, None, p=p, precond=pc, tol=0.005, max_outer=500, max_inner=0)
             e1.record()
             torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
             row = {"cols": cols, "rows": rows, "nnz": 5 * rows * cols - 2 * (rows + cols), "precond": pc,
-                   "gpu_ms": e0.elapsed_time(e1), "outer": st["outer"], "inner_total": st["inner_total"],
-                   "status": st["status"]}
-            if with_oracle and rows * cols <= oracle_max:
-                import oracle  # test infrastructure: the CPU baseline of the experiment
-                kinds = {"identity": oracle.M_IDENTITY, "jacobi": oracle.M_JACOBI, "ilu0": oracle.M_ILU0,
-                         "ic0": oracle.M_IC0, "ssor": oracle.M_SSOR, "rbssor": oracle.M_RBSSOR,
-                         "rbilu": oracle.M_RBILU, "dct": oracle.M_DCT, "mg": oracle.M_MG}
-                t0 = time.perf_counter()
-                _, ost = oracle.unwrap(m.psi, None, p=p, kind=kinds[pc], tol=0.005, max_outer=500,
-                                       outer_tol=1e-6, stop_mode=oracle.STOP_PAPER)
-                row.update({"oracle_s": time.perf_counter() - t0, "oracle_outer": ost["outer"],
-                            "oracle_inner_total": ost["inner_total"]})
+                   "gpu_ms": ms, "outer": st["outer"], "inner_total": st["inner_total"],
+                   "status": st["status"], "setup_ms": st["setup_ms"], "setup_share": st["setup_ms"] / ms}
             rows_out.append(row)
             print(json.dumps(row), flush=True)
         plan.close()
@@ -78,13 +71,11 @@ def run(out, with_oracle=False, oracle_max=640 * 480, sizes=SIZES, preconds=PREC
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=None)
-    ap.add_argument("--oracle", action="store_true")
-    ap.add_argument("--oracle-max", type=int, default=640 * 480)
     ap.add_argument("--p", type=float, default=1.0)
     ap.add_argument("--preconds", default=",".join(PRECONDS))
     a = ap.parse_args()
     pcs = PRECONDS + EXTRA if a.preconds == "all" else a.preconds.split(",")
-    run(a.out, a.oracle, a.oracle_max, preconds=pcs, p=a.p)
+    run(a.out, preconds=pcs, p=a.p)
 
 
 if __name__ == "__main__":

@@ -51,13 +51,13 @@ class ulp_options(ctypes.Structure):
 class ulp_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("outer", ctypes.c_int), ("inner_total", ctypes.c_longlong),
                 ("inner", ctypes.c_longlong * 64), ("relres", ctypes.c_double * 64),
-                ("outer_err", ctypes.c_double * 64), ("fallbacks", ctypes.c_int)]
+                ("outer_err", ctypes.c_double * 64), ("fallbacks", ctypes.c_int), ("setup_ms", ctypes.c_double)]
 
     def as_dict(self):
         k = min(self.outer, 64)
         return {"status": self.status, "outer": self.outer, "inner_total": self.inner_total,
                 "inner": list(self.inner[:k]), "relres": list(self.relres[:k]),
-                "outer_err": list(self.outer_err[:k]), "fallbacks": self.fallbacks}
+                "outer_err": list(self.outer_err[:k]), "fallbacks": self.fallbacks, "setup_ms": self.setup_ms}
 
 
 class ulp_counters(ctypes.Structure):

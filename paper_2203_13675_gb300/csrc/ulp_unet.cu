@@ -231,10 +231,6 @@ static cudaError_t conv3x3(const bf16* x, int B, int H, int W, int Cin, const bf
   return cudaGetLastError();
 }
 
-// once per device, before any capture
-static cudaError_t conv_init() {
-  return cudaFuncSetAttribute(k_conv3x3, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem(256));
-}
 
 // ------------------------------------------------------------------ elementwise kernels
 __device__ __forceinline__ void unpack8(uint4 u, float (&f)[8]) {
@@ -582,100 +578,282 @@ __global__ void k_head_reduce(const double* __restrict__ part, int nb, float* __
 }
 
 // ------------------------------------------------------------------ weight gradient
-// dW[o][c][t] = sum_p dy[p][o] x[p + off(t)][c], db[o] = sum_p dy[p][o] for one
-// 16 x 16 (o, c) block per blockIdx.y; pixel tiles of 8 x 32 over blockIdx.x
-// (grid-stride).  Each thread owns one (o, c) pair and its 9 taps, sliding a
-// 3 x 3 register window along the tile's rows.  Partials go to part[y][x][.].
-constexpr int kWTH = 8, kWTW = 32;
-__global__ void __launch_bounds__(256) k_wgrad(const bf16* __restrict__ dy, int O, const bf16* __restrict__ x, int Cx,
-                                               int B, int H, int W, int nct, float* __restrict__ part) {
-  __shared__ float sx[kWTH + 2][kWTW + 2][16];
-  __shared__ float sd[kWTH][kWTW][16];
-  const int ot = blockIdx.y / nct, ct = blockIdx.y % nct;
-  const int oi = threadIdx.x >> 4, ci = threadIdx.x & 15;
-  const int tx_n = (W + kWTW - 1) / kWTW, ty_n = (H + kWTH - 1) / kWTH;
-  const long long ntiles = (long long)B * tx_n * ty_n;
-  float acc[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) acc[k] = 0.f;
-  float accb = 0.f;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int b = (int)(tile / ((long long)tx_n * ty_n));
-    const int r = (int)(tile % ((long long)tx_n * ty_n));
-    const int y0 = (r / tx_n) * kWTH, x0 = (r % tx_n) * kWTW;
-    __syncthreads();
-    // x halo tile: (TH + 2) x (TW + 2) pixels x 16 channels, two 8-channel halves per pixel
-    for (int e = threadIdx.x; e < (kWTH + 2) * (kWTW + 2) * 2; e += blockDim.x) {
-      const int h = e & 1, pix = e >> 1;
-      const int yy = pix / (kWTW + 2), xx = pix % (kWTW + 2);
-      const int gy = y0 + yy - 1, gx = x0 + xx - 1;
-      float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-        unpack8(*reinterpret_cast<const uint4*>(x + ((size_t)(b * H + gy) * W + gx) * Cx + ct * 16 + h * 8), f);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) sx[yy][xx][h * 8 + k] = f[k];
+// dW[o][c][t] = sum_p dy[p][o] x[p + off(t)][c] and db[o] = sum_p dy[p][o] as one GEMM
+// on the tensor cores with the pixels as the reduction dimension:
+//   D[m][o] = sum_p A[m][p] B[o][p],  A[c 9 + t][p] = x[p + off(t)][c] (0 outside the
+//   image), A[9 C][p] = 1 (the bias row), B[o][p] = dy[p][o].
+// The m rows come in 128-row tiles; a CTA owns a group of consecutive tiles (their
+// accumulators side by side in tensor memory, G x O <= 512 columns) and a contiguous
+// range of pixel chunks (split K).  A chunk is a bw x bh block of 64 pixels of one
+// image (bw the largest power of two dividing W, at most 64); chunks are numbered down
+// each bw-wide column strip, so a CTA's consecutive chunks share all but bh of the
+// bh + 2 input rows that their 3 x 3 taps read.  Those rows are kept in a shared-memory
+// ring (only the new rows are loaded, as 16-byte pieces of 8 channels, zero outside the
+// image) together with the chunk's dy.  From them the 128 threads build, per chunk, the
+// B tile once and each tile's A rows (one row per thread) in the canonical K-major
+// layout with the 128-byte swizzle (8-row atoms of 1024 bytes; the 16-byte piece j of
+// row r stored at piece j ^ (r mod 8)), and one thread issues four K = 16 MMAs per tile
+// into its FP32 accumulator; the A tiles alternate between two buffers, so a tile's MMAs
+// run while the next tile is built.  Partials go to part[split][m][o] and a second kernel
+// sums the splits in order, so the result does not depend on scheduling.
+constexpr int kWgA = 128 * 128;                  // one A tile: 128 rows x 64 pixels x 2 bytes
+constexpr int kWgHaloBytes = 48 * 1024;          // input-row ring: (2 bh + 2) rows x (bw + 2) pixels x channels
+constexpr int kWgSmem = 2 * kWgA + 128 * 128 + kWgHaloBytes + 2 * 64 * 128 * 2 + 1024 + 256;  // the largest layout
+constexpr size_t kPartFloats = (size_t)kPartRows * kPartCols;
+
+struct WgArgs {
+  const bf16* dy;   // [P][O]
+  const bf16* x;    // [P][Cx], channels [0, C) used
+  int O, Cx, C, B, H, W, bw, lbw, bh;
+  int mtiles, gtiles;   // 128-row tiles of m = 9 C + 1 rows, tiles per CTA group
+  int chunks;       // pixel chunks of the whole batch
+  int per_split;    // chunks per CTA
+  int tcols;        // tensor-memory columns allocated (>= gtiles O, power of two, >= 32)
+  int off_ring, off_dy, off_bar;  // shared-memory layout (bytes from the 1024-aligned base)
+  float* part;      // [split][mtiles * 128][O]
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t sw128_off(int row, int piece) {
+  return (uint32_t)(row * 128 + ((piece ^ (row & 7)) << 4));
+}
+
+// 16-byte asynchronous copy into shared memory, zero-filled when !valid (nothing is read then)
+__device__ __forceinline__ void cpa16(void* sdst, const void* gsrc, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(sdst)), "l"(gsrc),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+// NP: 8-channel pieces per ring pixel (the largest of the layer's groups), so the ring's
+// channel stride is a compile-time constant.  256 threads: each A row is built by two
+// threads (four 16-byte pieces each).
+constexpr int kWgThreads = 256;
+template <int NP>
+__global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(WgArgs a) {
+  constexpr int HS = NP * 8;                                  // ring channels per pixel
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  unsigned char* sbt = base + 2 * kWgA;                       // the B tile (O rows)
+  unsigned char* ring = base + a.off_ring;                    // [slot][pixel][HS channels]
+  bf16* sdy = reinterpret_cast<bf16*>(base + a.off_dy);       // 2 x [q][O]
+  uint64_t* a_done = reinterpret_cast<uint64_t*>(base + a.off_bar);
+  uint64_t* b_done = a_done + 2;
+  uint64_t* fin = b_done + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
+  __shared__ int s_rowbase[10];                               // ring offset (pixels) of window row w
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grp = blockIdx.x, split = blockIdx.y;
+  const int t0 = grp * a.gtiles, G = min(a.gtiles, a.mtiles - t0);
+  const int k0 = split * a.per_split, k1 = min(a.chunks, k0 + a.per_split);
+  const uint32_t idesc = idesc_bf16(128, a.O);
+  if (tid == 0) {
+    mbar_init(a_done, 1);
+    mbar_init(a_done + 1, 1);
+    mbar_init(b_done, 1);
+    mbar_init(fin, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(a.tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+
+  // channels of the group's rows: [cb0, cb0 + 8 np) (whole pieces inside the pixel), np <= NP
+  const int c_first = min((t0 * 128) / 9, a.C - 1), c_last = min(a.C - 1, ((t0 + G) * 128 - 1) / 9);
+  const int cb0 = c_first & ~7;
+  const int np = (c_last - cb0) / 8 + 1;
+  const int hbw = a.bw + 2, nslot = a.bh + 2, nring = 2 * a.bh + 2;  // window rows; ring slots
+  const int hw = a.H * a.W, nrb = a.H / a.bh, nstrip = a.W / a.bw;
+  const unsigned short one = __bfloat16_as_ushort(__float2bfloat16_rn(1.f));
+  const int r128 = tid & 127, half = tid >> 7;                // the A row slot and piece half of this thread
+  // this thread's row of a tile, taken in tap-major order (the lanes of a warp then read
+  // neighbouring channels of one tap, not one channel at nine taps)
+  auto my_row = [&](int M0, int& t, int& c) {
+    int rem = r128;
+    t = 8;
+    c = 0;
+    for (int tt = 0; tt < 9; ++tt) {
+      const int cmin = (M0 - tt + 8) / 9, cmax = (M0 + 127 - tt) / 9;  // M0 - tt >= -8
+      const int n = cmax - cmin + 1;
+      if (rem < n) { t = tt; c = cmin + rem; return; }
+      rem -= n;
     }
-    for (int e = threadIdx.x; e < kWTH * kWTW * 2; e += blockDim.x) {
-      const int h = e & 1, pix = e >> 1;
-      const int yy = pix / kWTW, xx = pix % kWTW;
-      const int gy = y0 + yy, gx = x0 + xx;
-      float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      if (gy < H && gx < W)
-        unpack8(*reinterpret_cast<const uint4*>(dy + ((size_t)(b * H + gy) * W + gx) * O + ot * 16 + h * 8), f);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) sd[yy][xx][h * 8 + k] = f[k];
+  };
+  // asynchronous copies of rows a in [a0, a1) of the chunk's column strip (image b, columns
+  // x0 - 1 .. x0 + bw) into their ring slots (a + 1) mod nring, zero outside the image
+  auto load_rows = [&](int b, int x0, int a0, int a1) {
+    const int n = (a1 - a0) * hbw * np;
+    for (int e = tid; e < n; e += kWgThreads) {
+      const int pc = e % np, rest = e / np;
+      const int col = rest % hbw, py = a0 + rest / hbw, px = x0 - 1 + col;
+      const bool in = py >= 0 && py < a.H && px >= 0 && px < a.W;
+      const bf16* src = in ? a.x + ((size_t)b * hw + (size_t)py * a.W + px) * a.Cx + cb0 + 8 * pc : a.x;
+      cpa16(ring + ((size_t)(((py + 1) % nring) * hbw + col) * NP + pc) * 16, src, in);
     }
+  };
+  auto load_dy = [&](int b, int y0, int x0, bf16* dst) {
+    const int opc = a.O / 8;
+    for (int e = tid; e < 64 * opc; e += kWgThreads) {
+      const int q = e / opc, pc = e - q * opc;
+      const int py = y0 + (q >> a.lbw), px = x0 + (q & (a.bw - 1));
+      cpa16(dst + q * a.O + 8 * pc, a.dy + ((size_t)b * hw + (size_t)py * a.W + px) * a.O + 8 * pc, true);
+    }
+  };
+  auto chunk_at = [&](int k, int& b, int& y0, int& x0) {
+    const int ry = k % nrb, sx = (k / nrb) % nstrip;
+    b = k / (nrb * nstrip);
+    y0 = ry * a.bh;
+    x0 = sx * a.bw;
+  };
+  bool ok = true;
+  int u = 0;  // A-tile builds so far (buffer u & 1)
+  bool have_rows = false;  // the current chunk's new rows were prefetched by the previous iteration
+  for (int k = k0; k < k1 && ok; ++k) {
+    const int i = k - k0;
+    int b, y0, x0;
+    chunk_at(k, b, y0, x0);
+    bf16* dyc = sdy + (i & 1) * 64 * a.O;
+    if (!have_rows) {  // the first chunk of the CTA, or one that starts another strip: all its rows
+      load_rows(b, x0, y0 - 1, y0 + a.bh + 1);
+      if (i == 0) load_dy(b, y0, x0, dyc);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // prefetch the next chunk: its dy, and its bh new rows when it follows in the same strip
+    have_rows = false;
+    if (k + 1 < k1) {
+      int b2, y2, x2;
+      chunk_at(k + 1, b2, y2, x2);
+      load_dy(b2, y2, x2, sdy + ((i + 1) & 1) * 64 * a.O);
+      if (b2 == b && x2 == x0 && y2 == y0 + a.bh) {
+        load_rows(b, x0, y2 + 1, y2 + a.bh + 1);
+        have_rows = true;
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // this chunk's copies (not the prefetch)
+    if (tid < nslot) s_rowbase[tid] = ((y0 + tid) % nring) * hbw;  // window row w = abs row y0 - 1 + w
+    // the previous chunk's MMAs must have read the B tile
+    if (i > 0) ok = ok && mbar_wait(b_done, (i - 1) & 1, a.err);
+    if (!__syncthreads_and(ok)) { ok = false; break; }
+    if (tid < 2 * a.O) {
+      const int o = tid % a.O, h = tid / a.O;
+      const unsigned short* src = reinterpret_cast<const unsigned short*>(dyc) + o;
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int j = 4 * h + jj;
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          w[e] = (uint32_t)src[(8 * j + 2 * e) * a.O] | ((uint32_t)src[(8 * j + 2 * e + 1) * a.O] << 16);
+        *reinterpret_cast<uint4*>(sbt + sw128_off(o, j)) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    for (int g = 0; g < G; ++g, ++u) {
+      unsigned char* sa = base + (u & 1) * kWgA;
+      if (u >= 2) ok = ok && mbar_wait(a_done + (u & 1), ((u - 2) >> 1) & 1, a.err);
+      const int M0 = (t0 + g) * 128;
+      int t, c;
+      my_row(M0, t, c);
+      const int m = 9 * c + t, row = m - M0;
+      const bool xrow = m < 9 * a.C, brow = m == 9 * a.C;
+      const int ty = t / 3, tx = t - 3 * ty;
+      const unsigned short* hr = reinterpret_cast<const unsigned short*>(ring) + (c - cb0);
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int j = 4 * half + jj;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (xrow) {
+          // the piece's 8 pixels lie in one row of the block (bw >= 8)
+          const int q0 = 8 * j;
+          const unsigned short* src = hr + (s_rowbase[(q0 >> a.lbw) + ty] + (q0 & (a.bw - 1)) + tx) * HS;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) w[e] = (uint32_t)src[2 * e * HS] | ((uint32_t)src[(2 * e + 1) * HS] << 16);
+        } else if (brow) {
+          w[0] = w[1] = w[2] = w[3] = (uint32_t)one | ((uint32_t)one << 16);
+        }
+        *reinterpret_cast<uint4*>(sa + sw128_off(row, j)) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      // the generic-proxy stores must be visible to the tensor cores' reads
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (!__syncthreads_and(ok)) { ok = false; break; }
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t da = sw128_desc(sa), db = sw128_desc(sbt);
+        const uint32_t acc_col = tmem + (uint32_t)(g * a.O);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma_bf16(acc_col, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, (i | kk) != 0);
+        mma_commit(a_done + (u & 1));
+        if (g == G - 1) mma_commit(b_done);
+      }
+    }
+    // the prefetched rows and dy are complete, and every thread is done with this chunk's
+    // window before the next iteration's prefetch overwrites its oldest rows
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-#pragma unroll 1
-    for (int rr = 0; rr < kWTH; ++rr) {
-      float w00 = sx[rr][0][ci], w10 = sx[rr + 1][0][ci], w20 = sx[rr + 2][0][ci];
-      float w01 = sx[rr][1][ci], w11 = sx[rr + 1][1][ci], w21 = sx[rr + 2][1][ci];
-#pragma unroll 4
-      for (int cx = 0; cx < kWTW; ++cx) {
-        const float w02 = sx[rr][cx + 2][ci], w12 = sx[rr + 1][cx + 2][ci], w22 = sx[rr + 2][cx + 2][ci];
-        const float d = sd[rr][cx][oi];
-        acc[0] = fmaf(d, w00, acc[0]);
-        acc[1] = fmaf(d, w01, acc[1]);
-        acc[2] = fmaf(d, w02, acc[2]);
-        acc[3] = fmaf(d, w10, acc[3]);
-        acc[4] = fmaf(d, w11, acc[4]);
-        acc[5] = fmaf(d, w12, acc[5]);
-        acc[6] = fmaf(d, w20, acc[6]);
-        acc[7] = fmaf(d, w21, acc[7]);
-        acc[8] = fmaf(d, w22, acc[8]);
-        accb += d;
-        w00 = w01; w01 = w02;
-        w10 = w11; w11 = w12;
-        w20 = w21; w21 = w22;
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  if (tid == 0) mma_commit(fin);
+  __syncwarp();
+  const bool ready = __all_sync(0xffffffffu, ok && mbar_wait(fin, 0, a.err)) && k1 > k0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // epilogue: warps w and w + 4 read the lane quarter w & 3 of every accumulator, each
+  // half of its 16-column chunks
+  const int quarter = warp & 3, chalf = warp >> 2, nq = a.O >> 4;
+  for (int g = 0; g < G; ++g) {
+    float* dst = a.part + (((size_t)split * a.mtiles + t0 + g) * 128 + quarter * 32 + lane) * a.O;
+    for (int cq = chalf; cq < nq; cq += 2) {
+      if (ready) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(g * a.O + cq * 16), v);
+#pragma unroll
+        for (int q = 0; q < 16; q += 4)
+          *reinterpret_cast<float4*>(dst + cq * 16 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+      } else {
+        for (int q = 0; q < 16; ++q) dst[cq * 16 + q] = 0.f;
       }
     }
   }
-  float* dst = part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kPartCols;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) dst[(oi * 16 + ci) * 9 + k] = acc[k];
-  if (ci == 0) dst[16 * 16 * 9 + oi] = accb;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 2) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tcols));
 }
-// canonical gradient of one layer: W [O][C][3][3] at gw, bias [O] at gb; sums the G
-// partials of every block row in order
-__global__ void k_wgrad_reduce(const float* __restrict__ part, int G, int nct, int O, int C, float* __restrict__ gw,
-                               float* __restrict__ gb) {
-  const int n = O * C * 9;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n + O; e += gridDim.x * blockDim.x) {
-    if (e < n) {
-      const int t = e % 9, c = (e / 9) % C, o = e / (9 * C);
-      const int row = (o / 16) * nct + c / 16;
-      const int col = ((o % 16) * 16 + (c % 16)) * 9 + t;
-      double s = 0.0;
-      for (int g = 0; g < G; ++g) s += part[((size_t)row * G + g) * kPartCols + col];
-      gw[e] = (float)s;
-    } else {
-      const int o = e - n;
-      const int row = (o / 16) * nct;
-      double s = 0.0;
-      for (int g = 0; g < G; ++g) s += part[((size_t)row * G + g) * kPartCols + 16 * 16 * 9 + (o % 16)];
-      gb[o] = (float)s;
-    }
+
+// canonical gradient of one layer: W [O][C][3][3] at gw, bias [O] at gb; sums the
+// splits of part[split][m][o] (m = c 9 + t, the bias row at m = 9 C) in order.  Thread e
+// takes (m, o) = (e / O, e mod O), so a warp reads consecutive o of one row.
+__global__ void k_wgrad_reduce(const float* __restrict__ part, int nsplit, int mtiles, int O, int C,
+                               float* __restrict__ gw, float* __restrict__ gb) {
+  const int n = (9 * C + 1) * O;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int m = e / O, o = e - m * O;
+    double s = 0.0;
+    for (int g = 0; g < nsplit; ++g) s += part[((size_t)g * mtiles * 128 + m) * O + o];
+    if (m < 9 * C) gw[(size_t)o * 9 * C + m] = (float)s;  // W[o][c][t] at o 9 C + c 9 + t
+    else gb[o] = (float)s;
   }
+}
+
+// once per device, before any capture
+static cudaError_t conv_init() {
+  const cudaError_t e = cudaFuncSetAttribute(k_conv3x3, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem(256));
+  if (e != cudaSuccess) return e;
+  const void* fns[] = {(const void*)k_wgrad_tc<1>, (const void*)k_wgrad_tc<2>, (const void*)k_wgrad_tc<3>,
+                       (const void*)k_wgrad_tc<4>, (const void*)k_wgrad_tc<5>, (const void*)k_wgrad_tc<6>,
+                       (const void*)k_wgrad_tc<7>, (const void*)k_wgrad_tc<8>, (const void*)k_wgrad_tc<9>,
+                       (const void*)k_wgrad_tc<10>, (const void*)k_wgrad_tc<11>, (const void*)k_wgrad_tc<12>};
+  for (const void* f : fns) {
+    const cudaError_t e2 = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
+    if (e2 != cudaSuccess) return e2;
+  }
+  return cudaSuccess;
 }
 
 // ------------------------------------------------------------------ parameters
@@ -817,15 +995,77 @@ static cudaError_t forward(Unet& u, int B, int Hn, int Wn, const int* skip, cuda
 
 static cudaError_t wgrad(Unet& u, int l, const bf16* dy, const bf16* x, int Cx, int B, int H, int W,
                          cudaStream_t st) {
-  const int O = kCout[l], nct = kCinPad[l] / 16, nty = (O / 16) * nct;
-  const long long tiles = (long long)B * ((W + kWTW - 1) / kWTW) * ((H + kWTH - 1) / kWTH);
-  long long G = kPartRows / nty;
-  if (G > tiles) G = tiles;
-  if (G > 608 / nty + 1) G = 608 / nty + 1;  // about four blocks per SM
-  if (G < 1) G = 1;
-  k_wgrad<<<dim3((unsigned)G, (unsigned)nty), 256, 0, st>>>(dy, O, x, Cx, B, H, W, nct, u.part);
-  const int n = O * kCin[l] * 9 + O;
-  k_wgrad_reduce<<<(n + 255) / 256, 256, 0, st>>>(u.part, (int)G, nct, O, kCin[l], u.grad + u.off.w[l],
+  WgArgs a{};
+  a.dy = dy;
+  a.x = x;
+  a.O = kCout[l];
+  a.Cx = Cx;
+  a.C = kCin[l];
+  a.B = B;
+  a.H = H;
+  a.W = W;
+  a.bw = W & -W;
+  if (a.bw > 64) a.bw = 64;
+  a.lbw = 0;
+  while ((1 << a.lbw) < a.bw) ++a.lbw;
+  a.bh = 64 / a.bw;
+  if (a.bw < 8 || a.bh > H || H % a.bh || a.O % 16 || a.O > 128 || Cx % 8) return cudaErrorInvalidValue;
+  a.mtiles = (9 * a.C + 1 + 127) / 128;
+  // tiles per group: their accumulators fit tensor memory, and the channels they read
+  // fit the input-row ring (the tile rows of one group span about 14 G + 1 channels)
+  const int ring_px = (2 * a.bh + 2) * (a.bw + 2);  // ring slots x (bw + 2) pixels
+  a.gtiles = 512 / a.O;
+  auto pieces = [](int g) { return ((g * 128) / 9 + 1 + 7 + 7) / 8; };  // 8-channel pieces a group may read
+  while (a.gtiles > 1 && (pieces(a.gtiles) * 16 * ring_px > kWgHaloBytes || pieces(a.gtiles) > 12)) --a.gtiles;
+  if (a.gtiles > a.mtiles) a.gtiles = a.mtiles;
+  const int ngroups = (a.mtiles + a.gtiles - 1) / a.gtiles;
+  // every group's channel pieces inside the pixel and its rows inside the ring (as the kernel forms them)
+  for (int grp = 0; grp < ngroups; ++grp) {
+    const int t0 = grp * a.gtiles, G = a.gtiles < a.mtiles - t0 ? a.gtiles : a.mtiles - t0;
+    const int cf = ((t0 * 128) / 9 < a.C - 1) ? (t0 * 128) / 9 : a.C - 1;
+    const int cl = (((t0 + G) * 128 - 1) / 9 < a.C - 1) ? ((t0 + G) * 128 - 1) / 9 : a.C - 1;
+    const int np = (cl - (cf & ~7)) / 8 + 1;
+    if ((cf & ~7) + 8 * np > Cx || (long long)ring_px * np * 16 > kWgHaloBytes) return cudaErrorInvalidValue;
+  }
+  a.chunks = B * (H / a.bh) * (W / a.bw);
+  // about four CTAs per SM in all, within the partial buffer
+  long long nsplit = (4LL * 152 + ngroups - 1) / ngroups;
+  const long long cap = (long long)(kPartFloats / ((size_t)a.mtiles * 128 * a.O));
+  if (nsplit > cap) nsplit = cap;
+  if (nsplit > a.chunks) nsplit = a.chunks;
+  if (nsplit < 1) nsplit = 1;
+  a.per_split = (int)((a.chunks + nsplit - 1) / nsplit);
+  nsplit = (a.chunks + a.per_split - 1) / a.per_split;
+  a.tcols = 32;
+  while (a.tcols < a.gtiles * a.O) a.tcols <<= 1;
+  a.part = u.part;
+  a.err = u.err;
+  // shared memory: two A tiles, the B tile (O rows), the ring (the largest group's pieces),
+  // the chunk's dy, the barriers; sized per layer so that several CTAs share an SM
+  int np_max = 1;
+  for (int grp = 0; grp < ngroups; ++grp) {
+    const int t0 = grp * a.gtiles, G = a.gtiles < a.mtiles - t0 ? a.gtiles : a.mtiles - t0;
+    const int cf = ((t0 * 128) / 9 < a.C - 1) ? (t0 * 128) / 9 : a.C - 1;
+    const int cl = (((t0 + G) * 128 - 1) / 9 < a.C - 1) ? ((t0 + G) * 128 - 1) / 9 : a.C - 1;
+    const int np = (cl - (cf & ~7)) / 8 + 1;
+    if (np > np_max) np_max = np;
+  }
+  a.off_ring = 2 * kWgA + a.O * 128;
+  a.off_dy = a.off_ring + ((ring_px * np_max * 16 + 127) & ~127);
+  a.off_bar = a.off_dy + 2 * ((64 * a.O * 2 + 127) & ~127);
+  const int smem = a.off_bar + 64 + 1024;
+  if (smem > kWgSmem) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)ngroups, (unsigned)nsplit);
+  switch (np_max) {
+#define WG_CASE(N) \
+  case N: k_wgrad_tc<N><<<grid, kWgThreads, smem, st>>>(a); break;
+    WG_CASE(1) WG_CASE(2) WG_CASE(3) WG_CASE(4) WG_CASE(5) WG_CASE(6) WG_CASE(7) WG_CASE(8) WG_CASE(9)
+    WG_CASE(10) WG_CASE(11) WG_CASE(12)
+#undef WG_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  const int n = (9 * a.C + 1) * a.O;
+  k_wgrad_reduce<<<(n + 255) / 256, 256, 0, st>>>(u.part, (int)nsplit, a.mtiles, a.O, a.C, u.grad + u.off.w[l],
                                                   u.grad + u.off.b[l]);
   return cudaGetLastError();
 }

@@ -109,11 +109,14 @@ def _pairs(B, H, W, seed):
     return ounet.stencil(U, V, e), U, V, e
 
 
-def test_loss_and_gradient_vs_oracle():
+@pytest.mark.parametrize("B,H,W", [(2, 128, 128), (1, 128, 384)])
+def test_loss_and_gradient_vs_oracle(B, H, W):
+    # 128 x 384: the lower levels are 48 and 24 pixels wide, so the weight gradient's
+    # pixel chunks are 16 x 4 and 8 x 8 blocks there
     theta = _params(4)
     net = native.Unet()
     net.set_params(theta)
-    r, U, V, e = _pairs(2, 128, 128, 13)
+    r, U, V, e = _pairs(B, H, W, 13)
     loss, g = net.loss_grad(_cuda(r), _cuda(U), _cuda(V), _cuda(e))
     rloss, rg = ounet.loss_grad(theta, r, U, V, e)
     assert abs(loss - rloss) <= 1e-2 * rloss, (loss, rloss)

@@ -385,10 +385,12 @@ ULP_API int ulp_unet_train_step(ulp_unet net, int B, const long long* pair_idx, 
                                 const double* V, float lr, double* loss, void* cuda_stream);
 
 /* Training pairs from the inner PCG of Algorithm 1 on A(U,V) phi = b: phi* is
- * the PCG solution to relative residual tol_star (from 0), and for each
- * k < n, phi_l is the PCG iterate after iters[k] iterations from 0; writes
- * r_out[k] = b - A phi_l and e_out[k] = phi* - phi_l ([n][H][W] FP64).
- * precond: identity or Jacobi.  Synchronises. */
+ * the solution to relative residual tol_star (from 0; solved with the multigrid
+ * flexible CG, which reaches it in tens of iterations), and for each k < n,
+ * phi_l is the iterate of the PCG with precond (identity or Jacobi) after
+ * iters[k] iterations from 0; writes r_out[k] = b - A phi_l and
+ * e_out[k] = phi* - phi_l ([n][H][W] FP64).  Allocates one plan and a workspace
+ * of 3 H W doubles for the call.  Synchronises. */
 ULP_API int ulp_unet_harvest(const double* U, const double* V, const double* b, int H, int W, int precond,
                              double tol_star, int n, const int* iters, double* r_out, double* e_out,
                              void* cuda_stream);

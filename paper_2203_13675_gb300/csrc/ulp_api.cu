@@ -744,6 +744,40 @@ extern "C" int ulp_precond_apply(int precond, const double* U, const double* V, 
   return ULP_OK;
 }
 
+namespace ulp {
+// The inner PCG of ulp_pcg on an existing single-map plan of that size, with the plan's
+// options (the training-pair harvest runs many solves on one plan).
+int pcg_on_plan(ulp_plan plan, const double* U, const double* V, const double* b, int precond, double tol,
+                int max_inner, double* phi, cudaStream_t st, ulp_stats* stats) {
+  Plan& pl = plan->p;
+  const MapDesc& M = pl.hmaps[0];
+  int rc = load_weights(pl, U, V, st);
+  if (rc != ULP_OK) return rc;
+  ULP_CU(launch_to_plane(pl, b, M.f.b, st));
+  ULP_CU(launch_to_plane(pl, phi, M.f.phi, st));
+  if (precond == ULP_PRECOND_LEARNED) return fail(ULP_ERR_UNSUPPORTED, "ulp_pcg: the learned preconditioner needs a plan");
+  if (is_fcg_kind(precond)) ULP_CU(launch_fcg(pl, precond, pcg_args(pl, tol, max_inner), st));
+  else ULP_CU(launch_pcg64(pl, precond, pcg_args(pl, tol, max_inner), st, nullptr, nullptr));
+  ULP_CU(launch_outer_error(pl, 0.0, 1, st));
+  ULP_CU(launch_from_plane(pl, M.f.phi, phi, st));
+  if (stats) return collect(pl, st, stats);
+  ULP_CU(cudaStreamSynchronize(st));
+  return ULP_OK;
+}
+
+// y = A(U, V) x on an existing single-map plan of that size.
+int matvec_on_plan(ulp_plan plan, const double* U, const double* V, const double* x, double* y, cudaStream_t st) {
+  Plan& pl = plan->p;
+  const MapDesc& M = pl.hmaps[0];
+  int rc = load_weights(pl, U, V, st);
+  if (rc != ULP_OK) return rc;
+  ULP_CU(launch_to_plane(pl, x, M.f.r, st));
+  ULP_CU(launch_matvec(pl, M.f.r, M.f.q, st));
+  ULP_CU(launch_from_plane(pl, M.f.q, y, st));
+  return ULP_OK;
+}
+}  // namespace ulp
+
 extern "C" int ulp_pcg(const double* U, const double* V, const double* b, int H, int W, int precond,
                        double tol, int max_inner, const ulp_options* opt, double* phi, void* stream,
                        ulp_stats* stats) {
@@ -753,18 +787,5 @@ extern "C" int ulp_pcg(const double* U, const double* V, const double* b, int H,
   TempPlan tp;
   rc = temp_plan(tp, H, W, opt, stream);
   if (rc != ULP_OK) return rc;
-  Plan& pl = tp.plan->p;
-  const MapDesc& M = pl.hmaps[0];
-  rc = load_weights(pl, U, V, tp.st);
-  if (rc != ULP_OK) return rc;
-  ULP_CU(launch_to_plane(pl, b, M.f.b, tp.st));
-  ULP_CU(launch_to_plane(pl, phi, M.f.phi, tp.st));
-  if (precond == ULP_PRECOND_LEARNED) return fail(ULP_ERR_UNSUPPORTED, "ulp_pcg: the learned preconditioner needs a plan");
-  if (is_fcg_kind(precond)) ULP_CU(launch_fcg(pl, precond, pcg_args(pl, tol, max_inner), tp.st));
-  else ULP_CU(launch_pcg64(pl, precond, pcg_args(pl, tol, max_inner), tp.st, nullptr, nullptr));
-  ULP_CU(launch_outer_error(pl, 0.0, 1, tp.st));
-  ULP_CU(launch_from_plane(pl, M.f.phi, phi, tp.st));
-  if (stats) return collect(pl, tp.st, stats);
-  ULP_CU(cudaStreamSynchronize(tp.st));
-  return ULP_OK;
+  return pcg_on_plan(tp.plan, U, V, b, precond, tol, max_inner, phi, tp.st, stats);
 }

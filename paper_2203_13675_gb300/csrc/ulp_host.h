@@ -146,6 +146,12 @@ namespace ulp {
 // ulp_api.cu: records the event that ends a phase interval of the host-driven flexible CG
 void phase_mark(Plan& pl, cudaStream_t st, int tag);
 
+// ulp_api.cu: the inner PCG of ulp_pcg and the matvec of ulp_matvec on an existing single-map
+// plan of that size (no allocation; the plan's options)
+int pcg_on_plan(ulp_plan plan, const double* U, const double* V, const double* b, int precond, double tol,
+                int max_inner, double* phi, cudaStream_t st, ulp_stats* stats);
+int matvec_on_plan(ulp_plan plan, const double* U, const double* V, const double* x, double* y, cudaStream_t st);
+
 // ulp_fcg.cu: the flexible-CG solve with the DCT, multigrid or learned preconditioner
 cudaError_t launch_fcg(Plan& pl, int kind, const PcgArgs& a, cudaStream_t st, cudaEvent_t e0 = nullptr,
                        cudaEvent_t e1 = nullptr);

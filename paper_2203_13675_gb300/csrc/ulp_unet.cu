@@ -1447,24 +1447,29 @@ extern "C" int ulp_unet_harvest(const double* U, const double* V, const double* 
   double* buf = nullptr;
   UCU(cudaMalloc(&buf, 3 * hw * sizeof(double)));
   double *phis = buf, *phil = buf + hw, *aphi = buf + 2 * hw;
-  int rc = ULP_OK;
+  // one plan for every solve of the harvest (its flexible-CG graph is built once)
+  ulp_plan plan = nullptr;
+  int rc = ulp_plan_create(H, W, nullptr, &plan);
   ulp_stats s;
-  if (cudaMemsetAsync(phis, 0, hw * sizeof(double), st) != cudaSuccess) rc = ULP_ERR_CUDA;
-  if (rc == ULP_OK) rc = ulp_pcg(U, V, b, H, W, precond, tol_star, 0, nullptr, phis, st, &s);
+  // phi*: the multigrid flexible-CG solution (the same system and tolerance, reached in tens of
+  // iterations instead of the thousands a plain PCG needs at tol_star)
+  if (rc == ULP_OK && cudaMemsetAsync(phis, 0, hw * sizeof(double), st) != cudaSuccess) rc = ULP_ERR_CUDA;
+  if (rc == ULP_OK) rc = pcg_on_plan(plan, U, V, b, ULP_PRECOND_MG, tol_star, 0, phis, st, &s);
   if (rc > 0) rc = ULP_OK;  // not converged to tol_star within l_max: the iterate is still the best estimate
   for (int k = 0; k < n && rc == ULP_OK; ++k) {
     if (cudaMemsetAsync(phil, 0, hw * sizeof(double), st) != cudaSuccess) rc = ULP_ERR_CUDA;
     if (rc == ULP_OK && iters[k] > 0) {
-      rc = ulp_pcg(U, V, b, H, W, precond, 1e-300, iters[k], nullptr, phil, st, &s);
+      rc = pcg_on_plan(plan, U, V, b, precond, 1e-300, iters[k], phil, st, &s);
       if (rc > 0) rc = ULP_OK;
     }
-    if (rc == ULP_OK) rc = ulp_matvec(U, V, phil, H, W, aphi, st);
+    if (rc == ULP_OK) rc = matvec_on_plan(plan, U, V, phil, aphi, st);
     if (rc == ULP_OK) {
       unet::k_pair<<<(int)((hw + 255) / 256 < 4096 ? (hw + 255) / 256 : 4096), 256, 0, st>>>(b, aphi, phis, phil, hw, r_out + k * hw, e_out + k * hw);
       if (cudaGetLastError() != cudaSuccess) rc = ULP_ERR_CUDA;
     }
   }
   cudaStreamSynchronize(st);
+  if (plan) ulp_plan_destroy(plan);
   cudaFree(buf);
   return rc == ULP_OK ? ULP_OK : (rc == ULP_ERR_CUDA ? unet_fail(ULP_ERR_CUDA, "ulp_unet_harvest: CUDA error") : rc);
 }

@@ -408,17 +408,18 @@ class Unet:
                                          _ptr(_dev(e)), ctypes.byref(loss), _ptr(g), _stream(stream)))
         return loss.value, g
 
-    def train_step(self, pair_idx, sys_idx, r, e, U, V, lr=1e-3, stream=None):
-        """One Adam step on pairs r[pair_idx] -> e[pair_idx] with weights U[sys_idx], V[sys_idx]."""
+    def train_step(self, pair_idx, sys_idx, r, e, U, V, lr=1e-3, stream=None, want_loss=True):
+        """One Adam step on pairs r[pair_idx] -> e[pair_idx] with weights U[sys_idx], V[sys_idx];
+        returns the batch loss (which synchronises), or None with want_loss=False."""
         _, H, W = r.shape
         B = len(pair_idx)
         pi = (ctypes.c_longlong * B)(*[int(x) for x in pair_idx])
         si = (ctypes.c_int * B)(*[int(x) for x in sys_idx])
         loss = ctypes.c_double()
         _check(load().ulp_unet_train_step(self._h, B, pi, si, H, W, _ptr(_dev(r)), _ptr(_dev(e)),
-                                          _ptr(_dev(U)), _ptr(_dev(V)), float(lr), ctypes.byref(loss),
-                                          _stream(stream)))
-        return loss.value
+                                          _ptr(_dev(U)), _ptr(_dev(V)), float(lr),
+                                          ctypes.byref(loss) if want_loss else None, _stream(stream)))
+        return loss.value if want_loss else None
 
 
 def ulp_unet_harvest(U, V, b, iters, precond="jacobi", tol_star=1e-10, r_out=None, e_out=None, stream=None):

@@ -49,7 +49,8 @@ extern "C" {
  * this system, Sec. 1); RBSSOR and RBILU are items 3-5 with the unknowns in
  * red-black order instead of the natural one (the paper leaves the ordering
  * open), which makes each triangular solve one parallel pass per colour.  DCT,
- * LEARNED, MG, RBSSOR and RBILU run in flexible CG on single-map FP64 plans. */
+ * LEARNED, MG, RBSSOR and RBILU run in flexible CG on single-map FP64 plans; MG
+ * also on mixed-precision plans and, map by map, on batched plans. */
 typedef enum {
   ULP_PRECOND_IDENTITY = 0, /* M = I: PCG becomes CG */
   ULP_PRECOND_JACOBI = 1,   /* M = diag(A) */
@@ -175,7 +176,10 @@ typedef struct ulp_plan_s* ulp_plan;
 ULP_API int ulp_plan_create(int H, int W, const ulp_options* opt, ulp_plan* out);
 
 /* ulp_plan_create_batched: workspace for n maps of sizes H[t] x W[t] solved
- * together by one persistent launch per outer pass.  1 <= n <= 256. */
+ * together by one persistent launch per outer pass (I, Jacobi, ILU/IC/SSOR).
+ * 1 <= n <= 256.  With ULP_PRECOND_MG the first batched call also creates one
+ * single-map plan per map (the plan owns and destroys them) and runs the maps
+ * concurrently on eight streams forked from the call's stream. */
 ULP_API int ulp_plan_create_batched(int n, const int* H, const int* W, const ulp_options* opt,
                             ulp_plan* out);
 
@@ -202,9 +206,12 @@ typedef struct ulp_map {
 } ulp_map;
 
 /* ulp_unwrap_batched: the n maps of a batched plan (sizes in creation order),
- * all outer passes of all maps in max_outer persistent launches.  per_map:
- * host array of n stats or NULL (same synchronisation rule as ulp_unwrap).
- * Returns the worst status over the maps. */
+ * all outer passes of all maps in max_outer persistent launches; with
+ * ULP_PRECOND_MG (FP64 or mixed precision) each map runs the multigrid flexible
+ * CG of ulp_unwrap on its own plan, the maps spread over eight streams (largest
+ * first, on the least-loaded stream), all forked from and joined back into
+ * cuda_stream.  per_map: host array of n stats or NULL (same synchronisation
+ * rule as ulp_unwrap).  Returns the worst status over the maps. */
 ULP_API int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precond, double tol,
                        int max_outer, int max_inner, void* cuda_stream, ulp_stats* per_map);
 

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 
@@ -58,6 +59,12 @@ extern "C" const char* ulp_last_error(void) { return g_err.c_str(); }
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static void destroy_plan(Plan& pl) {
+  for (ulp_plan s : pl.sub) ulp_plan_destroy(s);
+  pl.sub.clear();
+  for (cudaStream_t s : pl.sub_st) cudaStreamDestroy(s);
+  pl.sub_st.clear();
+  for (cudaEvent_t e : pl.sub_ev) cudaEventDestroy(e);
+  pl.sub_ev.clear();
   destroy_fcg(pl);
   if (pl.dct) dct_destroy(pl.dct);
   if (pl.dct_mem) cudaFree(pl.dct_mem);
@@ -457,6 +464,83 @@ static int graph_call(Plan& pl, const ulp_map* maps, int precond, double tol, in
   return ULP_OK;
 }
 
+// Multigrid on a batched plan: every map on a single-map plan of its own (made on the first
+// such call, with the batch's options), the maps spread over a few streams forked from the
+// caller's stream and joined back into it, largest first on the least-loaded stream.  Each
+// map's call is exactly ulp_unwrap on its plan.
+constexpr int kBatchStreams = 8;
+static int batched_sub_call(Plan& pl, const ulp_map* maps, int precond, double tol, int max_outer, int max_inner,
+                            cudaStream_t st, ulp_stats* per_map) {
+  const int n = pl.nmaps;
+  if (pl.sub.empty()) {
+    std::vector<int> order(n);
+    for (int m = 0; m < n; ++m) order[m] = m;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+      return (long long)pl.hmaps[a].H * pl.hmaps[a].W > (long long)pl.hmaps[b].H * pl.hmaps[b].W;
+    });
+    const int ns = n < kBatchStreams ? n : kBatchStreams;
+    std::vector<long long> load(ns, 0);
+    pl.sub.assign(n, nullptr);
+    pl.sub_stream.assign(n, 0);
+    for (int m : order) {
+      int best = 0;
+      for (int s = 1; s < ns; ++s)
+        if (load[s] < load[best]) best = s;
+      pl.sub_stream[m] = best;
+      load[best] += (long long)pl.hmaps[m].H * pl.hmaps[m].W;
+    }
+    ulp_options o = pl.opt;
+    o.graph = 0;
+    for (int m = 0; m < n; ++m) {
+      const int rc = ulp_plan_create(pl.hmaps[m].H, pl.hmaps[m].W, &o, &pl.sub[m]);
+      if (rc != ULP_OK) {
+        for (ulp_plan s : pl.sub) ulp_plan_destroy(s);
+        pl.sub.clear();
+        return rc;
+      }
+    }
+    ULP_CU(cudaSetDevice(pl.device));
+    pl.sub_st.assign(ns, nullptr);
+    for (int s = 0; s < ns; ++s) ULP_CU(cudaStreamCreateWithFlags(&pl.sub_st[s], cudaStreamNonBlocking));
+    pl.sub_ev.assign(ns + 1, nullptr);
+    for (int s = 0; s <= ns; ++s) ULP_CU(cudaEventCreateWithFlags(&pl.sub_ev[s], cudaEventDisableTiming));
+  }
+  const int ns = (int)pl.sub_st.size();
+  long long host = 0;
+  for (int m = 0; m < n; ++m) host -= pl.sub[m]->p.kernel_launches;
+  ULP_CU(cudaEventRecord(pl.sub_ev[0], st));
+  for (int s = 0; s < ns; ++s) ULP_CU(cudaStreamWaitEvent(pl.sub_st[s], pl.sub_ev[0], 0));
+  for (int m = 0; m < n; ++m) {
+    const int rc = ulp_unwrap_batched(pl.sub[m], maps + m, precond, tol, max_outer, max_inner,
+                                      pl.sub_st[pl.sub_stream[m]], nullptr);
+    if (rc != ULP_OK) return rc;
+  }
+  for (int s = 0; s < ns; ++s) {
+    ULP_CU(cudaEventRecord(pl.sub_ev[1 + s], pl.sub_st[s]));
+    ULP_CU(cudaStreamWaitEvent(st, pl.sub_ev[1 + s], 0));
+  }
+  pl.last_stream = st;
+  // kernels of the call: the host launches on the maps' plans, and, where the statistics give
+  // the inner iterations, the kernels their solve graphs ran (start + iterations x body per pass)
+  for (int m = 0; m < n; ++m) host += pl.sub[m]->p.kernel_launches;
+  pl.kernel_launches += host;
+  if (!per_map) {
+    pl.last_status = ULP_OK;
+    return ULP_OK;
+  }
+  int worst = ULP_OK;
+  for (int m = 0; m < n; ++m) {
+    const int s = ulp_plan_last_status(pl.sub[m], per_map + m);
+    if (s < 0 && (worst >= 0 || s < worst)) worst = s;
+    else if (s == ULP_WARN_MAXITER && worst == ULP_OK) worst = s;
+    const Plan& sp = pl.sub[m]->p;
+    for (int k = 0; k < per_map[m].outer && k < ULP_MAX_OUTER_STATS; ++k)
+      pl.kernel_launches += sp.fcg_start_kernels + per_map[m].inner[k] * sp.fcg_body_kernels;
+  }
+  pl.last_status = worst;
+  return worst;
+}
+
 extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precond, double tol,
                                   int max_outer, int max_inner, void* cuda_stream, ulp_stats* per_map) {
   if (!plan || !maps) return fail(ULP_ERR_INVALID, "null argument");
@@ -468,8 +552,8 @@ extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precon
     return fail(ULP_ERR_UNSUPPORTED, "mixed precision supports the identity, Jacobi and multigrid preconditioners");
   if (precond == ULP_PRECOND_DCT && (pl.nmaps != 1 || !pl.dct))
     return fail(ULP_ERR_UNSUPPORTED, "the DCT preconditioner is available on single-map plans");
-  if (precond == ULP_PRECOND_MG && (pl.nmaps != 1 || !pl.mg))
-    return fail(ULP_ERR_UNSUPPORTED, "the multigrid preconditioner is available on single-map plans");
+  if (precond == ULP_PRECOND_MG && pl.nmaps == 1 && !pl.mg)
+    return fail(ULP_ERR_UNSUPPORTED, "the multigrid preconditioner is not set up on this plan");
   if ((precond == ULP_PRECOND_RBSSOR || precond == ULP_PRECOND_RBILU) && pl.nmaps != 1)
     return fail(ULP_ERR_UNSUPPORTED, "the red-black preconditioners are available on single-map plans");
   if (precond == ULP_PRECOND_LEARNED && (pl.nmaps != 1 || !pl.unet))
@@ -481,6 +565,8 @@ extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precon
   }
   ULP_CU(cudaSetDevice(pl.device));
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (precond == ULP_PRECOND_MG && pl.nmaps > 1)
+    return batched_sub_call(pl, maps, precond, tol, max_outer, max_inner, st, per_map);
   pl.last_stream = st;
   // the DCT, learned and multigrid solves are themselves graphs with a WHILE node, which cannot be
   // nested: they run eagerly
@@ -558,6 +644,17 @@ extern "C" int ulp_plan_last_status(ulp_plan plan, ulp_stats* stats) {
   if (!plan) return fail(ULP_ERR_INVALID, "null plan");
   Plan& pl = plan->p;
   ULP_CU(cudaSetDevice(pl.device));
+  if (!pl.sub.empty()) {  // a multigrid batch: the worst over the maps' own plans, the first map's stats
+    int worst = ULP_OK;
+    for (size_t m = 0; m < pl.sub.size(); ++m) {
+      ulp_stats s;
+      const int r = ulp_plan_last_status(pl.sub[m], &s);
+      if (m == 0 && stats) *stats = s;
+      if (r < 0 && (worst >= 0 || r < worst)) worst = r;
+      else if (r == ULP_WARN_MAXITER && worst == ULP_OK) worst = r;
+    }
+    return worst;
+  }
   std::vector<ulp_stats> all(pl.nmaps);  // collect() writes one record per map; the caller gets the first
   const int rc = collect(pl, pl.last_stream, all.data());
   if (stats) *stats = all[0];

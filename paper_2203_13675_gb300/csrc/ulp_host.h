@@ -59,6 +59,12 @@ struct Plan {
   std::vector<cudaEvent_t> ph_pool;
   std::vector<int> ph_tag;
   size_t ph_used = 0;
+  // multigrid batches: one single-map plan per map, run concurrently on a few streams (the
+  // flexible-CG solve of each map is itself a graph with a WHILE node, which does not nest)
+  std::vector<ulp_plan> sub;
+  std::vector<int> sub_stream;              // stream index of each map
+  std::vector<cudaStream_t> sub_st;
+  std::vector<cudaEvent_t> sub_ev;          // fork event, then one join event per stream
   // captured call (options.graph): the executable graph, the arguments it was captured with
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;

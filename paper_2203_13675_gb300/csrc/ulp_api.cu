@@ -231,7 +231,7 @@ static int plan_init(Plan& pl, int n, const int* H, const int* W, const ulp_opti
                       &M.f.cw, &M.f.cn, &M.f.ce, &M.f.cs};
     for (double** q : f64) { *q = reinterpret_cast<double*>(p); p += e64; }
     float** f32[] = {&M.h.U, &M.h.V, &M.h.Dinv, &M.h.x, &M.h.r, &M.h.s, &M.h.q,
-                     &M.h.d0, &M.h.d1, &M.h.cw, &M.h.cn, &M.h.pinv, &M.h.xl};
+                     &M.h.d0, &M.h.d1, &M.h.cw, &M.h.cn, &M.h.pinv, &M.h.y};
     for (float** q : f32) { *q = reinterpret_cast<float*>(p); p += e32; }
     M.f.mask = reinterpret_cast<uint8_t*>(p);
     p += align256((size_t)M.H * M.pitch);

@@ -165,7 +165,8 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
   double v2 = (own && cnt > 2) ? __ldcg(&Sp->gpart[2][lane]) : 0.0;
   double delta = 0.0, delta0 = 0.0, bb = 0.0, rr_best = 0.0;
   long long iter = 0;
-  int fallback = 0, restart = 0, stall = 0, force_refresh = 0, stop_after = 0, confirm = 0;
+  int fallback = 0, restart = 0, stall = 0, force_refresh = 0, stop_after = 0, confirm = 0, refresh_next = 0;
+  double rr_ref = 0.0;
   if (lane == 0) {
     delta = __ldcg(&Sp->delta);
     delta0 = __ldcg(&Sp->delta0);
@@ -178,6 +179,8 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
     force_refresh = __ldcg(&Sp->force_refresh);
     stop_after = __ldcg(&Sp->stop_after);
     confirm = __ldcg(&Sp->confirm);
+    refresh_next = __ldcg(&Sp->refresh_next);
+    rr_ref = __ldcg(&Sp->rr_ref);
   }
   v0 = warp_sum(v0);
   v1 = cnt > 1 ? warp_sum(v1) : 0.0;
@@ -226,11 +229,18 @@ __device__ __forceinline__ void finish_map(const PcgArgs& a, const MapDesc& M, M
         S->bb = v2;
         S->iter = 0;
         S->rr_best = v1;
+        S->rr_ref = v1;
+        S->refresh_next = 0;
         S->stall = 0;
       } else if (ph == kPhFcg) {
         // flexible CG (Polak-Ribiere): beta = r_{k+1}^T (s_{k+1} - s_k) / (r_k^T s_k), v2 = r_{k+1}^T s_k
         refreshed = (a.xfcg ? (iter > 0 && (iter % M.refresh) == 0) : (iter % M.refresh) == 0) || force_refresh ||
-                    confirm;
+                    confirm || refresh_next;
+        if (a.xfcg) {
+          // mixed: r^T r of the last true residual, and a refresh once ||r|| has fallen 100-fold since
+          S->refresh_next = (!refreshed && v1 < 1e-4 * rr_ref) ? 1 : 0;
+          if (refreshed) S->rr_ref = v1;
+        }
         if (confirm) {
           // mixed flexible CG: this body took no step; it folded the correction into phi and
           // recomputed r and s for the same iterate, so the iteration count and beta (the

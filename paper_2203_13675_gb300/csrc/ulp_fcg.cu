@@ -234,10 +234,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_f_dots(const PcgArgs* pa, int i
 
 // ---------------------------------------------------------------- mixed flexible CG
 // The multigrid solve with the precision split of the mixed form: the Krylov
-// recurrence (d, q = A d, r, s) on FP32 planes with FP32 weights, the correction
-// since the last refresh as a double-float pair of FP32 planes, the inner products
-// as double-float sums of exact FP32 products, alpha, beta and the stop tests in
-// FP64, and phi in FP64:
+// recurrence (d, q = A d, r, s and the correction x since the last refresh) on
+// FP32 planes with FP32 weights, the inner products as double-float sums of exact
+// FP32 products, alpha, beta and the stop tests in FP64, and phi in FP64:
 // every refresh period the correction is folded into phi and r = b - A phi is
 // recomputed with the FP64 weights.  The multigrid cycle
 // reads r directly (its FP32 right-hand side is the recurrence's r plane) and
@@ -253,22 +252,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_f_dots(const PcgArgs* pa, int i
 //   R: on refresh iterations r = b - A phi (FP64, rounded to FP32), r_{k+1}^T s_k, r^T r
 //   M: the V-cycle, whose last kernel sums r^T s and runs the dot phase
 
-// hi + lo += y with hi, lo a double-float pair: TwoSum of hi and y (the rounding error of the
-// FP32 sum, exact), added into lo
-__device__ __forceinline__ void df_add(float& hi, float& lo, float y) {
-  const float s = __fadd_rn(hi, y);
-  const float bp = __fsub_rn(s, hi);
-  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(y, bp));
-  hi = s;
-  lo = __fadd_rn(lo, err);
-}
-
 // refresh iterations: every M.refresh-th after the first (the start computed r in FP64
-// just before iteration 0), the confirmation body that follows the recurrence's first
-// report of convergence, and every iteration after a confirmation that missed the tolerance
+// just before iteration 0), the one after ||r|| has fallen 100-fold since the last true
+// residual (so the FP32 correction x never holds more than about 1 % of the iterate's
+// change since then, and its rounding stays below the tolerance's reach), the confirmation
+// body that follows the recurrence's first report of convergence, and every iteration
+// within a factor 2 of the tolerance or after a confirmation that missed it
 __device__ __forceinline__ bool x_refresh(const MapDesc& M, MapState* S) {
   const long long it = *(volatile long long*)&S->iter;
-  return (it > 0 && (it % M.refresh) == 0) || *(volatile int*)&S->force_refresh || *(volatile int*)&S->confirm;
+  return (it > 0 && (it % M.refresh) == 0) || *(volatile int*)&S->force_refresh || *(volatile int*)&S->confirm ||
+         *(volatile int*)&S->refresh_next;
 }
 
 __global__ void __launch_bounds__(kThreads, 2) k_x_a(const PcgArgs* pa) {
@@ -295,14 +288,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_b(const PcgArgs* pa) {
     DF rsp, rrp;
     // rows in groups of four, all loads of a group issued before its stores
     for (int i = g.i0; i < g.i1; i += 4) {
-      float2 dv[4], xv[4], xlv[4], qv[4], rv[4], sv[4];
+      float2 dv[4], xv[4], qv[4], rv[4], sv[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (i + k < g.i1) {
           const size_t off = (size_t)(i + k) * P + j;
           dv[k] = ldf2(d, off);
           xv[k] = ldf2(M.h.x, off);
-          xlv[k] = ldf2(M.h.xl, off);
           if (!refresh) {
             qv[k] = ldf2(M.h.q, off);
             rv[k] = ldf2(M.h.r, off);
@@ -314,21 +306,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_b(const PcgArgs* pa) {
       for (int k = 0; k < 4; ++k) {
         if (i + k < g.i1) {
           const size_t off = (size_t)(i + k) * P + j;
-          // the correction is a double-float sum x + xl (TwoSum of each step into it), so the
-          // iterate carries no FP32 rounding of x when it is folded into phi
-          float2 x = xv[k], xl = xlv[k];
-          df_add(x.x, xl.x, __fmul_rn(alpha, dv[k].x));
-          df_add(x.y, xl.y, __fmul_rn(alpha, dv[k].y));
+          float2 x = xv[k];
+          x.x = __fmaf_rn(alpha, dv[k].x, x.x);
+          x.y = __fmaf_rn(alpha, dv[k].y, x.y);
           if (refresh) {
             double2 ph = ld2(M.f.phi, off);
-            ph.x += (double)x.x + (double)xl.x;
-            ph.y += (double)x.y + (double)xl.y;
+            ph.x += (double)x.x;
+            ph.y += (double)x.y;
             st2(M.f.phi, off, ph);
             stf2(M.h.x, off, make_float2(0.f, 0.f));
-            stf2(M.h.xl, off, make_float2(0.f, 0.f));
           } else {
             stf2(M.h.x, off, x);
-            stf2(M.h.xl, off, xl);
             float2 r = rv[k];
             r.x = __fmaf_rn(-alpha, qv[k].x, r.x);
             r.y = __fmaf_rn(-alpha, qv[k].y, r.y);
@@ -374,7 +362,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_res(const PcgArgs* pa, int in
       rrp.add_prod(r.y, r.y);
       if (init) {
         stf2(M.h.x, off, make_float2(0.f, 0.f));
-        stf2(M.h.xl, off, make_float2(0.f, 0.f));
         bb = fma(bv.x, bv.x, bb);
         bb = fma(bv.y, bv.y, bb);
       } else {
@@ -442,13 +429,12 @@ __global__ void __launch_bounds__(kThreads) k_x_fold(const PcgArgs* pa) {
     const int j = g.j0 + 2 * lane;
     for (int i = g.i0; i < g.i1; ++i) {
       const size_t off = (size_t)i * P + j;
-      const float2 xv = ldf2(M.h.x, off), xlv = ldf2(M.h.xl, off);
+      const float2 xv = ldf2(M.h.x, off);
       double2 ph = ld2(M.f.phi, off);
-      ph.x += (double)xv.x + (double)xlv.x;
-      ph.y += (double)xv.y + (double)xlv.y;
+      ph.x += (double)xv.x;
+      ph.y += (double)xv.y;
       st2(M.f.phi, off, ph);
       stf2(M.h.x, off, make_float2(0.f, 0.f));
-      stf2(M.h.xl, off, make_float2(0.f, 0.f));
     }
   }
 }

@@ -627,6 +627,8 @@ __global__ void k_pcg_reset(MapState* S, int nmaps, int* n_active, Barrier* bar)
     s->force_refresh = 0;
     s->x_clean = 0;
     s->confirm = 0;
+    s->refresh_next = 0;
+    s->rr_ref = 0.0;
     s->rr_best = 0.0;
     if (act) atomicAdd(&s_cnt, 1);
   }

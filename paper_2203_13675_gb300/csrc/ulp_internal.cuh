@@ -45,8 +45,7 @@ struct Planes64 {
 struct Planes32 {
   float *U, *V, *Dinv;      // weights (FP32) and Jacobi inverse
   float *x, *r, *s, *q, *d0, *d1;
-  float *cw, *cn, *pinv;    // sweep coefficients (mixed ILU/SSOR)
-  float *xl;                // mixed flexible CG: low word of the double-float correction (x + xl)
+  float *cw, *cn, *pinv, *y; // sweep coefficients (mixed ILU/SSOR)
 };
 
 struct MapDesc {
@@ -82,6 +81,9 @@ struct MapState {
   int x_clean;              // mixed flexible CG: stopped right after a refresh, so the correction is 0
   int confirm;              // mixed flexible CG: the next body re-evaluates the current iterate on the FP64
                             // true residual without taking a step
+  int refresh_next;         // mixed flexible CG: ||r|| fell 100-fold since the last true residual
+  int pad3_;
+  double rr_ref;            // mixed flexible CG: r^T r of the last true residual
 };
 
 // Device-side record of one call (per map), copied to the host at the end.

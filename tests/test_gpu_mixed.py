@@ -4,7 +4,11 @@ true residual every 20 iterations) against the FP64 oracle.
 The bar is the spec one for the result: within 1e-4 rad RMS of the FP64
 oracle after removing the mean, and the FP64 true residual of the first pass,
 computed by the oracle from the GPU's phi, within the tolerance.  Iteration
-counts are reported against the oracle's and must stay within 10 %.
+counts: Jacobi within 2 of the oracle's (the FP64 bar).  Plain CG (M = I) with an
+FP32 recurrence converges later than in FP64 -- the finite-precision delay of CG,
+which grows with the length of an unpreconditioned recurrence: on these maps it
+takes 1.7-3.2 % more iterations than the oracle at 1.8e3-3.4e3 iterations -- so
+M = I is held to 5 % of the oracle's count; its solution still meets 1e-4 rad.
 """
 import numpy as np
 import pytest
@@ -44,7 +48,7 @@ def test_mixed_unwrap_vs_oracle(kind, H, W, p, mask):
     assert st["status"] == 0
     assert _rms(phi.cpu().numpy(), ref, keep) < 1e-4
     for a, b in zip(st["inner"], rst["inner"]):
-        assert abs(a - b) <= max(2, int(0.1 * b)), (st["inner"], rst["inner"])
+        assert abs(a - b) <= (2 if kind == "jacobi" else max(2, int(0.05 * b))), (st["inner"], rst["inner"])
 
 
 @pytest.mark.parametrize("kind", ["jacobi", "identity"])

@@ -252,22 +252,39 @@ __global__ void __launch_bounds__(kThreads, 2) k_f_dots(const PcgArgs* pa, int i
 //   R: on refresh iterations r = b - A phi (FP64, rounded to FP32), r_{k+1}^T s_k, r^T r
 //   M: the V-cycle, whose last kernel sums r^T s and runs the dot phase
 
-// refresh iterations: every M.refresh-th after the first (the start computed r in FP64
-// just before iteration 0), the one after ||r|| has fallen 100-fold since the last true
-// residual (so the FP32 correction x never holds more than about 1 % of the iterate's
-// change since then, and its rounding stays below the tolerance's reach), the confirmation
-// body that follows the recurrence's first report of convergence, and every iteration
-// within a factor 2 of the tolerance or after a confirmation that missed it
-__device__ __forceinline__ bool x_refresh(const MapDesc& M, MapState* S) {
-  const long long it = *(volatile long long*)&S->iter;
-  return (it > 0 && (it % M.refresh) == 0) || *(volatile int*)&S->force_refresh || *(volatile int*)&S->confirm ||
-         *(volatile int*)&S->refresh_next;
+// The map state a phase of the mixed flexible CG reads, loaded as one batch of
+// independent loads (one round trip to L2, where a chain of tests would wait for each).
+// refresh: the iteration recomputes the true residual -- every M.refresh-th after the
+// first (the start computed r in FP64 just before iteration 0), the one after ||r|| has
+// fallen 100-fold since the last true residual (so the FP32 correction x never holds more
+// than about 1 % of the iterate's change since then, and its rounding stays below the
+// tolerance's reach), the confirmation body that follows the recurrence's first report of
+// convergence, and every iteration within a factor 2 of the tolerance or after a
+// confirmation that missed it.
+struct XState {
+  long long it;
+  double alpha;
+  int done, confirm, refresh;
+};
+__device__ __forceinline__ XState x_state(const MapDesc& M, MapState* S) {
+  const volatile MapState* v = S;
+  XState x;
+  x.done = v->done;
+  x.it = v->iter;
+  const int fr = v->force_refresh;
+  x.confirm = v->confirm;
+  const int rn = v->refresh_next;
+  x.alpha = v->alpha;
+  x.refresh = ((x.it > 0 && (x.it % M.refresh) == 0) ? 1 : 0) | fr | x.confirm | rn;
+  return x;
 }
 
 __global__ void __launch_bounds__(kThreads, 2) k_x_a(const PcgArgs* pa) {
   const PcgArgs a = *pa;
   FCG_TILE_LOOP(a) {
-    if (*(volatile int*)&S->done || *(volatile int*)&S->confirm) return;  // a confirmation body takes no step
+    const volatile MapState* v = S;
+    const int done = v->done, confirm = v->confirm;
+    if (done | confirm) return;  // a confirmation body takes no step
     a32_tile<kJacobi>(a, M, S, t, lane);
   }
 }
@@ -275,15 +292,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_a(const PcgArgs* pa) {
 __global__ void __launch_bounds__(kThreads, 2) k_x_b(const PcgArgs* pa) {
   const PcgArgs a = *pa;
   FCG_TILE_LOOP(a) {
-    if (*(volatile int*)&S->done) return;
-    const bool refresh = x_refresh(M, S);
-    const bool confirm = *(volatile int*)&S->confirm;
-    const long long it = *(volatile long long*)&S->iter;
+    const XState xs = x_state(M, S);
+    if (xs.done) return;
+    const bool refresh = xs.refresh;
+    const long long it = xs.it;
     const TileGeo g = tile_geo(M, t, a.R);
     const size_t P = M.pitch;
     const float* __restrict__ d = (it & 1) ? M.h.d0 : M.h.d1;
     // a confirmation body only folds the correction into phi (no step: alpha = 0)
-    const float alpha = confirm ? 0.f : (float)*(volatile double*)&S->alpha;
+    const float alpha = xs.confirm ? 0.f : (float)xs.alpha;
     const int j = g.j0 + 2 * lane;
     DF rsp, rrp;
     // rows in groups of four, all loads of a group issued before its stores
@@ -346,10 +363,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_b(const PcgArgs* pa) {
 __global__ void __launch_bounds__(kThreads, 2) k_x_res(const PcgArgs* pa, int init) {
   const PcgArgs a = *pa;
   FCG_TILE_LOOP(a) {
-    if (*(volatile int*)&S->done) return;
-    if (!init && !x_refresh(M, S)) return;
+    const XState xs = x_state(M, S);
+    if (xs.done) return;
+    if (!init && !xs.refresh) return;
     // a confirmation body under the relative-residual stop decides here whether the solve ends
-    const bool confirm = !init && a.stop_mode == ULP_STOP_RELRES && *(volatile int*)&S->confirm;
+    const bool confirm = !init && a.stop_mode == ULP_STOP_RELRES && xs.confirm;
     const TileGeo g = tile_geo(M, t, a.R);
     XPlane x{M.f.phi, (size_t)M.pitch};
     DF rsp, rrp;

@@ -289,7 +289,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_a(const PcgArgs* pa) {
   }
 }
 
+// Phase B's row ring: kRingB slots per warp of the five FP32 rows it reads (dynamic
+// shared memory, kRingBSmem per block).
+constexpr int kLeadB = 6;
+constexpr int kRingB = kLeadB + 1;  // elementwise: a slot is refilled one row after it was read
+struct SlotB {
+  float2 d[32], x[32], q[32], r[32], s[32];
+};
+constexpr size_t kRingBSmem = (size_t)kWarps * kRingB * sizeof(SlotB);  // 71,680 bytes
+
 __global__ void __launch_bounds__(kThreads, 2) k_x_b(const PcgArgs* pa) {
+  extern __shared__ __align__(16) unsigned char xb_dsm[];
   const PcgArgs a = *pa;
   FCG_TILE_LOOP(a) {
     const XState xs = x_state(M, S);
@@ -303,48 +313,75 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_b(const PcgArgs* pa) {
     const float alpha = xs.confirm ? 0.f : (float)xs.alpha;
     const int j = g.j0 + 2 * lane;
     DF rsp, rrp;
-    // rows in groups of four, all loads of a group issued before its stores
-    for (int i = g.i0; i < g.i1; i += 4) {
-      float2 dv[4], xv[4], qv[4], rv[4], sv[4];
+    if (refresh) {
+      // phi += x + alpha d, x = 0: rows in groups of four, all loads of a group first
+      for (int i = g.i0; i < g.i1; i += 4) {
+        float2 dv[4], xv[4];
+        double2 pv[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (i + k < g.i1) {
-          const size_t off = (size_t)(i + k) * P + j;
-          dv[k] = ldf2(d, off);
-          xv[k] = ldf2(M.h.x, off);
-          if (!refresh) {
-            qv[k] = ldf2(M.h.q, off);
-            rv[k] = ldf2(M.h.r, off);
-            sv[k] = ldf2(M.h.s, off);
+        for (int k = 0; k < 4; ++k) {
+          if (i + k < g.i1) {
+            const size_t off = (size_t)(i + k) * P + j;
+            dv[k] = ldf2(d, off);
+            xv[k] = ldf2(M.h.x, off);
+            pv[k] = ld2(M.f.phi, off);
           }
         }
-      }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (i + k < g.i1) {
-          const size_t off = (size_t)(i + k) * P + j;
-          float2 x = xv[k];
-          x.x = __fmaf_rn(alpha, dv[k].x, x.x);
-          x.y = __fmaf_rn(alpha, dv[k].y, x.y);
-          if (refresh) {
-            double2 ph = ld2(M.f.phi, off);
+        for (int k = 0; k < 4; ++k) {
+          if (i + k < g.i1) {
+            const size_t off = (size_t)(i + k) * P + j;
+            float2 x = xv[k];
+            x.x = __fmaf_rn(alpha, dv[k].x, x.x);
+            x.y = __fmaf_rn(alpha, dv[k].y, x.y);
+            double2 ph = pv[k];
             ph.x += (double)x.x;
             ph.y += (double)x.y;
             st2(M.f.phi, off, ph);
             stf2(M.h.x, off, make_float2(0.f, 0.f));
-          } else {
-            stf2(M.h.x, off, x);
-            float2 r = rv[k];
-            r.x = __fmaf_rn(-alpha, qv[k].x, r.x);
-            r.y = __fmaf_rn(-alpha, qv[k].y, r.y);
-            stf2(M.h.r, off, r);
-            rsp.add_prod(r.x, sv[k].x);
-            rsp.add_prod(r.y, sv[k].y);
-            rrp.add_prod(r.x, r.x);
-            rrp.add_prod(r.y, r.y);
           }
         }
       }
+    } else {
+      // x += alpha d, r -= alpha q and the partials: rows in groups of four,
+      // software-pipelined (the next group's loads are issued before this group's
+      // arithmetic and stores, so two groups are in flight)
+      // rows stream through the warp's ring in shared memory, kLeadB rows ahead
+      SlotB* ring = reinterpret_cast<SlotB*>(xb_dsm) + (threadIdx.x >> 5) * kRingB;
+      auto issue = [&](SlotB& sl, int i) {
+        const size_t off = (size_t)i * P + j;
+        cpa8(&sl.d[lane], d + off, 8);
+        cpa8(&sl.x[lane], M.h.x + off, 8);
+        cpa8(&sl.q[lane], M.h.q + off, 8);
+        cpa8(&sl.r[lane], M.h.r + off, 8);
+        cpa8(&sl.s[lane], M.h.s + off, 8);
+      };
+#pragma unroll
+      for (int k = 0; k < kLeadB; ++k) {
+        if (g.i0 + k < g.i1) issue(ring[k], g.i0 + k);
+        cpa_commit();
+      }
+      for (int i = g.i0; i < g.i1; ++i) {
+        cpa_wait<kLeadB - 1>();  // row i has landed
+        const SlotB& sl = ring[(i - g.i0) % kRingB];
+        const float2 dv = sl.d[lane], qv = sl.q[lane], sv = sl.s[lane];
+        float2 x = sl.x[lane], r = sl.r[lane];
+        // the slot of row i - 1 is free: refill it with row i + kLeadB
+        if (i + kLeadB < g.i1) issue(ring[(i + kLeadB - g.i0) % kRingB], i + kLeadB);
+        cpa_commit();
+        const size_t off = (size_t)i * P + j;
+        x.x = __fmaf_rn(alpha, dv.x, x.x);
+        x.y = __fmaf_rn(alpha, dv.y, x.y);
+        stf2(M.h.x, off, x);
+        r.x = __fmaf_rn(-alpha, qv.x, r.x);
+        r.y = __fmaf_rn(-alpha, qv.y, r.y);
+        stf2(M.h.r, off, r);
+        rsp.add_prod(r.x, sv.x);
+        rsp.add_prod(r.y, sv.y);
+        rrp.add_prod(r.x, r.x);
+        rrp.add_prod(r.y, r.y);
+      }
+      cpa_wait_all();  // the warp's next tile refills the same slots
     }
     if (!refresh) {
       // r_{k+1}^T s_k and r_{k+1}^T r_{k+1} per tile for the dot phase
@@ -541,7 +578,7 @@ static cudaError_t fcg_iteration(Plan& pl, int kind, cudaStream_t st) {
   const bool fd = fused_dots(pl, kind);
   if (mixed_fcg(pl, kind)) {
     k_x_a<<<nb, kThreads, 0, st>>>(pl.dargs);
-    k_x_b<<<nb, kThreads, 0, st>>>(pl.dargs);
+    k_x_b<<<nb, kThreads, kRingBSmem, st>>>(pl.dargs);
     k_x_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = fcg_precond(pl, kind, st, fd);
@@ -557,9 +594,15 @@ static cudaError_t fcg_iteration(Plan& pl, int kind, cudaStream_t st) {
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
+// Dynamic shared memory above 48 KB is an attribute of the function on the current device.
+static cudaError_t fcg_attrs() {
+  return cudaFuncSetAttribute(k_x_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBSmem);
+}
+
 // Captures the solve graph: start, then WHILE { guard, iteration }.
 static cudaError_t fcg_build(Plan& pl, int kind) {
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = fcg_attrs();
+  if (e != cudaSuccess) return e;
   if (!pl.cap_stream) {
     e = cudaStreamCreateWithFlags(&pl.cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
@@ -638,7 +681,8 @@ static cudaError_t fcg_build(Plan& pl, int kind) {
 static cudaError_t fcg_eager_mixed(Plan& pl, int kind, cudaStream_t st) {
   const int nb = tile_blocks(pl);
   const bool fd = fused_dots(pl, kind);
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = fcg_attrs();
+  if (e != cudaSuccess) return e;
   phase_mark(pl, st, -1);
   k_x_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
   phase_mark(pl, st, 2);
@@ -657,7 +701,7 @@ static cudaError_t fcg_eager_mixed(Plan& pl, int kind, cudaStream_t st) {
     phase_mark(pl, st, -1);
     k_x_a<<<nb, kThreads, 0, st>>>(pl.dargs);
     phase_mark(pl, st, 0);
-    k_x_b<<<nb, kThreads, 0, st>>>(pl.dargs);
+    k_x_b<<<nb, kThreads, kRingBSmem, st>>>(pl.dargs);
     phase_mark(pl, st, 1);
     k_x_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
     phase_mark(pl, st, 2);

@@ -280,12 +280,13 @@ __device__ __forceinline__ XState x_state(const MapDesc& M, MapState* S) {
 }
 
 __global__ void __launch_bounds__(kThreads, 2) k_x_a(const PcgArgs* pa) {
+  __shared__ Slot32 ring[kWarps][kRing32];  // the stencil's row rings
   const PcgArgs a = *pa;
   FCG_TILE_LOOP(a) {
     const volatile MapState* v = S;
     const int done = v->done, confirm = v->confirm;
     if (done | confirm) return;  // a confirmation body takes no step
-    a32_tile<kJacobi>(a, M, S, t, lane);
+    a32_tile<kJacobi>(a, M, S, t, lane, ring[threadIdx.x >> 5]);
   }
 }
 

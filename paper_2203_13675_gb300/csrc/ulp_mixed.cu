@@ -70,12 +70,21 @@ __device__ __forceinline__ void res64_tile(const PcgArgs& a, const MapDesc& M, M
   tile_arrive(a, M, S, t, init ? kPhResInit : kPhRes, vrs, vrr, bb, lane);
 }
 
+// Phase B's ring slots (kRingB32 per warp, inside the warp's share of phase A's ring).
+constexpr int kLeadB32 = 3;
+constexpr int kRingB32 = kLeadB32 + 1;  // elementwise: a slot is refilled one row after it was read
+struct SlotB32 {
+  float2 d[32], x[32], q[32], r[32], di[32];
+};
+static_assert(kRingB32 * sizeof(SlotB32) <= kRing32 * sizeof(Slot32), "phase B's ring fits phase A's");
+
 // x += alpha d; then either r -= alpha q, s = M^-1 r (partials) or, on a
 // refresh iteration, phi += x, x = 0 (the residual is then recomputed in FP64).
-// Loads run two rows ahead.
+// wring: the warp's share of phase A's ring, through which the rows stream kLeadB32
+// ahead (or null, and on refresh iterations: loads two rows ahead in registers).
 template <int KIND>
 __device__ __forceinline__ void b32_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t, bool refresh,
-                                         int lane) {
+                                         int lane, unsigned char* wring) {
   const TileGeo g = tile_geo(M, t, a.R);
   const size_t P = M.pitch;
   const long long it = *(volatile long long*)&S->iter;
@@ -101,6 +110,52 @@ __device__ __forceinline__ void b32_tile(const PcgArgs& a, const MapDesc& M, Map
     return w;
   };
   DF rs, rr;
+  if (!refresh && wring) {
+    // the rows stream through the warp's ring in shared memory (phase A's ring, free in
+    // this phase), kLeadB32 rows ahead; the arithmetic is that of the loop below
+    SlotB32* ring = reinterpret_cast<SlotB32*>(wring);
+    auto issue = [&](SlotB32& sl, int i) {
+      const size_t off = (size_t)i * P + j;
+      cpa8(&sl.d[lane], d + off, 8);
+      cpa8(&sl.x[lane], M.h.x + off, 8);
+      cpa8(&sl.q[lane], M.h.q + off, 8);
+      cpa8(&sl.r[lane], M.h.r + off, 8);
+      if (KIND == kJacobi) cpa8(&sl.di[lane], M.h.Dinv + off, 8);
+    };
+#pragma unroll
+    for (int k = 0; k < kLeadB32; ++k) {
+      if (g.i0 + k < g.i1) issue(ring[k], g.i0 + k);
+      cpa_commit();
+    }
+    for (int i = g.i0; i < g.i1; ++i) {
+      cpa_wait<kLeadB32 - 1>();
+      const SlotB32& sl = ring[(i - g.i0) % kRingB32];
+      const float2 dv = sl.d[lane], qv = sl.q[lane];
+      float2 xv = sl.x[lane], r = sl.r[lane];
+      const float2 di = (KIND == kJacobi) ? sl.di[lane] : z2;
+      if (i + kLeadB32 < g.i1) issue(ring[(i + kLeadB32 - g.i0) % kRingB32], i + kLeadB32);
+      cpa_commit();
+      const size_t off = (size_t)i * P + j;
+      xv.x = __fmaf_rn(alpha, dv.x, xv.x);
+      xv.y = __fmaf_rn(alpha, dv.y, xv.y);
+      stf2(M.h.x, off, xv);
+      r.x = __fmaf_rn(-alpha, qv.x, r.x);
+      r.y = __fmaf_rn(-alpha, qv.y, r.y);
+      stf2(M.h.r, off, r);
+      if (KIND == kJacobi) {
+        const float2 sv = make_float2(di.x * r.x, di.y * r.y);
+        stf2(M.h.s, off, sv);
+        rs.add_prod(r.x, sv.x);
+        rs.add_prod(r.y, sv.y);
+      }
+      rr.add_prod(r.x, r.x);
+      rr.add_prod(r.y, r.y);
+    }
+    cpa_wait_all();
+    const double vrr = rr.value();
+    tile_arrive(a, M, S, t, kPhB, (KIND == kIdentity) ? vrr : rs.value(), vrr, 0.0, lane);
+    return;
+  }
   Row c0 = load(g.i0), c1 = load(g.i0 + 1);
   for (int i = g.i0; i < g.i1; ++i) {
     const Row c2 = load(i + 2);
@@ -156,6 +211,7 @@ __device__ __forceinline__ void fold_tile(const PcgArgs& a, const MapDesc& M, in
 
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 2) k_pcg32(PcgArgs a) {
+  __shared__ Slot32 ring32[kWarps][kRing32];  // phase A's row rings, phase B's in turn
   __shared__ int s_base[kMaxMaps + 1];
   __shared__ int s_any;
   for (int m = threadIdx.x; m <= a.nmaps; m += blockDim.x)
@@ -188,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_pcg32(PcgArgs a) {
 
   for (int g = 0;; ++g) {
     if (*(volatile int*)a.n_active == 0) break;
-    for_tiles([&](const MapDesc& M, MapState* S, int t) { a32_tile<KIND>(a, M, S, t, lane); });
+    for_tiles([&](const MapDesc& M, MapState* S, int t) { a32_tile<KIND>(a, M, S, t, lane, ring32[threadIdx.x >> 5]); });
     if (!grid_sync(a.bar, a.timeout_ns)) return;
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
@@ -197,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_pcg32(PcgArgs a) {
     __syncthreads();
     const bool any_refresh = s_any != 0;
     for_tiles([&](const MapDesc& M, MapState* S, int t) {
-      b32_tile<KIND>(a, M, S, t, (g % M.refresh) == 0, lane);
+      b32_tile<KIND>(a, M, S, t, (g % M.refresh) == 0, lane, reinterpret_cast<unsigned char*>(ring32[threadIdx.x >> 5]));
     });
     if (!grid_sync(a.bar, a.timeout_ns)) return;
     if (any_refresh) {

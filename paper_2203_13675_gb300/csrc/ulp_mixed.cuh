@@ -107,11 +107,11 @@ __device__ __forceinline__ void slot32_issue(Slot32& sl, const MapDesc& M, const
   }
 }
 
+// ring: the warp's kRing32 slots in shared memory
 template <class Epi>
 __device__ __forceinline__ void stencil_tile32(const MapDesc& M, int i0, int i1, int j0, int lane,
-                                               const float* U, const float* V, const XDir32& x, Epi& epi) {
-  __shared__ Slot32 ring_all[kWarps][kRing32];
-  Slot32* ring = ring_all[threadIdx.x >> 5];
+                                               const float* U, const float* V, const XDir32& x, Epi& epi,
+                                               Slot32* ring) {
   const int j = j0 + 2 * lane;
   const bool hw = (lane == 0) && (j0 > 0);
   const bool he = (lane == 31) && (j0 + kStrip < M.pitch);
@@ -179,8 +179,10 @@ __device__ __forceinline__ void stencil_tile32(const MapDesc& M, int i0, int i1,
 }
 
 // d = s + beta d_old, q = A d in FP32, d^T q FP64-accurate.
+// ring: the warp's kRing32 ring slots in shared memory
 template <int KIND>
-__device__ __forceinline__ void a32_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t, int lane) {
+__device__ __forceinline__ void a32_tile(const PcgArgs& a, const MapDesc& M, MapState* S, int t, int lane,
+                                         Slot32* ring) {
   const TileGeo g = tile_geo(M, t, a.R);
   const long long it = *(volatile long long*)&S->iter;
   const float* sv = (KIND == kIdentity) ? M.h.r : M.h.s;
@@ -194,7 +196,7 @@ __device__ __forceinline__ void a32_tile(const PcgArgs& a, const MapDesc& M, Map
     dq.add_prod(xc.x, ax.x);
     dq.add_prod(xc.y, ax.y);
   };
-  stencil_tile32(M, g.i0, g.i1, g.j0, lane, M.h.U, M.h.V, x, epi);
+  stencil_tile32(M, g.i0, g.i1, g.j0, lane, M.h.U, M.h.V, x, epi, ring);
   tile_arrive(a, M, S, t, kPhA, dq.value(), 0.0, 0.0, lane);
 }
 

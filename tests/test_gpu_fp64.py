@@ -61,6 +61,34 @@ def test_wrapped_diffs_bit_exact(H, W):
     assert np.array_equal(dy.cpu().numpy(), oy)
 
 
+def test_wrapped_diffs_bit_exact_at_the_branch_cuts():
+    """Differences at and a few units in the last place around the odd multiples of pi,
+    where the wrap's integer decision ceil((x - pi) / (2 pi)) flips, and large ones: the
+    decision and the result are the oracle's bit for bit."""
+    H, W = 64, 64
+    xs = []
+    for n in range(-6, 7):
+        c = math.pi * (2 * n + 1)
+        v = c
+        for _ in range(4):
+            xs += [v, -v]
+            v = np.nextafter(v, np.inf)
+        v = c
+        for _ in range(4):
+            v = np.nextafter(v, -np.inf)
+            xs += [v, -v]
+    rng = np.random.default_rng(11)
+    xs += list(rng.uniform(-1e4, 1e4, 200)) + list(rng.normal(0, 4, 200))
+    x = np.resize(np.asarray(xs), (H, W // 2))
+    psi = np.zeros((H, W))
+    psi[:, 1::2] = x          # differences x and -x along rows, exact in FP64
+    psi[1::2, :] += 0.25      # and 0.25 +- x between rows
+    dx, dy = native.ulp_wrapped_diffs(_cuda(psi))
+    ox, oy = oracle.wrapped_diffs(psi)
+    assert np.array_equal(dx.cpu().numpy(), ox)
+    assert np.array_equal(dy.cpu().numpy(), oy)
+
+
 @pytest.mark.parametrize("p", [0.0, 0.5, 1.0, 2.0, 1.3])
 def test_weights_and_rhs(p):
     H, W = 45, 70

@@ -235,7 +235,9 @@ def test_trained_network_gains_over_jacobi():
     iterations) to a solution of the same problem: within 1e-3 rad RMS of the
     Jacobi one (two solves stopped at relative residual 1e-6 with different
     preconditioners differ by about 1e-4 after the outer passes on this map),
-    with at most a few stall windows of extra iterations per pass."""
+    within 20 % (plus 10) of Jacobi PCG's inner iterations per pass: the network's
+    directions cost CG its Krylov acceleration (measured: 1856 against 1696 in the
+    first pass, no fallback) without letting the solve drift."""
     from paper_2203_13675_gb300 import learned
     data = learned.harvest(12, size=256, passes=(0, 2))
     held = learned.harvest(2, size=256, passes=(0, 2), seed0=2000)
@@ -252,7 +254,9 @@ def test_trained_network_gains_over_jacobi():
     assert l_net < 0.9 * l_jac, (l_net, l_jac)
     res = learned.evaluate(net, size=256, seed=5, max_outer=3, preconds=("jacobi", "learned"), reps=1)
     jac, lrn = res["jacobi"], res["learned"]
+    print(f"direction loss {l_net:.4f} (Jacobi step {l_jac:.4f}); inner learned {lrn['inner']} "
+          f"(fallbacks {lrn['fallbacks']}) vs Jacobi {jac['inner']}")
     assert jac["status"] == 0 and lrn["status"] == 0, res
     assert lrn["rms_vs_first"] < 1e-3, res
     for a, b in zip(lrn["inner"], jac["inner"]):
-        assert a <= 2 * b + 600, res
+        assert a <= 1.2 * b + 10, res

@@ -344,10 +344,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_x_b(const PcgArgs* pa) {
         }
       }
     } else {
-      // x += alpha d, r -= alpha q and the partials: rows in groups of four,
-      // software-pipelined (the next group's loads are issued before this group's
-      // arithmetic and stores, so two groups are in flight)
-      // rows stream through the warp's ring in shared memory, kLeadB rows ahead
+      // x += alpha d, r -= alpha q and the partials r^T s, r^T r: the five rows of
+      // each pixel row stream through the warp's ring in shared memory, kLeadB rows
+      // ahead of the arithmetic (the loads in flight cost no registers, and each lane
+      // reads back only what it copied)
       SlotB* ring = reinterpret_cast<SlotB*>(xb_dsm) + (threadIdx.x >> 5) * kRingB;
       auto issue = [&](SlotB& sl, int i) {
         const size_t off = (size_t)i * P + j;

@@ -123,8 +123,23 @@ __global__ void __launch_bounds__(kThreads) k_f_a(const PcgArgs* pa) {
   }
 }
 
+// Phase B's row ring of the FP64 flexible CG: kRingF slots per warp of the five FP64
+// rows it reads (dynamic shared memory, kRingFSmem per block).
+constexpr int kLeadF = 3;
+constexpr int kRingF = kLeadF + 1;  // elementwise: a slot is refilled one row after it was read
+struct SlotF {
+  double2 d[32], ph[32], q[32], s[32], r[32];
+};
+constexpr size_t kRingFSmem = (size_t)kWarps * kRingF * sizeof(SlotF);  // 81,920 bytes
+
+__device__ __forceinline__ void cpa16f(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+
 // phi += alpha d; r -= alpha q and r^T s_k (not on refresh iterations).
 __global__ void __launch_bounds__(kThreads) k_f_b(const PcgArgs* pa) {
+  extern __shared__ __align__(16) unsigned char fb_dsm[];
   const PcgArgs a = *pa;
   FCG_TILE_LOOP(a) {
     if (*(volatile int*)&S->done) return;
@@ -140,7 +155,47 @@ __global__ void __launch_bounds__(kThreads) k_f_b(const PcgArgs* pa) {
     const double alpha = *(volatile double*)&S->alpha;
     const int j = g.j0 + 2 * lane;
     double rsp = 0.0;
-    // rows in groups of four, all loads of a group issued before its stores
+    if (!refresh) {
+      // the rows stream through the warp's ring in shared memory, kLeadF rows ahead of
+      // the arithmetic (that of the loop below)
+      SlotF* ring = reinterpret_cast<SlotF*>(fb_dsm) + (threadIdx.x >> 5) * kRingF;
+      auto issue = [&](SlotF& sl, int i) {
+        const size_t off = (size_t)i * P + j;
+        cpa16f(&sl.d[lane], d + off);
+        cpa16f(&sl.ph[lane], phi + off);
+        cpa16f(&sl.q[lane], qp + off);
+        cpa16f(&sl.s[lane], sp + off);
+        cpa16f(&sl.r[lane], rp + off);
+      };
+#pragma unroll
+      for (int k = 0; k < kLeadF; ++k) {
+        if (g.i0 + k < g.i1) issue(ring[k], g.i0 + k);
+        cpa_commit();
+      }
+      for (int i = g.i0; i < g.i1; ++i) {
+        cpa_wait<kLeadF - 1>();
+        const SlotF& sl = ring[(i - g.i0) % kRingF];
+        const double2 dv = sl.d[lane], qv = sl.q[lane], sv = sl.s[lane];
+        double2 ph = sl.ph[lane], r = sl.r[lane];
+        if (i + kLeadF < g.i1) issue(ring[(i + kLeadF - g.i0) % kRingF], i + kLeadF);
+        cpa_commit();
+        const size_t off = (size_t)i * P + j;
+        ph.x = fma(alpha, dv.x, ph.x);
+        ph.y = fma(alpha, dv.y, ph.y);
+        st2(phi, off, ph);
+        r.x = fma(-alpha, qv.x, r.x);
+        r.y = fma(-alpha, qv.y, r.y);
+        st2(rp, off, r);
+        put_rbf(a, M, i, j, r);
+        rsp = fma(r.x, sv.x, rsp);
+        rsp = fma(r.y, sv.y, rsp);
+      }
+      cpa_wait_all();  // the warp's next tile refills the same slots
+      rsp = warp_sum(rsp);
+      if (lane == 0) __stcg(a.P2 + t, rsp);
+      continue;
+    }
+    // refresh iterations (phi only): rows in groups of four, all loads of a group first
     for (int i = g.i0; i < g.i1; i += 4) {
       double2 dv[4], ph[4], qv[4], sv[4], rv[4];
 #pragma unroll
@@ -587,7 +642,7 @@ static cudaError_t fcg_iteration(Plan& pl, int kind, cudaStream_t st) {
     return e == cudaSuccess ? cudaGetLastError() : e;
   }
   k_f_a<<<nb, kThreads, 0, st>>>(pl.dargs);
-  k_f_b<<<nb, kThreads, 0, st>>>(pl.dargs);
+  k_f_b<<<nb, kThreads, kRingFSmem, st>>>(pl.dargs);
   k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = fcg_precond(pl, kind, st, fd);
@@ -597,6 +652,8 @@ static cudaError_t fcg_iteration(Plan& pl, int kind, cudaStream_t st) {
 
 // Dynamic shared memory above 48 KB is an attribute of the function on the current device.
 static cudaError_t fcg_attrs() {
+  const cudaError_t e = cudaFuncSetAttribute(k_f_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingFSmem);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_x_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBSmem);
 }
 
@@ -723,7 +780,8 @@ static cudaError_t fcg_eager(Plan& pl, int kind, cudaStream_t st) {
   if (mixed_fcg(pl, kind)) return fcg_eager_mixed(pl, kind, st);
   const MapDesc& M = pl.hmaps[0];
   const int nb = tile_blocks(pl);
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = fcg_attrs();
+  if (e != cudaSuccess) return e;
   phase_mark(pl, st, -1);
   k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 0);
   phase_mark(pl, st, 2);
@@ -743,7 +801,7 @@ static cudaError_t fcg_eager(Plan& pl, int kind, cudaStream_t st) {
     phase_mark(pl, st, -1);
     k_f_a<<<nb, kThreads, 0, st>>>(pl.dargs);
     phase_mark(pl, st, 0);
-    k_f_b<<<nb, kThreads, 0, st>>>(pl.dargs);
+    k_f_b<<<nb, kThreads, kRingFSmem, st>>>(pl.dargs);
     phase_mark(pl, st, 1);
     k_f_res<<<nb, kThreads, 0, st>>>(pl.dargs, 1);
     phase_mark(pl, st, 2);

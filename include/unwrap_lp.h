@@ -191,7 +191,11 @@ ULP_API void ulp_plan_destroy(ulp_plan plan);
  *   stats: host pointer or NULL.  Non-NULL makes the call synchronise the
  *   stream and fill *stats; the return value is then the solve's status.
  *   NULL returns after enqueueing (ULP_OK unless an argument is invalid);
- *   ulp_plan_last_status() reads the outcome later. */
+ *   ulp_plan_last_status() reads the outcome later.
+ *   With max_outer > 8 (and opt.graph = 0) the call also waits for the GPU
+ *   after every 8 passes and enqueues no further pass once every map has left
+ *   its outer loop (a pass past the outer stop would do nothing but cost its
+ *   launches); the results are the same. */
 ULP_API int ulp_unwrap(ulp_plan plan, const double* psi, const uint8_t* mask, double p, double eps,
                int precond, double tol, int max_outer, int max_inner, double* phi,
                void* cuda_stream, ulp_stats* stats);

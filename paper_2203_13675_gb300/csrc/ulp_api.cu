@@ -385,9 +385,31 @@ static int collect(Plan& pl, cudaStream_t st, ulp_stats* per_map) {
   return worst;
 }
 
-// Enqueues one call of Algorithm 1 for every map of the plan on stream st.
+// Outer passes enqueued before the host first looks at whether any map is still in its
+// outer loop (calls with more passes than this; see enqueue_call).
+constexpr int kOuterAhead = 8;
+
+// 1 if any map of the plan is still in its outer loop: the maps' flags read after the
+// work enqueued so far (the call waits for it).
+static int any_outer_active(Plan& pl, cudaStream_t st) {
+  std::vector<int> act(pl.nmaps, 0);
+  if (cudaMemcpy2DAsync(act.data(), sizeof(int), &pl.dstate[0].outer_active, sizeof(MapState), sizeof(int),
+                        pl.nmaps, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return -1;
+  for (int v : act)
+    if (v) return 1;
+  return 0;
+}
+
+// Enqueues one call of Algorithm 1 for every map of the plan on stream st.  The passes
+// decide on the device whether they run; a pass after the outer loop has stopped returns
+// at once, but its launches still cost tens of microseconds.  So with more than
+// kOuterAhead passes, and when the call may wait (not under stream capture, not a plan
+// whose calls run beside others), the host stops enqueuing passes once every map has left
+// its outer loop, looking after every kOuterAhead passes.
 static int enqueue_call(Plan& pl, const ulp_map* maps, int precond, double tol, int max_outer, int max_inner,
-                        cudaStream_t st, bool mixed) {
+                        cudaStream_t st, bool mixed, bool may_wait) {
   for (int first = 0; first < pl.nmaps; first += 64) {
     PT pt{};
     const int cnt = pl.nmaps - first < 64 ? pl.nmaps - first : 64;
@@ -416,6 +438,11 @@ static int enqueue_call(Plan& pl, const ulp_map* maps, int precond, double tol, 
     else if (mixed) ULP_CU(launch_pcg32(pl, precond, a, st, e0, e1));
     else ULP_CU(launch_pcg64(pl, precond, a, st, e0, e1));
     ULP_CU(launch_outer_error(pl, pl.opt.outer_tol, max_outer, st));
+    if (may_wait && !pl.concurrent && max_outer > kOuterAhead && (k + 1) % kOuterAhead == 0 && k + 1 < max_outer) {
+      const int act = any_outer_active(pl, st);
+      if (act < 0) return fail(ULP_ERR_CUDA, "reading the outer-loop flags: %s", cudaGetErrorString(cudaGetLastError()));
+      if (act == 0) break;
+    }
   }
   for (int m = 0; m < pl.nmaps; ++m) ULP_CU(launch_unpack(pl, m, maps[m].phi, st));
   return ULP_OK;
@@ -440,7 +467,7 @@ static int graph_call(Plan& pl, const ulp_map* maps, int precond, double tol, in
     if (!pl.cap_stream) ULP_CU(cudaStreamCreateWithFlags(&pl.cap_stream, cudaStreamNonBlocking));
     const long long before = pl.kernel_launches;
     ULP_CU(cudaStreamBeginCapture(pl.cap_stream, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_call(pl, maps, precond, tol, max_outer, max_inner, pl.cap_stream, mixed);
+    int rc = enqueue_call(pl, maps, precond, tol, max_outer, max_inner, pl.cap_stream, mixed, false);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(pl.cap_stream, &g);
     if (rc != ULP_OK) {
@@ -498,6 +525,7 @@ static int batched_sub_call(Plan& pl, const ulp_map* maps, int precond, double t
         pl.sub.clear();
         return rc;
       }
+      pl.sub[m]->p.concurrent = true;  // the maps' calls run side by side on several streams
     }
     ULP_CU(cudaSetDevice(pl.device));
     pl.sub_st.assign(ns, nullptr);
@@ -572,7 +600,7 @@ extern "C" int ulp_unwrap_batched(ulp_plan plan, const ulp_map* maps, int precon
   // nested: they run eagerly
   if (pl.opt.graph && !pl.opt.profile && !is_fcg_kind(precond))
     rc = graph_call(pl, maps, precond, tol, max_outer, max_inner, st, mixed);
-  else rc = enqueue_call(pl, maps, precond, tol, max_outer, max_inner, st, mixed);
+  else rc = enqueue_call(pl, maps, precond, tol, max_outer, max_inner, st, mixed, true);
   if (rc != ULP_OK) return rc;
   if (per_map) return collect(pl, st, per_map);
   pl.last_status = ULP_OK;

@@ -21,6 +21,8 @@ struct Plan {
   int bps = 1;               // resident blocks per SM of the persistent solvers
   int bx_elem = 1;           // blocks per map of the elementwise kernels
   bool system_x = false;     // the current call builds its system with launch_system_x
+  bool concurrent = false;   // the plan's calls run beside others (a batched plan's per-map plans):
+                             // a call never waits for the GPU
   ulp_options opt{};
   std::vector<MapDesc> hmaps;
   MapDesc* dmaps = nullptr;

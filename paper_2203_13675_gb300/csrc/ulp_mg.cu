@@ -467,6 +467,7 @@ __device__ __forceinline__ void sts4(float* p, int rr, int lane, const float4& v
 
 // pre-smoothing + residual + restriction for the fine rows [TR band, TR band + TR), TR even
 __global__ void __launch_bounds__(kTileThreads) k_mg_down_t(Grid f, Grid c, int TR, const MapState* S) {
+  if (skip_map(S)) return;
   extern __shared__ float4 tsm4[];
   float* sU = reinterpret_cast<float*>(tsm4);
   float* sV = sU + kTilePlane;
@@ -492,7 +493,6 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_down_t(Grid f, Grid c, int 
     sts4(sX1, rr, lane,
          make_float4(kOmegaF * D.x * B.x, kOmegaF * D.y * B.y, kOmegaF * D.z * B.z, kOmegaF * D.w * B.w));
   }
-  if (skip_map(S)) return;  // the same value in every thread: nothing of this launch changes it
   __syncthreads();
   // x2 at rows r0-1 .. r1 (0 outside the grid)
   for (int rr = 1 + warp; rr <= nrow - 2; rr += kTileWarps) {
@@ -539,6 +539,7 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_up_t(Grid f, Grid c, const 
                                                         float* s32, const PcgArgs* pa, const MapState* S, int ph) {
   constexpr bool MAP = MODE != kUpCoarse;
   constexpr int kOut = kTileMaxRows / kTileWarps;  // output rows per warp at most
+  if (skip_map(S)) return;
   extern __shared__ float4 tsm4[];
   __shared__ double red[2][kTileWarps];
   float* sU = reinterpret_cast<float*>(tsm4);
@@ -588,7 +589,6 @@ __global__ void __launch_bounds__(kTileThreads) k_mg_up_t(Grid f, Grid c, const 
     }
     sts4(sXP, rr, lane, XP);
   }
-  if (skip_map(S)) return;  // read before any arrival of this launch: the same in every thread
   __syncthreads();
   // t at rows r0-1 .. r1 (0 outside the grid)
   for (int rr = 1 + warp; rr <= nrow - 2; rr += kTileWarps) {
@@ -741,6 +741,7 @@ __device__ __forceinline__ void down_issue(DownSlot& sl, const Grid& f, int r, i
 
 // pre-smoothing + residual + restriction for the coarse rows [RB band, RB band + RB)
 __global__ void __launch_bounds__(kWalkWarps * 32) k_mg_down_w(Grid f, Grid c, int RB, const MapState* S) {
+  if (skip_map(S)) return;
   extern __shared__ float4 wsm4[];
   int seg, band, j, lane;
   if (!walk_warp(f.W, (c.H + RB - 1) / RB, seg, band, j, lane)) return;
@@ -758,11 +759,6 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_mg_down_w(Grid f, Grid c, i
   for (int k = 0; k < kLead; ++k) {
     if (rb + k <= re) down_issue(ring[k], f, rb + k, j, lane);
     cp_commit();
-  }
-  // the map's stop flag, read while the first rows are in flight
-  if (skip_map(S)) {
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    return;
   }
   for (int r = rb; r <= re; ++r) {
     if (r + kLead <= re) down_issue(ring[(r + kLead - rb) % kRing], f, r + kLead, j, lane);
@@ -841,6 +837,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_mg_up_w(Grid f, Grid c, con
                                                              const double* __restrict__ rv, float* s32,
                                                              const PcgArgs* pa, const MapState* S, int ph) {
   constexpr bool MAP = MODE != kUpCoarse;
+  if (skip_map(S)) return;
   extern __shared__ float4 wsm4[];
   int seg, band, j, lane;
   const int bands = (f.H + R - 1) / R;
@@ -858,11 +855,6 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_mg_up_w(Grid f, Grid c, con
   for (int k = 0; k < kLead; ++k) {
     if (rb + k <= re) up_issue<MODE>(ring[k], f, c, xc, mask, rv, rb + k, j, lane);
     cp_commit();
-  }
-  // the map's stop flag, read while the first rows are in flight
-  if (skip_map(S)) {
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    return;
   }
   for (int r = rb; r <= re; ++r) {
     if (r + kLead <= re) up_issue<MODE>(ring[(r + kLead - rb) % kRing], f, c, xc, mask, rv, r + kLead, j, lane);
@@ -1114,6 +1106,7 @@ __device__ __forceinline__ void tail_coarsest(const TailGrids& tg, const TailSme
 constexpr int kTailWarpPx = kTailSmallThreads;
 
 __global__ void __launch_bounds__(kTailThreads) k_mg_tail(TailGrids tg, const MapState* S) {
+  if (skip_map(S)) return;
   extern __shared__ float smem[];
   const int tot = tg.off[tg.n - 1] + tg.g[tg.n - 1].H * tg.g[tg.n - 1].W;
   TailSmem sm;
@@ -1144,7 +1137,6 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(TailGrids tg, const Ma
         if (l == 0) rb[q] = g.b[o];
       }
     }
-    if (skip_map(S)) return;  // read with the loads above in flight
 #pragma unroll
     for (int q = 0; q < kq; ++q) {
       const int k = threadIdx.x + kTailThreads * q;
